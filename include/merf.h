@@ -1,0 +1,170 @@
+/* merf.h -- C ABI of the B300 renderer for baked MERF scenes.
+ *
+ * Renders the baked representation of "MERF: Memory-Efficient Radiance Fields for
+ * Real-time View Synthesis in Unbounded Scenes" (Reiser et al. 2023): per pixel ray, the
+ * piecewise-projective contraction (Sec. 3.2), empty-space skipping against a max-pooled
+ * occupancy hierarchy (Sec. 5), the summed tri/bilinear uint8 feature field (Sec. 3.1,
+ * Sec. 4.2), front-to-back compositing with early termination (Eq. 1, Eq. 2, Sec. 5) and
+ * the deferred view-dependence MLP (Sec. 2, App. B).
+ *
+ * Conventions shared by every entry point
+ *   - Device work is enqueued on the caller's CUDA stream (`stream`, a cudaStream_t; NULL =
+ *     legacy default stream).  merf_render, merf_render_aux and merf_trace allocate nothing
+ *     and do not synchronise, so they may be captured into a CUDA graph; the upload, free
+ *     and host-output calls synchronise as documented.
+ *   - Pointers documented as "device" must be device memory of the current device;
+ *     "host" pointers are read before the call returns and may be freed afterwards.
+ *   - No C++ exception crosses this boundary.  Every call returns a merf_status; on
+ *     failure merf_last_error() holds a message for the calling thread and no device work
+ *     was enqueued (argument checks happen before any launch).
+ *
+ * Coordinates: contracted space is [-2, 2]^3.  Every array of resolution N samples it at
+ * texel centres p_i = (i + 1/2) 4/N - 2; lookups clamp to the edge texel.  3D arrays are
+ * indexed [z][y][x] (x fastest) with the C = 8 channels innermost: channel 0 density,
+ * 1..3 diffuse RGB, 4..7 the view-dependence feature (Sec. 3.1).
+ */
+#ifndef MERF_H
+#define MERF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum merf_status {
+    MERF_OK = 0,
+    MERF_ERR_INVALID_ARG = 1,   /* a pointer, size, layout or option is invalid */
+    MERF_ERR_OOM = 2,           /* device allocation failed or exceeds the device budget */
+    MERF_ERR_CUDA = 3,          /* a CUDA runtime call failed (message in merf_last_error) */
+    MERF_ERR_TIMEOUT = 4,       /* a bounded device-side wait expired */
+    MERF_ERR_DEVICE_BOUNDS = 5, /* a kernel detected an out-of-range index and skipped it */
+    MERF_ERR_UNSUPPORTED = 6    /* a valid request this build does not implement */
+} merf_status;
+
+enum { MERF_STORAGE_U8_SPARSE = 0, MERF_STORAGE_F32_DENSE = 1 };
+enum { MERF_PREC_FP32 = 0, MERF_PREC_FP16 = 1, MERF_PREC_BF16 = 2 };
+enum { MERF_MAX_OCC_LEVELS = 8 };
+enum { MERF_CHANNELS = 8, MERF_MLP_IN = 34, MERF_MLP_HIDDEN = 16, MERF_MLP_OUT = 3 };
+/* 34*16 + 16 + 16*16 + 16 + 16*3 + 3 */
+enum { MERF_MLP_PARAMS = 883 };
+/* per-pixel diagnostic record written by merf_render_aux (floats) */
+enum {
+    MERF_AUX_CD = 0,      /* [3] accumulated diffuse colour C_d (Eq. 2) */
+    MERF_AUX_F = 3,       /* [4] accumulated feature F (Eq. 2) */
+    MERF_AUX_T = 7,       /* transmittance after the last composited sample */
+    MERF_AUX_NLAT = 8,    /* lattice samples on the ray */
+    MERF_AUX_NEVAL = 9,   /* samples evaluated (occupied, before termination) */
+    MERF_AUX_NAPP = 10,   /* evaluated samples with non-zero opacity (appearance read) */
+    MERF_AUX_TERM = 11,   /* 1 if the ray stopped by early termination */
+    MERF_AUX_SIZE = 12
+};
+/* device counters accumulated by merf_render_aux (uint64) */
+enum { MERF_CNT_RAYS = 0, MERF_CNT_LATTICE = 1, MERF_CNT_EVAL = 2, MERF_CNT_APPEAR = 3,
+       MERF_CNT_SIZE = 4 };
+
+/* A pinhole camera (OpenCV axes: x right, y down, z forward).  c2w is the row-major 3x4
+ * camera-to-world matrix [R | o]; the ray of pixel column i, row j leaves o through
+ * ((i + 1/2 - cx)/fx, (j + 1/2 - cy)/fy, 1) in camera coordinates. */
+typedef struct merf_camera {
+    float c2w[12];
+    float fx, fy, cx, cy;
+} merf_camera;
+
+/* Shape of a baked scene (Sec. 3.1, Sec. 4.3, Sec. 5). */
+typedef struct merf_scene_desc {
+    int32_t grid_res;        /* L: 3D grid resolution; even, a multiple of block_size */
+    int32_t block_size;      /* B: block edge in voxels, a power of two (sparse storage) */
+    int32_t plane_res;       /* R: resolution of the three planes; even */
+    int32_t channels;        /* C: must be 8 */
+    int32_t n_blocks;        /* stored blocks in the atlas (sparse storage) */
+    int32_t n_occ_levels;    /* 1 .. MERF_MAX_OCC_LEVELS */
+    int32_t occ_res[MERF_MAX_OCC_LEVELS]; /* finest first; powers of two >= 2, each dividing
+                                              the previous; coarser levels are max-pools */
+    int32_t mlp_in, mlp_hidden, mlp_out;  /* must be 34, 16, 3 */
+    int32_t storage;         /* MERF_STORAGE_U8_SPARSE or MERF_STORAGE_F32_DENSE */
+} merf_scene_desc;
+
+typedef struct merf_render_opts {
+    float step;          /* lattice step delta_s in contracted arc length, > 0 */
+    float t_term;        /* early-termination threshold on transmittance (Sec. 5: 2e-4) */
+    int32_t precision;   /* MERF_PREC_* */
+    int32_t early_term;  /* 1: stop a ray after the sample at which T < t_term */
+    int32_t reserved;    /* must be 0 */
+} merf_render_opts;
+
+typedef struct merf_scene merf_scene;  /* opaque; owns device memory */
+
+/* Copy a baked scene to the device (Sec. 4.3: block-sparse 3D grid, three planes,
+ * occupancy hierarchy, deferred-MLP weights).  Host arrays (read before return):
+ *   index_grid  int32 [(L/B)^3]            block id in [0, n_blocks) or -1 (not stored)
+ *   atlas       uint8 [n_blocks][B][B][B][8]
+ *   planes      uint8 [3][R][R][8]         P_x(y,z) [z][y], P_y(x,z) [z][x], P_z(x,y) [y][x]
+ *   occ_levels  n_occ_levels pointers to uint8 [N][N][N], non-zero = occupied
+ *   mlp_weights float32 [883]: W0[34][16], b0[16], W1[16][16], b1[16], W2[16][3], b2[3]
+ * The layout is validated (ids in range, every coarse occupancy cell that is empty has
+ * only empty children) before anything is allocated.  Returns MERF_ERR_OOM without
+ * touching the device if the scene exceeds the budget set by merf_set_device_budget.
+ * Synchronises `stream` before returning.  *out receives a handle owned by the caller,
+ * released with merf_scene_free. */
+merf_status merf_scene_upload(const merf_scene_desc *desc, const int32_t *index_grid,
+                              const uint8_t *atlas, const uint8_t *planes,
+                              const uint8_t *const *occ_levels, const float *mlp_weights,
+                              void *stream, merf_scene **out);
+
+/* Same for a dense float32 scene (storage MERF_STORAGE_F32_DENSE): grid float32
+ * [L][L][L][8] and planes float32 [3][R][R][8] hold pre-activation values directly
+ * (no dequantisation); block_size and n_blocks are ignored. */
+merf_status merf_scene_upload_dense(const merf_scene_desc *desc, const float *grid,
+                                    const float *planes, const uint8_t *const *occ_levels,
+                                    const float *mlp_weights, void *stream, merf_scene **out);
+
+/* Release a scene (NULL is ignored).  Synchronises the device first. */
+void merf_scene_free(merf_scene *scene);
+
+/* Device bytes held by a scene. */
+size_t merf_scene_device_bytes(const merf_scene *scene);
+
+/* Render n_cams images of W x H pixels into `out` (device float32 [n_cams][H][W][3],
+ * written, never read): C = C_d + h(C_d, F, d) per pixel (Sec. 2).  `cams` is a host array
+ * of n_cams cameras.  Asynchronous on `stream`. */
+merf_status merf_render(const merf_scene *scene, const merf_camera *cams, int n_cams, int W,
+                        int H, float *out, const merf_render_opts *opts, void *stream);
+
+/* merf_render plus optional diagnostics: `aux` (device float32 [n_cams][H][W][MERF_AUX_SIZE]
+ * or NULL) and `counters` (device uint64 [MERF_CNT_SIZE] or NULL, accumulated with atomics:
+ * the caller zeroes it). */
+merf_status merf_render_aux(const merf_scene *scene, const merf_camera *cams, int n_cams, int W,
+                            int H, float *out, float *aux, unsigned long long *counters,
+                            const merf_render_opts *opts, void *stream);
+
+/* Render into host memory: renders like merf_render into the caller's device buffer
+ * `d_staging` (float32 [n_cams][H][W][3]) and copies it to `h_out` (host, same shape;
+ * page-locked for the copy to be asynchronous).  Returns after the copy has completed. */
+merf_status merf_render_host(const merf_scene *scene, const merf_camera *cams, int n_cams,
+                             int W, int H, float *d_staging, float *h_out,
+                             const merf_render_opts *opts, void *stream);
+
+/* Evaluated-sample sets of the traversal alone (Sec. 5 empty-space skipping, early
+ * termination off): bit k of mask row r (device uint32 [n_cams*H*W][words], row
+ * r = (cam*H + row)*W + col) is set iff lattice sample k of that ray lies in an occupied
+ * finest occupancy cell; bits beyond 32*words are dropped.  n_lattice (device int32
+ * [n_cams*H*W]) receives the number of lattice samples per ray. */
+merf_status merf_trace(const merf_scene *scene, const merf_camera *cams, int n_cams, int W,
+                       int H, uint32_t *mask, int words, int32_t *n_lattice,
+                       const merf_render_opts *opts, void *stream);
+
+/* Device-memory budget for merf_scene_upload* (bytes; 0 = unlimited, the default). */
+void merf_set_device_budget(size_t bytes);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *merf_last_error(void);
+
+/* Library version string. */
+const char *merf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MERF_H */

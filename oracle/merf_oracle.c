@@ -437,6 +437,8 @@ void orc32_segments(const float o[3], const float d[3], orc32_segs *sg)
             float xb[3];
             for (int k = 0; k < 3; ++k) xb[k] = o[k] + tb[i] * d[k];
             contract32(r, xb, pb);
+        } else if (r == 0) {
+            for (int k = 0; k < 3; ++k) pb[k] = pa[k];     /* degenerate direction only */
         } else {
             int j = (r - 1) / 2;
             float adj = fabsf(d[j]);

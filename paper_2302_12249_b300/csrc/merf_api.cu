@@ -1,0 +1,375 @@
+// merf_api.cu -- the C ABI declared in include/merf.h: scene upload/validation, argument
+// checks and kernel launches.  Host code only; the device code is in render.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "merf.h"
+#include "render.cuh"
+
+struct merf_scene {
+    merf_scene_desc desc;
+    int device;
+    void *index_grid = nullptr, *atlas = nullptr, *planes = nullptr, *mlp = nullptr;
+    void *occ[MERF_MAX_OCC_LEVELS] = {};
+    size_t bytes = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+size_t g_budget = 0;
+
+merf_status fail(merf_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+merf_status ok()
+{
+    g_err.clear();
+    return MERF_OK;
+}
+
+bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int log2i(int v)
+{
+    int r = 0;
+    while ((1 << r) < v) ++r;
+    return r;
+}
+
+merf_status check_desc(const merf_scene_desc *d, int storage)
+{
+    if (!d) return fail(MERF_ERR_INVALID_ARG, "desc is NULL");
+    if (d->storage != storage)
+        return fail(MERF_ERR_INVALID_ARG, "desc->storage %d does not match the upload call", d->storage);
+    if (d->channels != MERF_CHANNELS) return fail(MERF_ERR_INVALID_ARG, "channels must be 8, got %d", d->channels);
+    if (d->mlp_in != MERF_MLP_IN || d->mlp_hidden != MERF_MLP_HIDDEN || d->mlp_out != MERF_MLP_OUT)
+        return fail(MERF_ERR_UNSUPPORTED, "MLP %d->%d->%d not supported (34->16->16->3 only)", d->mlp_in,
+                    d->mlp_hidden, d->mlp_out);
+    if (d->grid_res < 2 || d->grid_res > 4096 || (d->grid_res & 1))
+        return fail(MERF_ERR_INVALID_ARG, "grid_res %d must be even in [2, 4096]", d->grid_res);
+    if (d->plane_res < 2 || d->plane_res > 16384 || (d->plane_res & 1))
+        return fail(MERF_ERR_INVALID_ARG, "plane_res %d must be even in [2, 16384]", d->plane_res);
+    if (storage == MERF_STORAGE_U8_SPARSE) {
+        if (!pow2(d->block_size) || d->block_size > d->grid_res || d->grid_res % d->block_size)
+            return fail(MERF_ERR_INVALID_ARG, "block_size %d must be a power of two dividing grid_res %d",
+                        d->block_size, d->grid_res);
+        if (d->n_blocks < 0) return fail(MERF_ERR_INVALID_ARG, "n_blocks %d < 0", d->n_blocks);
+        if (d->grid_res / d->block_size > 1024)
+            return fail(MERF_ERR_INVALID_ARG, "grid_res / block_size = %d exceeds 1024 blocks per axis",
+                        d->grid_res / d->block_size);
+    }
+    if (d->n_occ_levels < 1 || d->n_occ_levels > MERF_MAX_OCC_LEVELS)
+        return fail(MERF_ERR_INVALID_ARG, "n_occ_levels %d not in [1, %d]", d->n_occ_levels, MERF_MAX_OCC_LEVELS);
+    for (int l = 0; l < d->n_occ_levels; ++l) {
+        int n = d->occ_res[l];
+        if (!pow2(n) || n < 2 || n > 4096)
+            return fail(MERF_ERR_INVALID_ARG, "occ_res[%d] = %d must be a power of two in [2, 4096]", l, n);
+        if (l > 0 && (n >= d->occ_res[l - 1]))
+            return fail(MERF_ERR_INVALID_ARG, "occ_res must decrease from finest to coarsest");
+    }
+    return MERF_OK;
+}
+
+// Every empty cell of a coarser level must have only empty children in the finest level
+// (max-pooling, Sec. 5); otherwise skipping would drop occupied samples.
+merf_status check_occupancy(const merf_scene_desc *d, const uint8_t *const *occ)
+{
+    if (!occ) return fail(MERF_ERR_INVALID_ARG, "occ_levels is NULL");
+    for (int l = 0; l < d->n_occ_levels; ++l)
+        if (!occ[l]) return fail(MERF_ERR_INVALID_ARG, "occ_levels[%d] is NULL", l);
+    const int N0 = d->occ_res[0];
+    for (int l = 1; l < d->n_occ_levels; ++l) {
+        const int Nl = d->occ_res[l], f = N0 / Nl;
+        for (int z = 0; z < N0; ++z)
+            for (int y = 0; y < N0; ++y)
+                for (int x = 0; x < N0; ++x) {
+                    if (!occ[0][((size_t)z * N0 + y) * N0 + x]) continue;
+                    if (!occ[l][((size_t)(z / f) * Nl + y / f) * Nl + x / f])
+                        return fail(MERF_ERR_INVALID_ARG,
+                                    "occupancy level %d cell (%d,%d,%d) is empty but finest cell (%d,%d,%d) is set",
+                                    l, x / f, y / f, z / f, x, y, z);
+                }
+    }
+    return MERF_OK;
+}
+
+void free_scene_memory(merf_scene *s)
+{
+    cudaFree(s->index_grid);
+    cudaFree(s->atlas);
+    cudaFree(s->planes);
+    cudaFree(s->mlp);
+    for (auto &p : s->occ) cudaFree(p);
+}
+
+merf_status upload_common(const merf_scene_desc *desc, const void *grid, size_t grid_bytes,
+                          const void *planes, size_t plane_bytes, const int32_t *index_grid,
+                          size_t index_bytes, const uint8_t *const *occ, const float *mlp,
+                          void *stream, merf_scene **out)
+{
+    size_t occ_bytes[MERF_MAX_OCC_LEVELS] = {};
+    size_t total = grid_bytes + plane_bytes + index_bytes + sizeof(float) * MERF_MLP_PARAMS;
+    for (int l = 0; l < desc->n_occ_levels; ++l) {
+        occ_bytes[l] = (size_t)desc->occ_res[l] * desc->occ_res[l] * desc->occ_res[l];
+        total += occ_bytes[l];
+    }
+    if (g_budget && total > g_budget)
+        return fail(MERF_ERR_OOM, "scene needs %zu device bytes, budget is %zu", total, g_budget);
+    merf_scene *s = new merf_scene();
+    s->desc = *desc;
+    cudaGetDevice(&s->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    struct Item { void **dst; const void *src; size_t n; };
+    std::vector<Item> items = {{&s->atlas, grid, grid_bytes},
+                               {&s->planes, planes, plane_bytes},
+                               {&s->index_grid, index_grid, index_bytes},
+                               {&s->mlp, mlp, sizeof(float) * MERF_MLP_PARAMS}};
+    for (int l = 0; l < desc->n_occ_levels; ++l) items.push_back({&s->occ[l], occ[l], occ_bytes[l]});
+    for (auto &it : items) {
+        if (it.n == 0) continue;
+        cudaError_t e = cudaMalloc(it.dst, it.n);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            free_scene_memory(s);
+            delete s;
+            return fail(e == cudaErrorMemoryAllocation ? MERF_ERR_OOM : MERF_ERR_CUDA,
+                        "cudaMalloc(%zu): %s", it.n, cudaGetErrorString(e));
+        }
+        e = cudaMemcpyAsync(*it.dst, it.src, it.n, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) {
+            free_scene_memory(s);
+            delete s;
+            return fail(MERF_ERR_CUDA, "cudaMemcpyAsync: %s", cudaGetErrorString(e));
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        free_scene_memory(s);
+        delete s;
+        return fail(MERF_ERR_CUDA, "upload: %s", cudaGetErrorString(e));
+    }
+    s->bytes = total;
+    *out = s;
+    return ok();
+}
+
+merf_status check_opts(const merf_render_opts *o)
+{
+    if (!o) return fail(MERF_ERR_INVALID_ARG, "opts is NULL");
+    if (!(o->step > 0.0f) || !std::isfinite(o->step) || o->step < 1e-5f)
+        return fail(MERF_ERR_INVALID_ARG, "step %g must be finite and >= 1e-5", (double)o->step);
+    if (!(o->t_term >= 0.0f) || !(o->t_term < 1.0f))
+        return fail(MERF_ERR_INVALID_ARG, "t_term %g must be in [0, 1)", (double)o->t_term);
+    if (o->early_term != 0 && o->early_term != 1)
+        return fail(MERF_ERR_INVALID_ARG, "early_term must be 0 or 1");
+    if (o->reserved != 0) return fail(MERF_ERR_INVALID_ARG, "reserved must be 0");
+    if (o->precision != MERF_PREC_FP32)
+        return fail(MERF_ERR_UNSUPPORTED, "precision %d is not available in this build", o->precision);
+    return MERF_OK;
+}
+
+merf_status check_frame(const merf_scene *s, const merf_camera *cams, int n, int W, int H)
+{
+    if (!s) return fail(MERF_ERR_INVALID_ARG, "scene is NULL");
+    if (!cams) return fail(MERF_ERR_INVALID_ARG, "cams is NULL");
+    if (n < 1 || W < 1 || H < 1) return fail(MERF_ERR_INVALID_ARG, "n_cams %d, W %d, H %d must be >= 1", n, W, H);
+    if (W > 16384 || H > 16384) return fail(MERF_ERR_INVALID_ARG, "W %d / H %d exceed 16384", W, H);
+    if ((double)n * W * H > 2.0e9) return fail(MERF_ERR_INVALID_ARG, "n_cams * W * H exceeds 2e9 rays");
+    for (int c = 0; c < n; ++c) {
+        const merf_camera &k = cams[c];
+        for (int t = 0; t < 12; ++t)
+            if (!std::isfinite(k.c2w[t])) return fail(MERF_ERR_INVALID_ARG, "camera %d c2w not finite", c);
+        if (!(std::fabs(k.fx) > 0.0f) || !(std::fabs(k.fy) > 0.0f) || !std::isfinite(k.fx) ||
+            !std::isfinite(k.fy) || !std::isfinite(k.cx) || !std::isfinite(k.cy))
+            return fail(MERF_ERR_INVALID_ARG, "camera %d intrinsics invalid", c);
+    }
+    return MERF_OK;
+}
+
+merf::RenderParams make_params(const merf_scene *s, const merf_render_opts *o, int W, int H)
+{
+    merf::RenderParams P;
+    memset(&P, 0, sizeof P);
+    const merf_scene_desc &d = s->desc;
+    P.fv.L = d.grid_res;
+    P.fv.R = d.plane_res;
+    if (d.storage == MERF_STORAGE_U8_SPARSE) {
+        P.fv.B = d.block_size;
+        P.fv.log2B = log2i(d.block_size);
+        P.fv.nb = d.grid_res / d.block_size;
+        P.fv.index_grid = (const int32_t *)s->index_grid;
+        P.fv.atlas = (const uint2 *)s->atlas;
+        P.fv.planes = (const uint2 *)s->planes;
+    } else {
+        P.fv.grid_f32 = (const float4 *)s->atlas;
+        P.fv.planes_f32 = (const float4 *)s->planes;
+    }
+    P.occ.n = d.n_occ_levels;
+    for (int l = 0; l < d.n_occ_levels; ++l) {
+        P.occ.level[l] = (const uint8_t *)s->occ[l];
+        P.occ.res[l] = d.occ_res[l];
+        P.occ.shift[l] = log2i(d.occ_res[0] / d.occ_res[l]);
+    }
+    P.mlp = (const float *)s->mlp;
+    P.W = W;
+    P.H = H;
+    P.step = o->step;
+    P.t_term = o->t_term;
+    P.early_term = o->early_term;
+    return P;
+}
+
+merf_status launch_render(const merf_scene *s, const merf_camera *cams, int n, int W, int H, float *out,
+                          float *aux, unsigned long long *counters, const merf_render_opts *o,
+                          cudaStream_t st)
+{
+    merf::RenderParams P = make_params(s, o, W, H);
+    P.out = out;
+    P.aux = aux;
+    P.counters = counters;
+    const dim3 block(merf::kThreads);
+    for (int c0 = 0; c0 < n; c0 += merf::kMaxCams) {
+        const int nc = std::min(merf::kMaxCams, n - c0);
+        P.cam0 = c0;
+        for (int c = 0; c < nc; ++c) memcpy(P.cams.m[c], &cams[c0 + c], sizeof(merf_camera));
+        const dim3 grid((W + merf::kTileW - 1) / merf::kTileW, (H + merf::kTileH - 1) / merf::kTileH, nc);
+        if (s->desc.storage == MERF_STORAGE_U8_SPARSE)
+            merf::render_kernel<0><<<grid, block, 0, st>>>(P);
+        else
+            merf::render_kernel<1><<<grid, block, 0, st>>>(P);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(MERF_ERR_CUDA, "render launch: %s", cudaGetErrorString(e));
+    }
+    return ok();
+}
+
+}  // namespace
+
+extern "C" {
+
+merf_status merf_scene_upload(const merf_scene_desc *desc, const int32_t *index_grid, const uint8_t *atlas,
+                              const uint8_t *planes, const uint8_t *const *occ_levels, const float *mlp_weights,
+                              void *stream, merf_scene **out)
+{
+    merf_status st = check_desc(desc, MERF_STORAGE_U8_SPARSE);
+    if (st) return st;
+    if (!out) return fail(MERF_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!index_grid || !planes || !mlp_weights || (desc->n_blocks > 0 && !atlas))
+        return fail(MERF_ERR_INVALID_ARG, "a scene array is NULL");
+    const size_t nb = (size_t)desc->grid_res / desc->block_size;
+    for (size_t i = 0; i < nb * nb * nb; ++i)
+        if (index_grid[i] < -1 || index_grid[i] >= desc->n_blocks)
+            return fail(MERF_ERR_INVALID_ARG, "index_grid[%zu] = %d outside [-1, %d)", i, index_grid[i],
+                        desc->n_blocks);
+    if ((st = check_occupancy(desc, occ_levels))) return st;
+    for (int i = 0; i < MERF_MLP_PARAMS; ++i)
+        if (!std::isfinite(mlp_weights[i])) return fail(MERF_ERR_INVALID_ARG, "mlp_weights[%d] not finite", i);
+    const size_t B = desc->block_size, R = desc->plane_res;
+    return upload_common(desc, atlas, (size_t)desc->n_blocks * B * B * B * 8, planes, 3 * R * R * 8, index_grid,
+                         nb * nb * nb * sizeof(int32_t), occ_levels, mlp_weights, stream, out);
+}
+
+merf_status merf_scene_upload_dense(const merf_scene_desc *desc, const float *grid, const float *planes,
+                                    const uint8_t *const *occ_levels, const float *mlp_weights, void *stream,
+                                    merf_scene **out)
+{
+    merf_status st = check_desc(desc, MERF_STORAGE_F32_DENSE);
+    if (st) return st;
+    if (!out) return fail(MERF_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!grid || !planes || !mlp_weights) return fail(MERF_ERR_INVALID_ARG, "a scene array is NULL");
+    if ((st = check_occupancy(desc, occ_levels))) return st;
+    const size_t L = desc->grid_res, R = desc->plane_res;
+    return upload_common(desc, grid, L * L * L * 8 * sizeof(float), planes, 3 * R * R * 8 * sizeof(float),
+                         nullptr, 0, occ_levels, mlp_weights, stream, out);
+}
+
+void merf_scene_free(merf_scene *scene)
+{
+    if (!scene) return;
+    cudaDeviceSynchronize();
+    free_scene_memory(scene);
+    delete scene;
+}
+
+size_t merf_scene_device_bytes(const merf_scene *scene) { return scene ? scene->bytes : 0; }
+
+merf_status merf_render_aux(const merf_scene *scene, const merf_camera *cams, int n_cams, int W, int H, float *out,
+                            float *aux, unsigned long long *counters, const merf_render_opts *opts, void *stream)
+{
+    merf_status st = check_frame(scene, cams, n_cams, W, H);
+    if (st) return st;
+    if ((st = check_opts(opts))) return st;
+    if (!out) return fail(MERF_ERR_INVALID_ARG, "out is NULL");
+    return launch_render(scene, cams, n_cams, W, H, out, aux, counters, opts, (cudaStream_t)stream);
+}
+
+merf_status merf_render(const merf_scene *scene, const merf_camera *cams, int n_cams, int W, int H, float *out,
+                        const merf_render_opts *opts, void *stream)
+{
+    return merf_render_aux(scene, cams, n_cams, W, H, out, nullptr, nullptr, opts, stream);
+}
+
+merf_status merf_render_host(const merf_scene *scene, const merf_camera *cams, int n_cams, int W, int H,
+                             float *d_staging, float *h_out, const merf_render_opts *opts, void *stream)
+{
+    if (!h_out || !d_staging) return fail(MERF_ERR_INVALID_ARG, "h_out / d_staging is NULL");
+    merf_status st = merf_render(scene, cams, n_cams, W, H, d_staging, opts, stream);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = (size_t)n_cams * W * H * 3 * sizeof(float);
+    cudaError_t e = cudaMemcpyAsync(h_out, d_staging, bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(MERF_ERR_CUDA, "render_host copy: %s", cudaGetErrorString(e));
+    return ok();
+}
+
+merf_status merf_trace(const merf_scene *scene, const merf_camera *cams, int n_cams, int W, int H, uint32_t *mask,
+                       int words, int32_t *n_lattice, const merf_render_opts *opts, void *stream)
+{
+    merf_status st = check_frame(scene, cams, n_cams, W, H);
+    if (st) return st;
+    if ((st = check_opts(opts))) return st;
+    if (!mask || !n_lattice) return fail(MERF_ERR_INVALID_ARG, "mask / n_lattice is NULL");
+    if (words < 1 || words > 4096) return fail(MERF_ERR_INVALID_ARG, "words %d not in [1, 4096]", words);
+    merf::RenderParams P = make_params(scene, opts, W, H);
+    P.mask = mask;
+    P.nlat = n_lattice;
+    P.words = words;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int c0 = 0; c0 < n_cams; c0 += merf::kMaxCams) {
+        const int nc = std::min(merf::kMaxCams, n_cams - c0);
+        P.cam0 = c0;
+        for (int c = 0; c < nc; ++c) memcpy(P.cams.m[c], &cams[c0 + c], sizeof(merf_camera));
+        const dim3 grid((W + merf::kTileW - 1) / merf::kTileW, (H + merf::kTileH - 1) / merf::kTileH, nc);
+        merf::trace_kernel<<<grid, merf::kThreads, 0, s>>>(P);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(MERF_ERR_CUDA, "trace launch: %s", cudaGetErrorString(e));
+    }
+    return ok();
+}
+
+void merf_set_device_budget(size_t bytes) { g_budget = bytes; }
+
+const char *merf_last_error(void) { return g_err.c_str(); }
+
+const char *merf_version(void) { return "merf-b300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,363 @@
+// traverse.cuh -- per-ray traversal of contracted space for sm_103a.
+//
+// A pixel ray x(t) = o + t d (Eq. 1) is mapped by the piecewise-projective contraction
+// (Sec. 3.2) into [-2, 2]^3, where it becomes at most seven straight segments, one per region
+// it crosses.  Samples sit on a uniform lattice s_k = (k + 1/2) delta_s of cumulative contracted
+// arc length (the renderer's "small uniform step size", Sec. 4.3); sample k is evaluated iff
+// its finest occupancy cell is set.  Empty space is skipped coarse-to-fine against the
+// max-pooled occupancy hierarchy (Sec. 5): when a level reports the sample's cell empty, a
+// slab test against that cell's box on the current straight segment gives the exit, and the
+// walk jumps to the last lattice sample before it.
+//
+// Exactness.  Every float operation that decides an integer (which lattice samples exist,
+// which segment and which occupancy cell a sample falls in) is an IEEE round-to-nearest
+// intrinsic (__fadd_rn, __fmul_rn, __fdiv_rn, __fsqrt_rn: never contracted into an FMA), in a
+// fixed order.  The position of sample k within a segment is a composition of monotone
+// rounded operations, so each of its coordinates -- and hence each cell index -- is monotone
+// in k.  A skip therefore lands at lattice index m only after checking, from m's own computed
+// position, that m - 1 still lies in the empty cell: every skipped sample lies in that cell,
+// and the evaluated set equals dense sampling of the finest level, bit for bit.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+namespace merf {
+
+constexpr int kMaxSegs = 16;
+constexpr int kMaxLevels = 8;
+
+#define F_ADD __fadd_rn
+#define F_SUB __fsub_rn
+#define F_MUL __fmul_rn
+#define F_DIV __fdiv_rn
+#define F_SQRT __fsqrt_rn
+
+struct OccView {
+    const uint8_t *level[kMaxLevels];   // [N][N][N] bytes, finest first
+    int res[kMaxLevels];
+    int shift[kMaxLevels];              // log2(res[0] / res[l])
+    int n;
+};
+
+// Pinhole ray through the centre of pixel (i, j); cam = c2w[12], fx, fy, cx, cy.
+__device__ __forceinline__ void ray_f32(const float *cam, int i, int j, float o[3], float d[3])
+{
+    float u = F_ADD((float)i, 0.5f), v = F_ADD((float)j, 0.5f);
+    float xc = F_DIV(F_SUB(u, cam[14]), cam[12]);
+    float yc = F_DIV(F_SUB(v, cam[15]), cam[13]);
+    float w[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        w[r] = F_ADD(F_ADD(F_MUL(cam[4 * r + 0], xc), F_MUL(cam[4 * r + 1], yc)), cam[4 * r + 2]);
+        o[r] = cam[4 * r + 3];
+    }
+    float n2 = F_ADD(F_ADD(F_MUL(w[0], w[0]), F_MUL(w[1], w[1])), F_MUL(w[2], w[2]));
+    float n = F_SQRT(n2);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) d[r] = F_DIV(w[r], n);
+}
+
+// Region of a point: 0 inside |x|_inf <= 1, else 1 + 2 j + (x_j < 0), j the first axis of
+// largest magnitude.
+__device__ __forceinline__ int region_f32(const float x[3])
+{
+    int j = 0;
+    float ax = fabsf(x[0]);
+    if (fabsf(x[1]) > ax) { ax = fabsf(x[1]); j = 1; }
+    if (fabsf(x[2]) > ax) { ax = fabsf(x[2]); j = 2; }
+    if (ax <= 1.0f) return 0;
+    return 1 + 2 * j + (x[j] < 0.0f ? 1 : 0);
+}
+
+// One region's projective map (Sec. 3.2): x_k / |x_j| and (2 - 1/|x_j|) sign(x_j).
+__device__ __forceinline__ void contract_f32(int region, const float x[3], float p[3])
+{
+    if (region == 0) { p[0] = x[0]; p[1] = x[1]; p[2] = x[2]; return; }
+    int j = (region - 1) >> 1;
+    float ax = fabsf(x[j]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) p[k] = F_DIV(x[k], ax);
+    float q = F_SUB(2.0f, F_DIV(1.0f, ax));
+    p[j] = ((region - 1) & 1) ? -q : q;
+}
+
+__device__ __forceinline__ float lattice_s(int k, float step)
+{
+    return F_MUL(F_ADD((float)k, 0.5f), step);
+}
+
+__device__ __forceinline__ bool lattice_exists(int k, float step, float total)
+{
+    return F_MUL(F_ADD((float)k, 1.0f), step) < total;
+}
+
+// smallest k >= 0 with lattice_s(k) >= S
+__device__ __forceinline__ int first_k_at(float S, float step)
+{
+    float est = fmaxf(0.0f, fminf(ceilf(S / step - 0.5f), 16777216.0f));
+    int k = (int)est;
+    while (k > 0 && lattice_s(k - 1, step) >= S) --k;
+    while (k < (1 << 24) && lattice_s(k, step) < S) ++k;
+    return k;
+}
+
+// number of lattice samples: k exists iff ((float)k + 1) step < total
+__device__ __forceinline__ int lattice_count(float total, float step)
+{
+    float est = fmaxf(0.0f, fminf(floorf(total / step), 16777216.0f));
+    int n = (int)est;
+    while (n > 0 && !lattice_exists(n - 1, step, total)) --n;
+    while (n < (1 << 24) && lattice_exists(n, step, total)) ++n;
+    return n;
+}
+
+// Segment table of one ray: start point A, unit direction e, cumulative arc length S, and
+// the constants of the arc-length -> world-length map: the world length of arcs [u1, u2]
+// (relative to the segment start) is c (u2 - u1) / ((1 - g u1)(1 - g u2)).
+struct Segs {
+    float A[kMaxSegs][3];
+    float e[kMaxSegs][3];
+    float c[kMaxSegs];
+    float g[kMaxSegs];
+    float S[kMaxSegs + 1];
+    int n;
+};
+
+__device__ __forceinline__ void build_segments(const float o[3], const float d[3], Segs &sg)
+{
+    // region-boundary candidates: |x_a| = 1 and x_a = +-x_b
+    float cand[12];
+    int nc = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float t1 = F_DIV(F_SUB(1.0f, o[a]), d[a]);
+        float t2 = F_DIV(F_SUB(-1.0f, o[a]), d[a]);
+        if (t1 > 0.0f && t1 < CUDART_INF_F) cand[nc++] = t1;
+        if (t2 > 0.0f && t2 < CUDART_INF_F) cand[nc++] = t2;
+    }
+#pragma unroll
+    for (int pr = 0; pr < 3; ++pr) {
+        const int a = pr == 2 ? 1 : 0, b = pr == 0 ? 1 : 2;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            float num = F_SUB(s == 0 ? o[b] : -o[b], o[a]);
+            float den = F_SUB(d[a], s == 0 ? d[b] : -d[b]);
+            float t = F_DIV(num, den);
+            if (t > 0.0f && t < CUDART_INF_F) cand[nc++] = t;
+        }
+    }
+    for (int i = 1; i < nc; ++i) {
+        float v = cand[i];
+        int k = i - 1;
+        while (k >= 0 && cand[k] > v) { cand[k + 1] = cand[k]; --k; }
+        cand[k + 1] = v;
+    }
+    float bounds[14];
+    int nb = 0;
+    bounds[nb++] = 0.0f;
+    for (int i = 0; i < nc; ++i)
+        if (cand[i] > bounds[nb - 1]) bounds[nb++] = cand[i];
+    bounds[nb++] = CUDART_INF_F;
+
+    float ta[kMaxSegs], tb[kMaxSegs];
+    int reg[kMaxSegs];
+    int n = 0;
+    for (int m = 0; m + 1 < nb; ++m) {
+        float t0 = bounds[m], t1 = bounds[m + 1];
+        float tm = (t1 < CUDART_INF_F) ? F_MUL(F_ADD(t0, t1), 0.5f) : F_ADD(F_MUL(t0, 2.0f), 1.0f);
+        float x[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) x[k] = F_ADD(o[k], F_MUL(tm, d[k]));
+        int r = region_f32(x);
+        if (n > 0 && reg[n - 1] == r) { tb[n - 1] = t1; continue; }
+        reg[n] = r;
+        ta[n] = t0;
+        tb[n] = t1;
+        ++n;
+    }
+    sg.n = n;
+    sg.S[0] = 0.0f;
+    for (int i = 0; i < n; ++i) {
+        const int r = reg[i];
+        float xa[3], pa[3], pb[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) xa[k] = F_ADD(o[k], F_MUL(ta[i], d[k]));
+        contract_f32(r, xa, pa);
+        const int j = (r - 1) >> 1;
+        if (tb[i] < CUDART_INF_F) {
+            float xb[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) xb[k] = F_ADD(o[k], F_MUL(tb[i], d[k]));
+            contract_f32(r, xb, pb);
+        } else if (r == 0) {
+            // only reachable for a degenerate direction: an empty segment
+            pb[0] = pa[0]; pb[1] = pa[1]; pb[2] = pa[2];
+        } else {
+            // image of t -> infinity in region (j, s): p_j = 2 s, p_k = d_k / |d_j|
+            float adj = fabsf(d[j]);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) pb[k] = F_DIV(d[k], adj);
+            pb[j] = ((r - 1) & 1) ? -2.0f : 2.0f;
+        }
+        float ev[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) ev[k] = F_SUB(pb[k], pa[k]);
+        float l2 = F_ADD(F_ADD(F_MUL(ev[0], ev[0]), F_MUL(ev[1], ev[1])), F_MUL(ev[2], ev[2]));
+        float len = F_SQRT(l2);
+        if (!(len < CUDART_INF_F)) len = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            sg.A[i][k] = pa[k];
+            sg.e[i][k] = len > 0.0f ? F_DIV(ev[k], len) : 0.0f;
+        }
+        sg.S[i + 1] = F_ADD(sg.S[i], len);
+        // world-length constants (values, not decisions: ordinary float arithmetic)
+        if (r == 0) {
+            sg.c[i] = 1.0f;
+            sg.g[i] = 0.0f;
+        } else {
+            const float sgn = ((r - 1) & 1) ? -1.0f : 1.0f;
+            const float xj = o[j] + ta[i] * d[j];
+            const float w = 1.0f / fabsf(xj);           // 1 / |x_j| at the segment start
+            float v2 = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                // contracted velocity per unit t: w^2 d_j along j, w (d_k - s d_j p_k) otherwise
+                const float vk = (k == j) ? d[j] * w * w : w * (d[k] - sgn * d[j] * pa[k]);
+                v2 += vk * vk;
+            }
+            sg.c[i] = 1.0f / sqrtf(v2);
+            sg.g[i] = sgn * sg.e[i][j] / w;
+        }
+    }
+}
+
+// cell of a contracted coordinate at resolution N (N even): floor(p N/4) + N/2, clamped
+__device__ __forceinline__ int cell_of(float p, float scale, int half, int N)
+{
+    int c = (int)floorf(F_MUL(p, scale)) + half;
+    return min(max(c, 0), N - 1);
+}
+
+// Walk state of one ray.
+struct Walker {
+    Segs sg;
+    float A0, A1, A2, e0, e1, e2, S0, S1;  // current segment
+    int seg, kend, k, nlat;
+    float step, total;
+
+    __device__ __forceinline__ void load_seg(int i)
+    {
+        seg = i;
+        A0 = sg.A[i][0]; A1 = sg.A[i][1]; A2 = sg.A[i][2];
+        e0 = sg.e[i][0]; e1 = sg.e[i][1]; e2 = sg.e[i][2];
+        S0 = sg.S[i];
+        S1 = sg.S[i + 1];
+        kend = (i == sg.n - 1) ? 0x7fffffff : first_k_at(S1, step);
+    }
+
+    __device__ __forceinline__ void init(const float o[3], const float d[3], float step_)
+    {
+        step = step_;
+        build_segments(o, d, sg);
+        total = sg.S[sg.n];
+        nlat = lattice_count(total, step);
+        k = 0;
+        load_seg(0);
+    }
+
+    __device__ __forceinline__ void position(int kk, float &p0, float &p1, float &p2) const
+    {
+        const float u = F_SUB(lattice_s(kk, step), S0);
+        p0 = F_ADD(A0, F_MUL(u, e0));
+        p1 = F_ADD(A1, F_MUL(u, e1));
+        p2 = F_ADD(A2, F_MUL(u, e2));
+    }
+
+    // Advance k (>= current) to the next occupied lattice sample; false when the ray ends.
+    __device__ __forceinline__ bool next(const OccView &occ, float &p0, float &p1, float &p2)
+    {
+        const int N0 = occ.res[0];
+        const float sc0 = (float)N0 * 0.25f;
+        const int h0 = N0 >> 1;
+        while (k < nlat) {
+            while (k >= kend) load_seg(seg + 1);
+            position(k, p0, p1, p2);
+            const int c0 = cell_of(p0, sc0, h0, N0), c1 = cell_of(p1, sc0, h0, N0),
+                      c2 = cell_of(p2, sc0, h0, N0);
+            int lvl = -1;
+            for (int l = occ.n - 1; l >= 0; --l) {
+                const int sh = occ.shift[l], Nl = occ.res[l];
+                const int x = c0 >> sh, y = c1 >> sh, z = c2 >> sh;
+                if (__ldg(occ.level[l] + ((size_t)z * Nl + y) * Nl + x) == 0) { lvl = l; break; }
+            }
+            if (lvl < 0) return true;
+            // skip the empty level-`lvl` cell: exit of its box along the current segment
+            const int sh = occ.shift[lvl], Nl = occ.res[lvl];
+            const int x = c0 >> sh, y = c1 >> sh, z = c2 >> sh;
+            const float inv = 4.0f / (float)Nl;
+            const int hl = Nl >> 1;
+            const float lo0 = (float)(x - hl) * inv, lo1 = (float)(y - hl) * inv, lo2 = (float)(z - hl) * inv;
+            float umin = CUDART_INF_F;
+            if (e0 > 0.0f) umin = fminf(umin, (lo0 + inv - p0) / e0);
+            else if (e0 < 0.0f) umin = fminf(umin, (lo0 - p0) / e0);
+            if (e1 > 0.0f) umin = fminf(umin, (lo1 + inv - p1) / e1);
+            else if (e1 < 0.0f) umin = fminf(umin, (lo1 - p1) / e1);
+            if (e2 > 0.0f) umin = fminf(umin, (lo2 + inv - p2) / e2);
+            else if (e2 < 0.0f) umin = fminf(umin, (lo2 - p2) / e2);
+            const int last = min(kend, nlat) - 1;
+            int m = last;
+            const float s_exit = lattice_s(k, step) + umin;
+            if (s_exit < CUDART_INF_F) {
+                const float mf = ceilf(s_exit / step - 0.5f) - 1.0f;
+                m = (mf < (float)last) ? (int)fmaxf(mf, -1.0f) : last;
+            }
+            int nk = k + 1;
+            if (m > k) {
+                float q0, q1, q2;
+                position(m, q0, q1, q2);
+                if ((cell_of(q0, sc0, h0, N0) >> sh) == x && (cell_of(q1, sc0, h0, N0) >> sh) == y &&
+                    (cell_of(q2, sc0, h0, N0) >> sh) == z) {
+                    nk = m + 1;
+                } else if (m - 1 > k) {
+                    position(m - 1, q0, q1, q2);
+                    if ((cell_of(q0, sc0, h0, N0) >> sh) == x && (cell_of(q1, sc0, h0, N0) >> sh) == y &&
+                        (cell_of(q2, sc0, h0, N0) >> sh) == z)
+                        nk = m;
+                }
+            }
+            k = nk;
+        }
+        return false;
+    }
+
+    // World length of the lattice interval [k step, (k + 1) step] of sample k (Eq. 1's delta),
+    // summed over the segments it overlaps.
+    __device__ __forceinline__ float delta_world(int kk) const
+    {
+        const float lo = (float)kk * step, hi = ((float)kk + 1.0f) * step;
+        if (lo >= S0 && hi <= S1) {
+            const float c = sg.c[seg], g = sg.g[seg];
+            const float u1 = lo - S0, u2 = hi - S0;
+            return c * (hi - lo) / ((1.0f - g * u1) * (1.0f - g * u2));
+        }
+        int m = seg;
+        while (m > 0 && lo < sg.S[m]) --m;
+        float dw = 0.0f;
+        for (;;) {
+            const float a = fmaxf(lo, sg.S[m]), b = fminf(hi, sg.S[m + 1]);
+            if (b > a) {
+                const float c = sg.c[m], g = sg.g[m];
+                const float u1 = a - sg.S[m], u2 = b - sg.S[m];
+                dw += c * (b - a) / ((1.0f - g * u1) * (1.0f - g * u2));
+            }
+            if (hi <= sg.S[m + 1] || m >= sg.n - 1) break;
+            ++m;
+        }
+        return dw;
+    }
+};
+
+}  // namespace merf

@@ -1,0 +1,217 @@
+"""Python binding of the C-ABI renderer in libmerf.so (argument marshalling only).
+
+Every step of rendering runs in the library's CUDA kernels; this module turns numpy arrays
+and torch CUDA tensors into the plain pointers and structs of ``include/merf.h`` and turns
+status codes into exceptions.  PyTorch supplies device memory and the current stream.
+There is no CPU fallback: if the library cannot be built or loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+MERF_OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_DEVICE_BOUNDS, ERR_UNSUPPORTED = range(7)
+STORAGE_U8_SPARSE, STORAGE_F32_DENSE = 0, 1
+PREC_FP32, PREC_FP16, PREC_BF16 = 0, 1, 2
+MAX_OCC_LEVELS = 8
+AUX_SIZE = 12
+AUX_CD, AUX_F, AUX_T, AUX_NLAT, AUX_NEVAL, AUX_NAPP, AUX_TERM = 0, 3, 7, 8, 9, 10, 11
+CNT_RAYS, CNT_LATTICE, CNT_EVAL, CNT_APPEAR = 0, 1, 2, 3
+
+EXPORTS = ("merf_scene_upload", "merf_scene_upload_dense", "merf_scene_free", "merf_scene_device_bytes",
+           "merf_render", "merf_render_aux", "merf_render_host", "merf_trace", "merf_set_device_budget",
+           "merf_last_error", "merf_version")
+
+
+class MerfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"merf status {status}: {msg}")
+        self.status = status
+
+
+class Desc(ct.Structure):
+    _fields_ = [("grid_res", ct.c_int32), ("block_size", ct.c_int32), ("plane_res", ct.c_int32),
+                ("channels", ct.c_int32), ("n_blocks", ct.c_int32), ("n_occ_levels", ct.c_int32),
+                ("occ_res", ct.c_int32 * MAX_OCC_LEVELS), ("mlp_in", ct.c_int32), ("mlp_hidden", ct.c_int32),
+                ("mlp_out", ct.c_int32), ("storage", ct.c_int32)]
+
+
+class Opts(ct.Structure):
+    _fields_ = [("step", ct.c_float), ("t_term", ct.c_float), ("precision", ct.c_int32),
+                ("early_term", ct.c_int32), ("reserved", ct.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libmerf.so, building it in-tree with nvcc first if it is missing or stale."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ct.CDLL(path)
+        vp, i32 = ct.c_void_p, ct.c_int
+        L.merf_scene_upload.argtypes = [ct.POINTER(Desc), vp, vp, vp, vp, vp, vp, ct.POINTER(vp)]
+        L.merf_scene_upload_dense.argtypes = [ct.POINTER(Desc), vp, vp, vp, vp, vp, ct.POINTER(vp)]
+        L.merf_scene_free.argtypes = [vp]
+        L.merf_scene_free.restype = None
+        L.merf_scene_device_bytes.argtypes = [vp]
+        L.merf_scene_device_bytes.restype = ct.c_size_t
+        L.merf_render.argtypes = [vp, vp, i32, i32, i32, vp, ct.POINTER(Opts), vp]
+        L.merf_render_aux.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, ct.POINTER(Opts), vp]
+        L.merf_render_host.argtypes = [vp, vp, i32, i32, i32, vp, vp, ct.POINTER(Opts), vp]
+        L.merf_trace.argtypes = [vp, vp, i32, i32, i32, vp, i32, vp, ct.POINTER(Opts), vp]
+        L.merf_set_device_budget.argtypes = [ct.c_size_t]
+        L.merf_set_device_budget.restype = None
+        L.merf_last_error.restype = ct.c_char_p
+        L.merf_version.restype = ct.c_char_p
+        for name in ("merf_scene_upload", "merf_scene_upload_dense", "merf_render", "merf_render_aux",
+                     "merf_render_host", "merf_trace"):
+            getattr(L, name).restype = ct.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != MERF_OK:
+        raise MerfError(status, lib().merf_last_error().decode())
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _np_ptr(a: np.ndarray):
+    return a.ctypes.data_as(ct.c_void_p)
+
+
+def _dev_ptr(t: torch.Tensor, dtype, numel: int, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() != numel:
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor of {numel} elements")
+    return ct.c_void_p(t.data_ptr())
+
+
+def opts(step: float, t_term: float = 2e-4, early_term: bool = True, precision: int = PREC_FP32) -> Opts:
+    return Opts(step=step, t_term=t_term, precision=precision, early_term=int(early_term), reserved=0)
+
+
+def cameras(cams: np.ndarray) -> np.ndarray:
+    cams = np.ascontiguousarray(cams, dtype=np.float32).reshape(-1, 16)
+    return cams
+
+
+class Scene:
+    """A baked scene resident on the current CUDA device (owns device memory)."""
+
+    def __init__(self, scene, stream=None):
+        cfg = scene.cfg
+        d = Desc()
+        d.grid_res, d.plane_res, d.channels = cfg.L, cfg.R, 8
+        d.n_occ_levels = len(scene.occ)
+        for i, o in enumerate(scene.occ):
+            d.occ_res[i] = o.shape[0]
+        d.mlp_in, d.mlp_hidden, d.mlp_out = 34, 16, 3
+        self._occ = [np.ascontiguousarray(o, dtype=np.uint8) for o in scene.occ]
+        occ_ptrs = (ct.c_void_p * MAX_OCC_LEVELS)(*[o.ctypes.data for o in self._occ])
+        mlp = np.ascontiguousarray(scene.mlp, dtype=np.float32)
+        handle = ct.c_void_p()
+        s = _stream(stream)
+        if cfg.storage == "u8":
+            d.storage = STORAGE_U8_SPARSE
+            d.block_size, d.n_blocks = cfg.B, scene.n_blocks
+            ig = np.ascontiguousarray(scene.index_grid, dtype=np.int32)
+            atlas = np.ascontiguousarray(scene.atlas, dtype=np.uint8)
+            planes = np.ascontiguousarray(scene.planes, dtype=np.uint8)
+            _check(lib().merf_scene_upload(ct.byref(d), _np_ptr(ig), _np_ptr(atlas), _np_ptr(planes),
+                                           ct.cast(occ_ptrs, ct.c_void_p), _np_ptr(mlp), s, ct.byref(handle)))
+        else:
+            d.storage = STORAGE_F32_DENSE
+            grid = np.ascontiguousarray(scene.grid_f32, dtype=np.float32)
+            planes = np.ascontiguousarray(scene.planes_f32, dtype=np.float32)
+            _check(lib().merf_scene_upload_dense(ct.byref(d), _np_ptr(grid), _np_ptr(planes),
+                                                 ct.cast(occ_ptrs, ct.c_void_p), _np_ptr(mlp), s,
+                                                 ct.byref(handle)))
+        self.handle = handle
+        self.desc = d
+        self.source = scene
+
+    @property
+    def device_bytes(self) -> int:
+        return int(lib().merf_scene_device_bytes(self.handle))
+
+    def close(self):
+        if self.handle:
+            lib().merf_scene_free(self.handle)
+            self.handle = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def render(scene: Scene, cams: np.ndarray, W: int, H: int, step: float, out: Optional[torch.Tensor] = None,
+           t_term: float = 2e-4, early_term: bool = True, precision: int = PREC_FP32,
+           aux: Optional[torch.Tensor] = None, counters: Optional[torch.Tensor] = None,
+           stream=None) -> torch.Tensor:
+    """Render n cameras into a CUDA float32 tensor [n, H, W, 3]."""
+    cams = cameras(cams)
+    n = cams.shape[0]
+    if out is None:
+        out = torch.empty((n, H, W, 3), dtype=torch.float32, device="cuda")
+    o = opts(step, t_term, early_term, precision)
+    op = _dev_ptr(out, torch.float32, n * H * W * 3, "out")
+    ap = _dev_ptr(aux, torch.float32, n * H * W * AUX_SIZE, "aux") if aux is not None else None
+    cp = _dev_ptr(counters, torch.int64, 4, "counters") if counters is not None else None
+    if ap is None and cp is None:
+        _check(lib().merf_render(scene.handle, _np_ptr(cams), n, W, H, op, ct.byref(o), _stream(stream)))
+    else:
+        _check(lib().merf_render_aux(scene.handle, _np_ptr(cams), n, W, H, op, ap, cp, ct.byref(o),
+                                     _stream(stream)))
+    return out
+
+
+def render_host(scene: Scene, cams: np.ndarray, W: int, H: int, step: float, staging: torch.Tensor,
+                host_out: torch.Tensor, t_term: float = 2e-4, early_term: bool = True,
+                precision: int = PREC_FP32, stream=None) -> torch.Tensor:
+    """Render into host memory through the library's host-output entry point."""
+    cams = cameras(cams)
+    n = cams.shape[0]
+    if host_out.is_cuda or host_out.dtype != torch.float32 or not host_out.is_contiguous() or \
+            host_out.numel() != n * H * W * 3:
+        raise ValueError("host_out must be a contiguous host float32 tensor [n, H, W, 3]")
+    o = opts(step, t_term, early_term, precision)
+    _check(lib().merf_render_host(scene.handle, _np_ptr(cams), n, W, H,
+                                  _dev_ptr(staging, torch.float32, n * H * W * 3, "staging"),
+                                  ct.c_void_p(host_out.data_ptr()), ct.byref(o), _stream(stream)))
+    return host_out
+
+
+def trace(scene: Scene, cams: np.ndarray, W: int, H: int, step: float, words: int, stream=None):
+    """Evaluated lattice-sample bit masks [n*H*W, words] (uint32 as int32) and lattice counts."""
+    cams = cameras(cams)
+    n = cams.shape[0]
+    mask = torch.empty((n * H * W, words), dtype=torch.int32, device="cuda")
+    nlat = torch.empty((n * H * W,), dtype=torch.int32, device="cuda")
+    o = opts(step, early_term=False)
+    _check(lib().merf_trace(scene.handle, _np_ptr(cams), n, W, H, ct.c_void_p(mask.data_ptr()), words,
+                            ct.c_void_p(nlat.data_ptr()), ct.byref(o), _stream(stream)))
+    return mask, nlat
+
+
+def set_device_budget(nbytes: int):
+    lib().merf_set_device_budget(int(nbytes))
+
+
+def version() -> str:
+    return lib().merf_version().decode()

@@ -1,0 +1,129 @@
+"""The C-ABI library builds, loads and exports every entry point of include/merf.h; host-side
+argument checks reject bad input before touching a device -- CPU only (no compute calls)."""
+import ctypes as ct
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2302_12249_b300 import merf, synth
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "merf.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(merf_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declarations_are_exported():
+    L = merf.lib()
+    names = _declared()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(L, name), name
+    assert set(names) == set(merf.EXPORTS)
+
+
+def test_version_string():
+    assert "sm_103a" in merf.version()
+
+
+def _desc(**kw):
+    d = merf.Desc()
+    d.grid_res, d.block_size, d.plane_res, d.channels, d.n_blocks = 16, 4, 32, 8, 0
+    d.n_occ_levels = 1
+    d.occ_res[0] = 16
+    d.mlp_in, d.mlp_hidden, d.mlp_out = 34, 16, 3
+    d.storage = 0
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d
+
+
+def _upload(d, ig=None, occ=None, mlp=None):
+    L = merf.lib()
+    nb = max(1, d.grid_res // max(1, d.block_size))
+    ig = np.full(nb ** 3, -1, np.int32) if ig is None else ig
+    planes = np.zeros(3 * d.plane_res * d.plane_res * 8, np.uint8)
+    occ = [np.ones((d.occ_res[0],) * 3, np.uint8)] if occ is None else occ
+    ptrs = (ct.c_void_p * 8)(*[o.ctypes.data for o in occ])
+    mlp = np.zeros(883, np.float32) if mlp is None else mlp
+    h = ct.c_void_p()
+    st = L.merf_scene_upload(ct.byref(d), ig.ctypes.data, None, planes.ctypes.data, ct.cast(ptrs, ct.c_void_p),
+                             mlp.ctypes.data, None, ct.byref(h))
+    return st, L.merf_last_error().decode()
+
+
+@pytest.mark.parametrize("field,value", [("channels", 4), ("grid_res", 15), ("block_size", 3),
+                                         ("plane_res", 7), ("n_occ_levels", 0), ("n_occ_levels", 9),
+                                         ("storage", 1), ("n_blocks", -1)])
+def test_upload_rejects_bad_desc(field, value):
+    st, msg = _upload(_desc(**{field: value}))
+    assert st == merf.ERR_INVALID_ARG and msg
+
+
+def test_upload_rejects_unsupported_mlp():
+    st, _ = _upload(_desc(mlp_hidden=32))
+    assert st == merf.ERR_UNSUPPORTED
+
+
+def test_upload_rejects_block_id_out_of_range():
+    ig = np.full(64, -1, np.int32)
+    ig[5] = 3                      # n_blocks = 0
+    st, msg = _upload(_desc(), ig=ig)
+    assert st == merf.ERR_INVALID_ARG and "index_grid" in msg
+
+
+def test_upload_rejects_inconsistent_occupancy():
+    d = _desc(n_occ_levels=2)
+    d.occ_res[1] = 4
+    fine = np.zeros((16, 16, 16), np.uint8)
+    fine[3, 9, 12] = 1
+    coarse = np.zeros((4, 4, 4), np.uint8)          # not a max-pool of `fine`
+    st, msg = _upload(d, occ=[fine, coarse])
+    assert st == merf.ERR_INVALID_ARG and "occupancy" in msg
+
+
+def test_upload_rejects_non_finite_weights():
+    mlp = np.zeros(883, np.float32)
+    mlp[100] = np.nan
+    st, _ = _upload(_desc(), mlp=mlp)
+    assert st == merf.ERR_INVALID_ARG
+
+
+def test_device_budget_refuses_before_allocating():
+    merf.set_device_budget(1000)
+    try:
+        st, msg = _upload(_desc())
+        assert st == merf.ERR_OOM and "budget" in msg
+    finally:
+        merf.set_device_budget(0)
+
+
+def test_render_rejects_null_and_bad_sizes():
+    L = merf.lib()
+    o = merf.opts(1 / 64)
+    cams = synth.config_cameras("tiny")
+    assert L.merf_render(None, cams.ctypes.data, 1, 4, 4, None, ct.byref(o), None) == merf.ERR_INVALID_ARG
+    fake = ct.c_void_p(1)          # never dereferenced: the size checks fail first
+    assert L.merf_render(fake, cams.ctypes.data, 0, 4, 4, None, ct.byref(o), None) == merf.ERR_INVALID_ARG
+    assert L.merf_render(fake, cams.ctypes.data, 1, 0, 4, None, ct.byref(o), None) == merf.ERR_INVALID_ARG
+    assert L.merf_render(fake, None, 1, 4, 4, None, ct.byref(o), None) == merf.ERR_INVALID_ARG
+    bad = cams.copy()
+    bad[0, 12] = 0.0               # fx = 0
+    assert L.merf_render(fake, bad.ctypes.data, 1, 4, 4, None, ct.byref(o), None) == merf.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("kw", [dict(step=0.0), dict(step=float("nan")), dict(t_term=1.5),
+                                dict(early_term=2), dict(reserved=1)])
+def test_render_rejects_bad_opts(kw):
+    L = merf.lib()
+    o = merf.opts(1 / 64)
+    for k, v in kw.items():
+        setattr(o, k, v)
+    cams = synth.config_cameras("tiny")
+    fake = ct.c_void_p(1)
+    out = ct.c_void_p(1)
+    assert L.merf_render(fake, cams.ctypes.data, 1, 4, 4, out, ct.byref(o), None) == merf.ERR_INVALID_ARG

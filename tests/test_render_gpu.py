@@ -1,0 +1,201 @@
+"""GPU parity of the FP32 render path against the FP64 oracle, through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2302_12249_b300 import merf, synth
+from tests import parity, scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tiny(tiny_scene):
+    return merf.Scene(tiny_scene), oracle.OracleScene(tiny_scene)
+
+
+@pytest.fixture(scope="module")
+def paper_scene():
+    return synth.make_scene("paper")
+
+
+@pytest.fixture(scope="module")
+def paper(paper_scene):
+    return merf.Scene(paper_scene), oracle.OracleScene(paper_scene)
+
+
+def _words(nlat):
+    return int(math.ceil(max(1, int(nlat.max())) / 32))
+
+
+def test_tiny_full_image_parity(tiny):
+    """Config: 64^3 grid in 8^3 blocks, 256^2 planes, 64x64 pixels, fov 60, radius 3, step 1/64."""
+    gs, osc = tiny
+    cams = synth.config_cameras("tiny")
+    rgb, aux = parity.gpu_render(gs, cams, 64, 64, 1 / 64)
+    lo, hi = parity.oracle_rgb(osc, cams, 64, 64, 1 / 64)
+    err = parity.max_err(rgb, lo, hi)
+    assert err.max() <= parity.RGB_TOL, err.max()
+    np.testing.assert_array_equal(aux[:, merf.AUX_NLAT], lo[:, oracle.ORC_NLAT])
+    assert (aux[:, merf.AUX_NEVAL] > 0).mean() > 0.2
+
+
+@pytest.mark.parametrize("W,H", [(1, 1), (17, 9), (33, 70), (250, 131)])
+def test_tiny_ragged_sizes(tiny, W, H):
+    gs, osc = tiny
+    cams = synth.config_cameras("tiny", W=W, H=H, n=2)
+    rgb, _ = parity.gpu_render(gs, cams, W, H, 1 / 64)
+    lo, hi = parity.oracle_rgb(osc, cams, W, H, 1 / 64)
+    assert parity.max_err(rgb, lo, hi).max() <= parity.RGB_TOL
+
+
+def test_tiny_without_termination(tiny):
+    gs, osc = tiny
+    cams = synth.config_cameras("tiny", W=48, H=40)
+    rgb, aux = parity.gpu_render(gs, cams, 48, 40, 1 / 64, early_term=False)
+    lo, _ = parity.oracle_rgb(osc, cams, 48, 40, 1 / 64, early_term=False)
+    assert np.abs(rgb - lo[:, 0:3]).max() <= parity.RGB_TOL
+    np.testing.assert_array_equal(aux[:, merf.AUX_NEVAL], lo[:, oracle.ORC_NEVAL])
+    np.testing.assert_allclose(aux[:, merf.AUX_T], lo[:, oracle.ORC_T], atol=1e-5)
+
+
+def test_tiny_traversal_bit_exact(tiny):
+    """Evaluated lattice samples identical to the FP32 restatement of dense sampling."""
+    gs, osc = tiny
+    cams = synth.config_cameras("tiny", W=64, H=64, n=3)
+    mask, nlat = merf.trace(gs, cams, 64, 64, 1 / 64, words=16)
+    m_o, _, n_o = oracle.trace(osc, cams, 64, 64, 1 / 64, words=16, decide_f32=True)
+    np.testing.assert_array_equal(nlat.cpu().numpy(), n_o)
+    np.testing.assert_array_equal(mask.cpu().numpy().view(np.uint32), m_o)
+
+
+def test_many_cameras_chunked_launches(tiny):
+    """More cameras than one launch carries (32)."""
+    gs, osc = tiny
+    cams = synth.sphere_cameras(37, 8, 6, radius=2.5, seed=11)
+    rgb, _ = parity.gpu_render(gs, cams, 8, 6, 1 / 64)
+    lo, hi = parity.oracle_rgb(osc, cams, 8, 6, 1 / 64)
+    assert parity.max_err(rgb, lo, hi).max() <= parity.RGB_TOL
+
+
+def test_camera_inside_unit_cube_and_axis_aligned(tiny):
+    """Rays starting inside the cube, and rays along the axes and diagonals (region ties)."""
+    gs, osc = tiny
+    recs = []
+    for eye, tgt in [((0.1, 0.2, -0.3), (1, 0.2, -0.3)), ((0, 0, 0), (0, 0, 1)), ((0, 0, 0), (1, 1, 0)),
+                     ((0.5, 0.5, 0.5), (2, 2, 2)), ((-3, 0, 0), (0, 0, 0))]:
+        up = (0, 0, 1) if abs(np.subtract(tgt, eye)[2]) < 0.9 * np.linalg.norm(np.subtract(tgt, eye)) else (1, 0, 0)
+        recs.append(synth.camera_record(synth.look_at(eye, tgt, up), 21, 21))
+    cams = np.stack(recs)
+    rgb, _ = parity.gpu_render(gs, cams, 21, 21, 1 / 64)
+    lo, hi = parity.oracle_rgb(osc, cams, 21, 21, 1 / 64)
+    assert parity.max_err(rgb, lo, hi).max() <= parity.RGB_TOL
+    mask, nlat = merf.trace(gs, cams, 21, 21, 1 / 64, words=24)
+    m_o, _, n_o = oracle.trace(osc, cams, 21, 21, 1 / 64, words=24, decide_f32=True)
+    np.testing.assert_array_equal(mask.cpu().numpy().view(np.uint32), m_o)
+
+
+def test_empty_and_full_occupancy():
+    """No occupied cell: C = h(0, 0, d).  Every cell occupied: nothing is skipped."""
+    for occ_val in (0, 1):
+        sc = scenes.const_scene(L=16, B=4, R=32, occ_N=16, dens_byte=110, app_byte=90,
+                                occ=np.full((16, 16, 16), occ_val, np.uint8), mlp=synth._mlp_weights(5))
+        gs, osc = merf.Scene(sc), oracle.OracleScene(sc)
+        cams = synth.sphere_cameras(2, 19, 11, radius=1.7, seed=3)
+        rgb, aux = parity.gpu_render(gs, cams, 19, 11, 1 / 64)
+        lo, hi = parity.oracle_rgb(osc, cams, 19, 11, 1 / 64)
+        assert parity.max_err(rgb, lo, hi).max() <= parity.RGB_TOL
+        if occ_val == 0:
+            assert aux[:, merf.AUX_NEVAL].max() == 0
+
+
+def test_missing_blocks_contribute_nothing():
+    """A scene whose index grid drops occupied blocks: missing voxels add zero (both sides)."""
+    rng = np.random.default_rng(9)
+    sc = scenes.const_scene(L=16, B=4, R=32, occ_N=16, mlp=synth._mlp_weights(6))
+    sc.atlas[...] = rng.integers(60, 200, size=sc.atlas.shape, dtype=np.uint8)
+    sc.planes[...] = rng.integers(60, 200, size=sc.planes.shape, dtype=np.uint8)
+    ig = sc.index_grid
+    ig[rng.uniform(size=ig.shape) < 0.3] = -1
+    gs, osc = merf.Scene(sc), oracle.OracleScene(sc)
+    cams = synth.sphere_cameras(2, 32, 24, radius=2.2, seed=4)
+    rgb, _ = parity.gpu_render(gs, cams, 32, 24, 1 / 64)
+    lo, hi = parity.oracle_rgb(osc, cams, 32, 24, 1 / 64)
+    assert parity.max_err(rgb, lo, hi).max() <= parity.RGB_TOL
+
+
+def test_deterministic(tiny):
+    gs, _ = tiny
+    cams = synth.config_cameras("tiny")
+    a = merf.render(gs, cams, 64, 64, 1 / 64)
+    b = merf.render(gs, cams, 64, 64, 1 / 64)
+    assert torch.equal(a, b)
+
+
+def test_render_host_matches_device(tiny):
+    gs, _ = tiny
+    cams = synth.config_cameras("tiny")
+    dev = merf.render(gs, cams, 64, 64, 1 / 64)
+    staging = torch.empty_like(dev)
+    host = torch.empty(dev.shape, dtype=torch.float32, pin_memory=True)
+    merf.render_host(gs, cams, 64, 64, 1 / 64, staging, host)
+    assert torch.equal(host, dev.cpu())
+
+
+def test_counters_match_aux(tiny):
+    gs, _ = tiny
+    cams = synth.config_cameras("tiny")
+    aux = torch.zeros((1, 64, 64, merf.AUX_SIZE), device="cuda")
+    cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+    merf.render(gs, cams, 64, 64, 1 / 64, aux=aux, counters=cnt)
+    a = aux.reshape(-1, merf.AUX_SIZE).double()
+    c = cnt.cpu().tolist()
+    assert c[merf.CNT_RAYS] == 64 * 64
+    assert c[merf.CNT_LATTICE] == int(a[:, merf.AUX_NLAT].sum())
+    assert c[merf.CNT_EVAL] == int(a[:, merf.AUX_NEVAL].sum())
+    assert c[merf.CNT_APPEAR] == int(a[:, merf.AUX_NAPP].sum())
+
+
+def test_dense_float_storage():
+    """Dense float32 grid 128^3 and planes 512^2 (the differentiable variant's storage)."""
+    sc = synth.make_scene("dense128")
+    gs, osc = merf.Scene(sc), oracle.OracleScene(sc)
+    cams = synth.config_cameras("dense128", W=64, H=48, n=2)
+    rgb, _ = parity.gpu_render(gs, cams, 64, 48, sc.cfg.step)
+    lo, hi = parity.oracle_rgb(osc, cams, 64, 48, sc.cfg.step)
+    assert parity.max_err(rgb, lo, hi).max() <= parity.RGB_TOL
+
+
+# ---------------------------------------------------------------------------------------------
+# paper-scale scene (L = 512 in 16^3 blocks, R = 2048, four occupancy levels), 1920 x 1080,
+# in the launch configuration the benchmark times; sampled pixels are checked one by one.
+
+def test_paper_scale_sampled_pixels(paper):
+    gs, osc = paper
+    cams = synth.config_cameras("paper")                    # 8 cameras, 1920 x 1080
+    W, H, step = 1920, 1080, 1 / 256
+    out = merf.render(gs, cams, W, H, step)
+    aux = torch.zeros((cams.shape[0], H, W, merf.AUX_SIZE), device="cuda")
+    out2 = merf.render(gs, cams, W, H, step, aux=aux)
+    torch.cuda.synchronize()
+    assert torch.equal(out, out2)
+    pix, lin = parity.pick_pixels(cams.shape[0], W, H, 3000, seed=0)
+    rgb = out.reshape(-1, 3)[torch.from_numpy(lin).cuda()].double().cpu().numpy()
+    lo, hi = parity.oracle_rgb(osc, cams, W, H, step, pix=pix)
+    err = parity.max_err(rgb, lo, hi)
+    assert err.max() <= parity.RGB_TOL, (err.max(), np.argmax(err))
+    a = aux.reshape(-1, merf.AUX_SIZE)[torch.from_numpy(lin).cuda()].double().cpu().numpy()
+    np.testing.assert_array_equal(a[:, merf.AUX_NLAT], lo[:, oracle.ORC_NLAT])
+    assert np.isfinite(out.cpu().numpy()).all()
+
+
+def test_paper_scale_traversal_bit_exact(paper):
+    gs, osc = paper
+    cams = synth.config_cameras("paper", W=480, H=270, n=2)
+    mask, nlat = merf.trace(gs, cams, 480, 270, 1 / 256, words=64)
+    m_o, _, n_o = oracle.trace(osc, cams, 480, 270, 1 / 256, words=64, decide_f32=True)
+    np.testing.assert_array_equal(nlat.cpu().numpy(), n_o)
+    np.testing.assert_array_equal(mask.cpu().numpy().view(np.uint32), m_o)
