@@ -1,0 +1,283 @@
+#!/usr/bin/env python3
+"""Benchmark: MERF baked-scene rendering on B300 (Mrays/s and 1080p frames/s vs the
+feature-gather bandwidth roofline).
+
+One step renders 8 cameras at 1920 x 1080 (16.6 M pixel rays) of the paper-scale synthetic
+scene: 512^3 grid in 16^3 blocks, three 2048^2 planes, occupancy 128^3..16^3, step 1/256,
+cameras on a ring of radius 1.5.  Inputs are resident in HBM before timing; the scene
+(~620 MB) and each step's output (199 MB) exceed the 126 MB L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  `--impl reference` times the FP64 CPU oracle on host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mrays/s and 1080p frames/s vs gather-BW roofline; FP16 vs FP32 at PSNR>50 dB; p99 ms"
+UNIT = "Mrays/s"
+W_IMG, H_IMG, N_CAMS, STEP = 1920, 1080, 8, 1.0 / 256
+WORKLOAD = ("paper-scale synthetic MERF scene (L=512 in 16^3 blocks, R=2048, uint8, occupancy "
+            "128/64/32/16), 8 ring cameras (radius 1.5) at 1920x1080, lattice step 1/256, FP32 path")
+# algorithmic gather bytes (no reuse): per evaluated sample 8 grid corners + 12 plane texels of
+# the density byte (20 B) and one 4-byte index-grid entry; per sample with non-zero opacity the
+# 7 appearance bytes of the same 20 texels (140 B); per ray the 12-byte RGB output.
+B_DENSITY, B_INDEX, B_APPEAR, B_OUT = 20, 4, 140, 12
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.proc, self.path = index, None, None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 7:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    n = int(os.environ.get("WORLD_SIZE", "1"))
+    if n > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group("nccl")
+        return dist, int(os.environ["RANK"]), n, int(os.environ.get("LOCAL_RANK", "0"))
+    return None, 0, 1, 0
+
+
+def _cpu_baseline(scene, cams, seconds: float = 12.0):
+    """The FP64 oracle on the host cores, on random pixels of the same frames, for ~`seconds`."""
+    import oracle
+    osc = oracle.OracleScene(scene)
+    threads = oracle.default_threads()
+    rng = np.random.default_rng(12345)
+    rays, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        n = 2048
+        pix = np.stack([rng.integers(0, N_CAMS, n), rng.integers(0, W_IMG, n), rng.integers(0, H_IMG, n)], 1)
+        oracle.render(osc, cams, W_IMG, H_IMG, STEP, pix=pix.astype(np.int32), threads=threads)
+        rays += n
+    dt = time.perf_counter() - t0
+    return {"value": rays / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{rays} random pixel rays of the 8 x 1920x1080 frames ({dt:.1f} s, FP64, {threads} threads)"}
+
+
+def run_reference(args):
+    dist, rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    from paper_2302_12249_b300 import synth
+    import oracle
+    scene = synth.make_scene("paper")
+    cams = synth.config_cameras("paper")
+    osc = oracle.OracleScene(scene)
+    threads = oracle.default_threads()
+    rng = np.random.default_rng(777)
+    per_step = 4096
+    samples = [np.stack([rng.integers(0, N_CAMS, per_step), rng.integers(0, W_IMG, per_step),
+                         rng.integers(0, H_IMG, per_step)], 1).astype(np.int32)
+               for _ in range(args.warmup + args.steps)]
+    for s in range(args.warmup):
+        oracle.render(osc, cams, W_IMG, H_IMG, STEP, pix=samples[s], threads=threads)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        oracle.render(osc, cams, W_IMG, H_IMG, STEP, pix=samples[args.warmup + s], threads=threads)
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt / 1e6
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD + "; each step renders 4096 random pixel rays of it",
+                       "parallelism": "host threads"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{per_step} random pixel rays per step, FP64 oracle, {threads} threads"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    dist, rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    from paper_2302_12249_b300 import merf, synth
+    scene = synth.make_scene("paper")
+    cams = synth.config_cameras("paper")
+    gs = merf.Scene(scene)
+    cams = cams[:args.cams]
+    n_cams = cams.shape[0]
+    rays_per_step = n_cams * W_IMG * H_IMG
+    out = torch.empty((n_cams, H_IMG, W_IMG, 3), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    # untimed pass with counters: units of work per launch for the algorithmic byte count
+    cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+    aux = torch.empty((n_cams, H_IMG, W_IMG, merf.AUX_SIZE), dtype=torch.float32, device="cuda")
+    merf.render(gs, cams, W_IMG, H_IMG, STEP, out=out, aux=aux, counters=cnt)
+    torch.cuda.synchronize()
+    c = [int(v) for v in cnt.cpu().tolist()]
+    del aux
+    alg_bytes = (c[merf.CNT_EVAL] * (B_DENSITY + B_INDEX) + c[merf.CNT_APPEAR] * B_APPEAR +
+                 c[merf.CNT_RAYS] * B_OUT)
+
+    for _ in range(args.warmup):
+        merf.render(gs, cams, W_IMG, H_IMG, STEP, out=out)
+    torch.cuda.synchronize()
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for s in range(args.steps):
+        ev[s][0].record(stream)
+        merf.render(gs, cams, W_IMG, H_IMG, STEP, out=out)
+        ev[s][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    kern_ms = [a.elapsed_time(b) for a, b in ev]
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = rays_per_step * world * args.steps / (total_ms / 1e3) / 1e6
+    mean_kern_ms = sum(kern_ms) / len(kern_ms)
+    peak, peak_src = _peaks()
+    achieved = alg_bytes / (mean_kern_ms / 1e3) / 1e9
+
+    # end to end through the host-output entry point: camera records in, RGB frames out
+    e2e = None
+    if not args.no_e2e:
+        staging = torch.empty_like(out)
+        host = torch.empty(out.shape, dtype=torch.float32, pin_memory=True)
+        merf.render_host(gs, cams, W_IMG, H_IMG, STEP, staging, host)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            merf.render_host(gs, cams, W_IMG, H_IMG, STEP, staging, host)
+        e2e_s = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": rays_per_step * world * args.steps / e2e_s / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": n_cams * 64, "d2h_bytes_per_step": int(out.numel() * 4)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = _cpu_baseline(scene, cams)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "rays_per_step_per_gpu": rays_per_step,
+                           "scene_device_mb": round(gs.device_bytes / 1e6, 1),
+                           "block_fraction": round(scene.stats["block_fraction"], 4),
+                           "l2": "inputs larger than L2 (scene and per-step output each exceed 126 MB); no flush",
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                "frames_per_s_1080p": value * 1e6 / (W_IMG * H_IMG),
+                "work": {"lattice_per_ray": c[merf.CNT_LATTICE] / c[merf.CNT_RAYS],
+                         "evaluated_per_ray": c[merf.CNT_EVAL] / c[merf.CNT_RAYS],
+                         "appearance_per_ray": c[merf.CNT_APPEAR] / c[merf.CNT_RAYS],
+                         "algorithmic_bytes_per_ray": alg_bytes / c[merf.CNT_RAYS]},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": None,
+                             "kernel": "render_kernel<0>", "kernel_ms": mean_kern_ms,
+                             "peak_source": peak_src},
+                "gpu_launches": args.steps,
+                "e2e": e2e, "clocks": ck}
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cams", type=int, default=N_CAMS, help="cameras per step (profiling cases)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-output measurement (profiling)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
