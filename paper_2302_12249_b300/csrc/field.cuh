@@ -9,10 +9,16 @@
 // with W_V the weight of the 3D-grid corners that are stored (a voxel of a block that is not
 // stored contributes nothing).
 //
-// Layout in HBM: every texel is 8 bytes (one uint2: channels 0..3 in .x, 4..7 in .y), so
-// one 64-bit load fetches density and appearance of a corner.  The 3D grid is block-sparse:
-// an int32 index grid over (L/B)^3 blocks points into an atlas of B^3-voxel blocks laid out
-// [z][y][x].
+// Layout in HBM.  Every texel is 8 bytes (one uint2: channels 0..3 in .x, 4..7 in .y), so a
+// single 64-bit load fetches density and appearance of a corner.  The 3D grid is
+// block-sparse: an int32 index grid over (L/B)^3 blocks holds, for a stored block, its atlas
+// slot in bits 0..23 and in bits 24..30 a mask of which of its +x/+y/+z neighbour blocks are
+// not stored (neighbour dx + 2 dy + 4 dz in 1..7 at bit 23 + that number); -1 marks a block
+// that is not stored.  Each atlas slot holds (B+1)^3 voxels [z][y][x]: the block plus a
+// one-voxel apron copied from its +x/+y/+z neighbours, so the eight corners of any sample
+// whose lowest corner lies in the block are one base address plus constant offsets.
+// Clamp-to-edge is folded into the integer coordinate and weight (lowest corner kept in
+// [0, N-2]), so no lookup leaves the array.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -21,115 +27,167 @@
 namespace merf {
 
 struct FieldView {
-    const int32_t *index_grid;   // [(L/B)^3]
-    const uint2 *atlas;          // [n_blocks][B][B][B]
+    const int32_t *index_grid;   // [(L/B)^3] slot | missing-neighbour mask << 24, or -1
+    const uint2 *atlas;          // [n_blocks][B+1][B+1][B+1]
     const uint2 *planes;         // [3][R][R]
     const float4 *grid_f32;      // dense storage: [L][L][L][2]
     const float4 *planes_f32;    // dense storage: [3][R][R][2]
     int L, B, log2B, nb, R;
 };
 
-// Continuous texel index u = (p + 2) N / 4 - 1/2 split into an integer part and a fraction
-// without rounding: p * N/4 is exact when N/4 is a power of two, floor and the difference are
-// exact, and the +-1/2 shift of the remainder is exact or below one float ulp of 1/2.
-__device__ __forceinline__ void texel_coord(float p, float scale, int half, int N, int &i0, int &i1,
-                                            float &f)
+// Lowest corner i0 and weight f of the upper corner for the continuous texel index
+// u = (p + 2) N / 4 - 1/2 with clamp-to-edge: p * N/4 is exact when N/4 is a power of two,
+// floor and remainder are exact, and the shift by 1/2 is exact or below one float ulp of 1/2.
+// Outside [0, N-1] the clamped value is expressed as i0 in {0, N-2} with f in {0, 1}.
+__device__ __forceinline__ void texel_coord(float p, float scale, int half, int N, int &i0, float &f)
 {
     const float a = __fmul_rn(p, scale);
     const float fl = floorf(a);
     const float r = a - fl;
     const int ib = (int)fl + half;
     if (r >= 0.5f) { i0 = ib; f = r - 0.5f; } else { i0 = ib - 1; f = r + 0.5f; }
-    i1 = min(max(i0 + 1, 0), N - 1);
-    i0 = min(max(i0, 0), N - 1);
+    if (i0 < 0) { i0 = 0; f = 0.0f; }
+    if (i0 > N - 2) { i0 = N - 2; f = 1.0f; }
 }
 
-__device__ __forceinline__ float byte_of(uint32_t w, int b)
+// Byte b of a 32-bit word as a float: the byte is placed in the low mantissa bits of 2^23
+// (one byte permute) and 2^23 is subtracted; both steps are exact.
+template <int b>
+__device__ __forceinline__ float byte_f(uint32_t w)
 {
-    return (float)((w >> (8 * b)) & 0xffu);
+    return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u | b)) - 8388608.0f;
 }
 
-// The 20 texels of one sample: 8 grid corners and 4 texels in each plane, with weights.
+template <int c>
+__device__ __forceinline__ float byte_of(uint2 v)
+{
+    return c < 4 ? byte_f<c & 3>(v.x) : byte_f<c & 3>(v.y);
+}
+
+// The 20 texels of one sample (8 grid corners, 4 texels in each plane) and their weights.
 struct Taps {
     uint2 v[20];
-    float w[20];
+    float fx, fy, fz;       // grid fractions
+    float fu[3];            // plane fractions along x, y, z
+    float wv;               // weight of the stored grid corners
+    uint32_t gmask;         // bit c set: grid corner c is stored
 };
+
+__device__ __forceinline__ float grid_w(const Taps &t, int c)
+{
+    const float w = ((c & 1) ? t.fx : 1.0f - t.fx) * ((c & 2) ? t.fy : 1.0f - t.fy) * ((c & 4) ? t.fz : 1.0f - t.fz);
+    return ((t.gmask >> c) & 1u) ? w : 0.0f;
+}
+
+__device__ __forceinline__ float plane_w(const Taps &t, int q, int c)
+{
+    const int ca = q == 0 ? 1 : 0, ra = q == 2 ? 1 : 2;
+    return ((c & 1) ? t.fu[ca] : 1.0f - t.fu[ca]) * ((c & 2) ? t.fu[ra] : 1.0f - t.fu[ra]);
+}
+
+// Lowest corner in a block that is not stored: every corner is looked up on its own.
+__device__ __forceinline__ void gather_grid_slow(const FieldView &fv, int x0, int y0, int z0, Taps &t)
+{
+    const int sh = fv.log2B, msk = fv.B - 1, nb = fv.nb, B1 = fv.B + 1;
+    t.gmask = 0u;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int x = x0 + (c & 1), y = y0 + ((c >> 1) & 1), z = z0 + (c >> 2);
+        const int ent = __ldg(fv.index_grid + ((z >> sh) * nb + (y >> sh)) * nb + (x >> sh));
+        if (ent >= 0) {
+            const size_t slot = (size_t)(ent & 0xffffff);
+            t.v[c] = __ldg(fv.atlas + ((slot * B1 + (z & msk)) * B1 + (y & msk)) * B1 + (x & msk));
+            t.gmask |= 1u << c;
+        } else {
+            t.v[c] = make_uint2(0u, 0u);
+        }
+    }
+}
 
 __device__ __forceinline__ void gather_u8(const FieldView &fv, float p0, float p1, float p2, Taps &t)
 {
     const float sL = (float)fv.L * 0.25f;
     const int hL = fv.L >> 1;
-    int x0, x1, y0, y1, z0, z1;
-    float fx, fy, fz;
-    texel_coord(p0, sL, hL, fv.L, x0, x1, fx);
-    texel_coord(p1, sL, hL, fv.L, y0, y1, fy);
-    texel_coord(p2, sL, hL, fv.L, z0, z1, fz);
-    const int sh = fv.log2B, msk = fv.B - 1, nb = fv.nb, B = fv.B;
-    const int bx0 = x0 >> sh, bx1 = x1 >> sh, by0 = y0 >> sh, by1 = y1 >> sh, bz0 = z0 >> sh, bz1 = z1 >> sh;
-    const int b000 = __ldg(fv.index_grid + (bz0 * nb + by0) * nb + bx0);
-    const bool one = (bx0 == bx1) & (by0 == by1) & (bz0 == bz1);
+    int x0, y0, z0;
+    texel_coord(p0, sL, hL, fv.L, x0, t.fx);
+    texel_coord(p1, sL, hL, fv.L, y0, t.fy);
+    texel_coord(p2, sL, hL, fv.L, z0, t.fz);
+    const int sh = fv.log2B, msk = fv.B - 1, nb = fv.nb, B1 = fv.B + 1;
+    const int ent = __ldg(fv.index_grid + ((z0 >> sh) * nb + (y0 >> sh)) * nb + (x0 >> sh));
+    if (ent >= 0) {
+        const int lx = x0 & msk, ly = y0 & msk, lz = z0 & msk;
+        const uint2 *base = fv.atlas + ((size_t)(ent & 0xffffff) * B1 + lz) * B1 * B1 + ly * B1 + lx;
+        const int sy = B1, sz = B1 * B1;
+        t.v[0] = __ldg(base);
+        t.v[1] = __ldg(base + 1);
+        t.v[2] = __ldg(base + sy);
+        t.v[3] = __ldg(base + sy + 1);
+        t.v[4] = __ldg(base + sz);
+        t.v[5] = __ldg(base + sz + 1);
+        t.v[6] = __ldg(base + sz + sy);
+        t.v[7] = __ldg(base + sz + sy + 1);
+        t.gmask = 0xffu;
+        const uint32_t miss = ((uint32_t)ent >> 24) << 1;     // bit n: neighbour n not stored
+        if (miss) {
+            // corners that fall in the apron of a neighbour that is not stored
+            const int ex = lx == msk, ey = ly == msk, ez = lz == msk;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
-        const int bx = cx ? bx1 : bx0, by = cy ? by1 : by0, bz = cz ? bz1 : bz0;
-        const int blk = (one || c == 0) ? b000 : __ldg(fv.index_grid + (bz * nb + by) * nb + bx);
-        const int lx = (cx ? x1 : x0) & msk, ly = (cy ? y1 : y0) & msk, lz = (cz ? z1 : z0) & msk;
-        const float w = (cx ? fx : 1.0f - fx) * (cy ? fy : 1.0f - fy) * (cz ? fz : 1.0f - fz);
-        if (blk >= 0) {
-            t.v[c] = __ldg(fv.atlas + (((size_t)blk * B + lz) * B + ly) * B + lx);
-            t.w[c] = w;
-        } else {
-            t.v[c] = make_uint2(0u, 0u);
-            t.w[c] = 0.0f;
+            for (int c = 1; c < 8; ++c) {
+                const int nbr = ((c & 1) & ex) | ((((c >> 1) & 1) & ey) << 1) | ((((c >> 2) & 1) & ez) << 2);
+                if ((miss >> nbr) & 1u) t.gmask &= ~(1u << c);
+            }
         }
+    } else {
+        gather_grid_slow(fv, x0, y0, z0, t);
     }
     const float sR = (float)fv.R * 0.25f;
     const int hR = fv.R >> 1, R = fv.R;
-    int u0[3], u1[3];
-    float fu[3];
-    texel_coord(p0, sR, hR, R, u0[0], u1[0], fu[0]);
-    texel_coord(p1, sR, hR, R, u0[1], u1[1], fu[1]);
-    texel_coord(p2, sR, hR, R, u0[2], u1[2], fu[2]);
+    int u0[3];
+    texel_coord(p0, sR, hR, R, u0[0], t.fu[0]);
+    texel_coord(p1, sR, hR, R, u0[1], t.fu[1]);
+    texel_coord(p2, sR, hR, R, u0[2], t.fu[2]);
     // plane q: columns along axis (1, 0, 0)[q], rows along axis (2, 2, 1)[q]
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         const int ca = q == 0 ? 1 : 0, ra = q == 2 ? 1 : 2;
-        const uint2 *base = fv.planes + (size_t)q * R * R;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int cu = c & 1, cv = c >> 1;
-            const int col = cu ? u1[ca] : u0[ca], row = cv ? u1[ra] : u0[ra];
-            t.v[8 + 4 * q + c] = __ldg(base + (size_t)row * R + col);
-            t.w[8 + 4 * q + c] = (cu ? fu[ca] : 1.0f - fu[ca]) * (cv ? fu[ra] : 1.0f - fu[ra]);
-        }
+        const uint2 *base = fv.planes + ((size_t)q * R + u0[ra]) * R + u0[ca];
+        t.v[8 + 4 * q + 0] = __ldg(base);
+        t.v[8 + 4 * q + 1] = __ldg(base + 1);
+        t.v[8 + 4 * q + 2] = __ldg(base + R);
+        t.v[8 + 4 * q + 3] = __ldg(base + R + 1);
     }
-}
-
-// Density pre-activation t~_0 from gathered taps.
-__device__ __forceinline__ float density_u8(const Taps &t)
-{
-    float k = 0.0f, wv = 0.0f;
-#pragma unroll
-    for (int i = 0; i < 20; ++i) k = fmaf(t.w[i], byte_of(t.v[i].x, 0), k);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) wv += t.w[i];
-    return k * (28.0f / 255.0f) - 14.0f * (wv + 3.0f);
-}
-
-// Appearance pre-activations t~_1..7.
-__device__ __forceinline__ void appearance_u8(const Taps &t, float out[7])
-{
     float wv = 0.0f;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) wv += t.w[i];
-    const float off = 7.0f * (wv + 3.0f);
+    for (int c = 0; c < 8; ++c) wv += grid_w(t, c);
+    t.wv = wv;
+}
+
+// Pre-activation of channel c from gathered taps.
+template <int c>
+__device__ __forceinline__ float channel_u8(const Taps &t)
+{
+    float k = 0.0f;
 #pragma unroll
-    for (int c = 1; c < 8; ++c) {
-        float k = 0.0f;
+    for (int i = 0; i < 8; ++i) k = fmaf(grid_w(t, i), byte_of<c>(t.v[i]), k);
 #pragma unroll
-        for (int i = 0; i < 20; ++i) k = fmaf(t.w[i], byte_of(c < 4 ? t.v[i].x : t.v[i].y, c & 3), k);
-        out[c - 1] = k * (14.0f / 255.0f) - off;
-    }
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) k = fmaf(plane_w(t, q, i), byte_of<c>(t.v[8 + 4 * q + i]), k);
+    constexpr float m = c == 0 ? 14.0f : 7.0f;
+    return k * (2.0f * m / 255.0f) - m * (t.wv + 3.0f);
+}
+
+__device__ __forceinline__ float density_u8(const Taps &t) { return channel_u8<0>(t); }
+
+__device__ __forceinline__ void appearance_u8(const Taps &t, float out[7])
+{
+    out[0] = channel_u8<1>(t);
+    out[1] = channel_u8<2>(t);
+    out[2] = channel_u8<3>(t);
+    out[3] = channel_u8<4>(t);
+    out[4] = channel_u8<5>(t);
+    out[5] = channel_u8<6>(t);
+    out[6] = channel_u8<7>(t);
 }
 
 // Dense float storage: all eight channels of all 20 taps, summed.
@@ -137,18 +195,18 @@ __device__ __forceinline__ void field_f32(const FieldView &fv, float p0, float p
 {
     const float sL = (float)fv.L * 0.25f;
     const int hL = fv.L >> 1, L = fv.L;
-    int x[2], y[2], z[2];
+    int x0, y0, z0;
     float fx, fy, fz;
-    texel_coord(p0, sL, hL, L, x[0], x[1], fx);
-    texel_coord(p1, sL, hL, L, y[0], y[1], fy);
-    texel_coord(p2, sL, hL, L, z[0], z[1], fz);
+    texel_coord(p0, sL, hL, L, x0, fx);
+    texel_coord(p1, sL, hL, L, y0, fy);
+    texel_coord(p2, sL, hL, L, z0, fz);
 #pragma unroll
     for (int c = 0; c < 8; ++c) out[c] = 0.0f;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
         const float w = (cx ? fx : 1.0f - fx) * (cy ? fy : 1.0f - fy) * (cz ? fz : 1.0f - fz);
-        const float4 *q = fv.grid_f32 + (((size_t)z[cz] * L + y[cy]) * L + x[cx]) * 2;
+        const float4 *q = fv.grid_f32 + (((size_t)(z0 + cz) * L + (y0 + cy)) * L + (x0 + cx)) * 2;
         const float4 a = __ldg(q), b = __ldg(q + 1);
         out[0] = fmaf(w, a.x, out[0]); out[1] = fmaf(w, a.y, out[1]);
         out[2] = fmaf(w, a.z, out[2]); out[3] = fmaf(w, a.w, out[3]);
@@ -157,20 +215,19 @@ __device__ __forceinline__ void field_f32(const FieldView &fv, float p0, float p
     }
     const float sR = (float)fv.R * 0.25f;
     const int hR = fv.R >> 1, R = fv.R;
-    int u0[3], u1[3];
+    int u0[3];
     float fu[3];
-    texel_coord(p0, sR, hR, R, u0[0], u1[0], fu[0]);
-    texel_coord(p1, sR, hR, R, u0[1], u1[1], fu[1]);
-    texel_coord(p2, sR, hR, R, u0[2], u1[2], fu[2]);
+    texel_coord(p0, sR, hR, R, u0[0], fu[0]);
+    texel_coord(p1, sR, hR, R, u0[1], fu[1]);
+    texel_coord(p2, sR, hR, R, u0[2], fu[2]);
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         const int ca = q == 0 ? 1 : 0, ra = q == 2 ? 1 : 2;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int cu = c & 1, cv = c >> 1;
-            const int col = cu ? u1[ca] : u0[ca], row = cv ? u1[ra] : u0[ra];
             const float w = (cu ? fu[ca] : 1.0f - fu[ca]) * (cv ? fu[ra] : 1.0f - fu[ra]);
-            const float4 *t = fv.planes_f32 + (((size_t)q * R + row) * R + col) * 2;
+            const float4 *t = fv.planes_f32 + (((size_t)q * R + u0[ra] + cv) * R + u0[ca] + cu) * 2;
             const float4 a = __ldg(t), b = __ldg(t + 1);
             out[0] = fmaf(w, a.x, out[0]); out[1] = fmaf(w, a.y, out[1]);
             out[2] = fmaf(w, a.z, out[2]); out[3] = fmaf(w, a.w, out[3]);

@@ -281,8 +281,46 @@ merf_status merf_scene_upload(const merf_scene_desc *desc, const int32_t *index_
     if ((st = check_occupancy(desc, occ_levels))) return st;
     for (int i = 0; i < MERF_MLP_PARAMS; ++i)
         if (!std::isfinite(mlp_weights[i])) return fail(MERF_ERR_INVALID_ARG, "mlp_weights[%d] not finite", i);
-    const size_t B = desc->block_size, R = desc->plane_res;
-    return upload_common(desc, atlas, (size_t)desc->n_blocks * B * B * B * 8, planes, 3 * R * R * 8, index_grid,
+    if (desc->n_blocks >= (1 << 24)) return fail(MERF_ERR_INVALID_ARG, "n_blocks %d >= 2^24", desc->n_blocks);
+    // Device layout: each stored block gets a one-voxel apron copied from its +x/+y/+z
+    // neighbours, and its index-grid entry carries in bits 24..30 a mask of the neighbours
+    // (dx + 2 dy + 4 dz in 1..7, bit 23 + that number) that are not stored or lie past the
+    // grid edge.
+    const int B = desc->block_size, B1 = B + 1, L = desc->grid_res;
+    const size_t R = desc->plane_res, nbi = nb;
+    std::vector<uint8_t> apron;
+    std::vector<int32_t> ig(nb * nb * nb);
+    try {
+        apron.assign((size_t)desc->n_blocks * B1 * B1 * B1 * 8, 0);
+    } catch (...) {
+        return fail(MERF_ERR_OOM, "host memory for the padded atlas");
+    }
+    auto id_at = [&](size_t bx, size_t by, size_t bz) -> int32_t {
+        if (bx >= nbi || by >= nbi || bz >= nbi) return -1;
+        return index_grid[(bz * nbi + by) * nbi + bx];
+    };
+    for (size_t bz = 0; bz < nbi; ++bz)
+        for (size_t by = 0; by < nbi; ++by)
+            for (size_t bx = 0; bx < nbi; ++bx) {
+                const int32_t id = id_at(bx, by, bz);
+                if (id < 0) { ig[(bz * nbi + by) * nbi + bx] = -1; continue; }
+                uint32_t miss = 0;
+                for (int n = 1; n < 8; ++n)
+                    if (id_at(bx + (n & 1), by + ((n >> 1) & 1), bz + (n >> 2)) < 0) miss |= 1u << (n - 1);
+                ig[(bz * nbi + by) * nbi + bx] = (int32_t)((uint32_t)id | (miss << 24));
+                uint8_t *dst = apron.data() + (size_t)id * B1 * B1 * B1 * 8;
+                for (int lz = 0; lz < B1; ++lz)
+                    for (int ly = 0; ly < B1; ++ly)
+                        for (int lx = 0; lx < B1; ++lx) {
+                            const size_t gx = bx * B + lx, gy = by * B + ly, gz = bz * B + lz;
+                            if (gx >= (size_t)L || gy >= (size_t)L || gz >= (size_t)L) continue;
+                            const int32_t src = id_at(gx / B, gy / B, gz / B);
+                            if (src < 0) continue;
+                            const uint8_t *sv = atlas + ((((size_t)src * B + gz % B) * B + gy % B) * B + gx % B) * 8;
+                            memcpy(dst + (((size_t)lz * B1 + ly) * B1 + lx) * 8, sv, 8);
+                        }
+            }
+    return upload_common(desc, apron.data(), apron.size(), planes, 3 * R * R * 8, ig.data(),
                          nb * nb * nb * sizeof(int32_t), occ_levels, mlp_weights, stream, out);
 }
 

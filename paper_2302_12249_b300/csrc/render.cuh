@@ -1,9 +1,9 @@
 // render.cuh -- fused per-ray render kernel and traversal-only kernel for sm_103a.
 //
 // One thread renders one pixel ray end to end: ray generation, segment table, lattice walk
-// with coarse-to-fine empty-space skipping, gather of the 20 texels of each evaluated
-// sample, density-first activation (Sec. 5: appearance is unpacked only when the sample's
-// opacity is non-zero), front-to-back compositing of C_d and F with early termination
+// with coarse-to-fine empty-space skipping (occupied samples come in runs that share a finest
+// occupancy cell), gather of the 20 texels of each evaluated sample, density-first activation
+// (Sec. 5: appearance is unpacked only when the sample's opacity is non-zero), front-to-back compositing of C_d and F with early termination
 // (Eq. 1, Eq. 2, Sec. 5), and finally the deferred MLP h(C_d, F, d) (Sec. 2, App. B), whose
 // 883 weights are staged once per CTA in shared memory and read as warp-wide broadcasts.
 // A warp covers an 8 x 4 pixel tile and a CTA a 16 x 8 tile, so neighbouring rays walk
@@ -40,7 +40,7 @@ struct RenderParams {
     CamBlock cams;
 };
 
-__device__ __forceinline__ float sigmoid_f(float x) { return 1.0f / (1.0f + expf(-x)); }
+__device__ __forceinline__ float sigmoid_f(float x) { return __fdividef(1.0f, 1.0f + __expf(-x)); }
 
 // h(C_d, F, d): [C_d, F, d, sin d, cos d, sin 2d, cos 2d, sin 4d, cos 4d, sin 8d, cos 8d]
 // -> 16 ReLU -> 16 ReLU -> 3 (App. B: three layers, 16 hidden units, 4 frequencies).
@@ -114,8 +114,11 @@ __global__ void __launch_bounds__(kThreads) render_kernel(const __grid_constant_
         nlat = wk.nlat;
         float T = 1.0f, cd[3] = {0.0f, 0.0f, 0.0f}, F[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         int term = 0;
-        float p0, p1, p2;
-        while (wk.next(P.occ, p0, p1, p2)) {
+        int run_end = 0;
+        for (;;) {
+            if (wk.k >= run_end && !wk.next_run(P.occ, run_end)) break;
+            float p0, p1, p2;
+            wk.position(wk.k, p0, p1, p2);
             float dens, app[7];
             Taps tp;
             if (kStorage == 0) {
@@ -128,9 +131,9 @@ __global__ void __launch_bounds__(kThreads) render_kernel(const __grid_constant_
 #pragma unroll
                 for (int c = 0; c < 7; ++c) app[c] = all[1 + c];
             }
-            const float tau = expf(dens);
+            const float tau = __expf(dens);
             const float dw = wk.delta_world(wk.k);
-            const float alpha = 1.0f - expf(-tau * dw);
+            const float alpha = 1.0f - __expf(-tau * dw);
             ++neval;
             if (alpha > 0.0f) {
                 ++napp;
@@ -192,10 +195,10 @@ __global__ void __launch_bounds__(kThreads) trace_kernel(const __grid_constant__
     Walker wk;
     wk.init(o, d, P.step);
     P.nlat[pix] = wk.nlat;
-    float p0, p1, p2;
-    while (wk.next(P.occ, p0, p1, p2)) {
-        if (wk.k < 32 * P.words) row[wk.k >> 5] |= 1u << (wk.k & 31);
-        ++wk.k;
+    int run_end = 0;
+    while (wk.next_run(P.occ, run_end)) {
+        for (; wk.k < run_end; ++wk.k)
+            if (wk.k < 32 * P.words) row[wk.k >> 5] |= 1u << (wk.k & 31);
     }
 }
 

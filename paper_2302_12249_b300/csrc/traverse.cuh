@@ -7,7 +7,9 @@
 // its finest occupancy cell is set.  Empty space is skipped coarse-to-fine against the
 // max-pooled occupancy hierarchy (Sec. 5): when a level reports the sample's cell empty, a
 // slab test against that cell's box on the current straight segment gives the exit, and the
-// walk jumps to the last lattice sample before it.
+// walk jumps past the last lattice sample before it.  When every level reports the cell
+// occupied, the same exit test on the finest cell yields the run of consecutive samples
+// that share it, and the run is evaluated without querying the hierarchy again.
 //
 // Exactness.  Every float operation that decides an integer (which lattice samples exist,
 // which segment and which occupancy cell a sample falls in) is an IEEE round-to-nearest
@@ -237,7 +239,7 @@ __device__ __forceinline__ void build_segments(const float o[3], const float d[3
 // cell of a contracted coordinate at resolution N (N even): floor(p N/4) + N/2, clamped
 __device__ __forceinline__ int cell_of(float p, float scale, int half, int N)
 {
-    int c = (int)floorf(F_MUL(p, scale)) + half;
+    int c = __float2int_rd(F_MUL(p, scale)) + half;
     return min(max(c, 0), N - 1);
 }
 
@@ -245,14 +247,16 @@ __device__ __forceinline__ int cell_of(float p, float scale, int half, int N)
 struct Walker {
     Segs sg;
     float A0, A1, A2, e0, e1, e2, S0, S1;  // current segment
+    float ie0, ie1, ie2;                   // approximate 1/e (slab-exit candidates only)
     int seg, kend, k, nlat;
-    float step, total;
+    float step, inv_step, total;
 
     __device__ __forceinline__ void load_seg(int i)
     {
         seg = i;
         A0 = sg.A[i][0]; A1 = sg.A[i][1]; A2 = sg.A[i][2];
         e0 = sg.e[i][0]; e1 = sg.e[i][1]; e2 = sg.e[i][2];
+        ie0 = __frcp_rn(e0); ie1 = __frcp_rn(e1); ie2 = __frcp_rn(e2);
         S0 = sg.S[i];
         S1 = sg.S[i + 1];
         kend = (i == sg.n - 1) ? 0x7fffffff : first_k_at(S1, step);
@@ -261,6 +265,7 @@ struct Walker {
     __device__ __forceinline__ void init(const float o[3], const float d[3], float step_)
     {
         step = step_;
+        inv_step = 1.0f / step_;
         build_segments(o, d, sg);
         total = sg.S[sg.n];
         nlat = lattice_count(total, step);
@@ -276,14 +281,57 @@ struct Walker {
         p2 = F_ADD(A2, F_MUL(u, e2));
     }
 
-    // Advance k (>= current) to the next occupied lattice sample; false when the ray ends.
-    __device__ __forceinline__ bool next(const OccView &occ, float &p0, float &p1, float &p2)
+    // One past the last lattice index whose sample still lies in the cell (x, y, z) of the
+    // level of resolution N0 >> sh; k + 1 if that cannot be shown.  The candidate comes from a
+    // slab test against the cell's box on the current segment; it is accepted only if the
+    // candidate sample's own position (the same rounded arithmetic as every sample) lands in
+    // the same cell.  By per-axis monotonicity of positions along a segment, every sample in
+    // between lands there too.
+    __device__ __forceinline__ int cell_exit(float p0, float p1, float p2, int x, int y, int z, int sh,
+                                             int N0, float sc0, int h0) const
+    {
+        const int Nl = N0 >> sh;
+        const float inv = 4.0f / (float)Nl;
+        const int hl = Nl >> 1;
+        const float lo0 = (float)(x - hl) * inv, lo1 = (float)(y - hl) * inv, lo2 = (float)(z - hl) * inv;
+        float umin = CUDART_INF_F;
+        if (e0 != 0.0f) umin = fminf(umin, ((e0 > 0.0f ? lo0 + inv : lo0) - p0) * ie0);
+        if (e1 != 0.0f) umin = fminf(umin, ((e1 > 0.0f ? lo1 + inv : lo1) - p1) * ie1);
+        if (e2 != 0.0f) umin = fminf(umin, ((e2 > 0.0f ? lo2 + inv : lo2) - p2) * ie2);
+        const int last = min(kend, nlat) - 1;
+        int m = last;
+        const float s_exit = lattice_s(k, step) + umin;
+        if (s_exit < CUDART_INF_F) {
+            const float mf = ceilf(s_exit * inv_step - 0.5f) - 1.0f;
+            m = (mf < (float)last) ? (int)fmaxf(mf, -1.0f) : last;
+        }
+        if (m > k) {
+            float q0, q1, q2;
+            position(m, q0, q1, q2);
+            if ((cell_of(q0, sc0, h0, N0) >> sh) == x && (cell_of(q1, sc0, h0, N0) >> sh) == y &&
+                (cell_of(q2, sc0, h0, N0) >> sh) == z)
+                return m + 1;
+            if (m - 1 > k) {
+                position(m - 1, q0, q1, q2);
+                if ((cell_of(q0, sc0, h0, N0) >> sh) == x && (cell_of(q1, sc0, h0, N0) >> sh) == y &&
+                    (cell_of(q2, sc0, h0, N0) >> sh) == z)
+                    return m;
+            }
+        }
+        return k + 1;
+    }
+
+    // Advance k to the next occupied lattice sample and return the end (exclusive) of the run
+    // of samples that share its finest occupancy cell: they are all evaluated without querying
+    // the hierarchy again.  False when the ray has no further occupied sample.
+    __device__ __forceinline__ bool next_run(const OccView &occ, int &run_end)
     {
         const int N0 = occ.res[0];
         const float sc0 = (float)N0 * 0.25f;
         const int h0 = N0 >> 1;
         while (k < nlat) {
             while (k >= kend) load_seg(seg + 1);
+            float p0, p1, p2;
             position(k, p0, p1, p2);
             const int c0 = cell_of(p0, sc0, h0, N0), c1 = cell_of(p1, sc0, h0, N0),
                       c2 = cell_of(p2, sc0, h0, N0);
@@ -293,41 +341,9 @@ struct Walker {
                 const int x = c0 >> sh, y = c1 >> sh, z = c2 >> sh;
                 if (__ldg(occ.level[l] + ((size_t)z * Nl + y) * Nl + x) == 0) { lvl = l; break; }
             }
-            if (lvl < 0) return true;
-            // skip the empty level-`lvl` cell: exit of its box along the current segment
-            const int sh = occ.shift[lvl], Nl = occ.res[lvl];
-            const int x = c0 >> sh, y = c1 >> sh, z = c2 >> sh;
-            const float inv = 4.0f / (float)Nl;
-            const int hl = Nl >> 1;
-            const float lo0 = (float)(x - hl) * inv, lo1 = (float)(y - hl) * inv, lo2 = (float)(z - hl) * inv;
-            float umin = CUDART_INF_F;
-            if (e0 > 0.0f) umin = fminf(umin, (lo0 + inv - p0) / e0);
-            else if (e0 < 0.0f) umin = fminf(umin, (lo0 - p0) / e0);
-            if (e1 > 0.0f) umin = fminf(umin, (lo1 + inv - p1) / e1);
-            else if (e1 < 0.0f) umin = fminf(umin, (lo1 - p1) / e1);
-            if (e2 > 0.0f) umin = fminf(umin, (lo2 + inv - p2) / e2);
-            else if (e2 < 0.0f) umin = fminf(umin, (lo2 - p2) / e2);
-            const int last = min(kend, nlat) - 1;
-            int m = last;
-            const float s_exit = lattice_s(k, step) + umin;
-            if (s_exit < CUDART_INF_F) {
-                const float mf = ceilf(s_exit / step - 0.5f) - 1.0f;
-                m = (mf < (float)last) ? (int)fmaxf(mf, -1.0f) : last;
-            }
-            int nk = k + 1;
-            if (m > k) {
-                float q0, q1, q2;
-                position(m, q0, q1, q2);
-                if ((cell_of(q0, sc0, h0, N0) >> sh) == x && (cell_of(q1, sc0, h0, N0) >> sh) == y &&
-                    (cell_of(q2, sc0, h0, N0) >> sh) == z) {
-                    nk = m + 1;
-                } else if (m - 1 > k) {
-                    position(m - 1, q0, q1, q2);
-                    if ((cell_of(q0, sc0, h0, N0) >> sh) == x && (cell_of(q1, sc0, h0, N0) >> sh) == y &&
-                        (cell_of(q2, sc0, h0, N0) >> sh) == z)
-                        nk = m;
-                }
-            }
+            const int sh = lvl < 0 ? 0 : occ.shift[lvl];
+            const int nk = cell_exit(p0, p1, p2, c0 >> sh, c1 >> sh, c2 >> sh, sh, N0, sc0, h0);
+            if (lvl < 0) { run_end = nk; return true; }
             k = nk;
         }
         return false;
@@ -341,7 +357,7 @@ struct Walker {
         if (lo >= S0 && hi <= S1) {
             const float c = sg.c[seg], g = sg.g[seg];
             const float u1 = lo - S0, u2 = hi - S0;
-            return c * (hi - lo) / ((1.0f - g * u1) * (1.0f - g * u2));
+            return __fdividef(c * (hi - lo), (1.0f - g * u1) * (1.0f - g * u2));
         }
         int m = seg;
         while (m > 0 && lo < sg.S[m]) --m;
