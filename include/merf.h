@@ -146,6 +146,25 @@ merf_status merf_render_host(const merf_scene *scene, const merf_camera *cams, i
                              int W, int H, float *d_staging, float *h_out,
                              const merf_render_opts *opts, void *stream);
 
+/* Like merf_render_host, but the caller passes no device buffer and the call allocates none.
+ * The paper has no counterpart; this is a service for callers that cannot allocate device
+ * memory themselves, for example an application whose own memory manager owns the whole device
+ * pool, or a per-frame render loop that must not call cudaMalloc because it can synchronise the
+ * device and stall other work.  The image is rendered into a fixed device staging area that
+ * is part of the library (MERF_NOALLOC_STAGING_BYTES = 32 MiB, enough for one 1920x1080 RGB
+ * float frame; every GPU that loads the library holds it until the process exits) and copied to
+ * `h_out` (host float32 [n_cams][H][W][3]; page-locked for the copy to be asynchronous).
+ * Requests whose image exceeds the staging area return MERF_ERR_INVALID_ARG.  The first call
+ * on a device looks up the staging area's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls share the one
+ * staging area: the kernel writes every pixel of it that the call returns, so nothing needs
+ * clearing, but calls that overlap on the GPU (from several host threads or streams at once)
+ * race on it.  Returns after the copy has completed. */
+enum { MERF_NOALLOC_STAGING_BYTES = 32 << 20 };
+merf_status merf_render_host_noalloc(const merf_scene *scene, const merf_camera *cams, int n_cams,
+                                     int W, int H, float *h_out, const merf_render_opts *opts,
+                                     void *stream);
+
 /* Evaluated-sample sets of the traversal alone (Sec. 5 empty-space skipping, early
  * termination off): bit k of mask row r (device uint32 [n_cams*H*W][words], row
  * r = (cam*H + row)*W + col) is set iff lattice sample k of that ray lies in an occupied

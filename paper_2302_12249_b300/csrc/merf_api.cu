@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -379,6 +380,18 @@ merf_status merf_render_host(const merf_scene *scene, const merf_camera *cams, i
     return ok();
 }
 
+// Staging area of merf_render_host_noalloc: device memory that belongs to the library, so a
+// caller that cannot allocate can still render into host memory.  Host code must not use the
+// name as a pointer (it denotes a host-side shadow); the device address is looked up once per
+// device with cudaGetSymbolAddress.
+static __device__ __align__(256) float g_noalloc_staging[MERF_NOALLOC_STAGING_BYTES / sizeof(float)];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+float *g_noalloc_ptr[kMaxDevices] = {};
+}  // namespace
+
 merf_status merf_trace(const merf_scene *scene, const merf_camera *cams, int n_cams, int W, int H, uint32_t *mask,
                        int words, int32_t *n_lattice, const merf_render_opts *opts, void *stream)
 {
@@ -401,6 +414,43 @@ merf_status merf_trace(const merf_scene *scene, const merf_camera *cams, int n_c
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return fail(MERF_ERR_CUDA, "trace launch: %s", cudaGetErrorString(e));
     }
+    return ok();
+}
+
+merf_status merf_render_host_noalloc(const merf_scene *scene, const merf_camera *cams, int n_cams, int W, int H,
+                                     float *h_out, const merf_render_opts *opts, void *stream)
+{
+    if (!h_out) return fail(MERF_ERR_INVALID_ARG, "h_out is NULL");
+    merf_status st = check_frame(scene, cams, n_cams, W, H);
+    if (st) return st;
+    if ((st = check_opts(opts))) return st;
+    const size_t bytes = (size_t)n_cams * W * H * 3 * sizeof(float);
+    if (bytes > (size_t)MERF_NOALLOC_STAGING_BYTES)
+        return fail(MERF_ERR_INVALID_ARG,
+                    "image of %zu bytes exceeds the %d-byte staging area of merf_render_host_noalloc "
+                    "(render fewer cameras per call or use merf_render_host)",
+                    bytes, (int)MERF_NOALLOC_STAGING_BYTES);
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(MERF_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return fail(MERF_ERR_UNSUPPORTED, "device ordinal %d >= %d", dev, kMaxDevices);
+    float *staging = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_staging);
+            if (e != cudaSuccess || !p)
+                return fail(MERF_ERR_CUDA, "cudaGetSymbolAddress(staging): %s", cudaGetErrorString(e));
+            g_noalloc_ptr[dev] = (float *)p;
+        }
+        staging = g_noalloc_ptr[dev];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = launch_render(scene, cams, n_cams, W, H, staging, nullptr, nullptr, opts, s))) return st;
+    e = cudaMemcpyAsync(h_out, staging, bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(MERF_ERR_CUDA, "render_host_noalloc copy: %s", cudaGetErrorString(e));
     return ok();
 }
 

@@ -20,11 +20,13 @@ STORAGE_U8_SPARSE, STORAGE_F32_DENSE = 0, 1
 PREC_FP32, PREC_FP16, PREC_BF16 = 0, 1, 2
 MAX_OCC_LEVELS = 8
 AUX_SIZE = 12
+NOALLOC_STAGING_BYTES = 32 << 20
 AUX_CD, AUX_F, AUX_T, AUX_NLAT, AUX_NEVAL, AUX_NAPP, AUX_TERM = 0, 3, 7, 8, 9, 10, 11
 CNT_RAYS, CNT_LATTICE, CNT_EVAL, CNT_APPEAR = 0, 1, 2, 3
 
 EXPORTS = ("merf_scene_upload", "merf_scene_upload_dense", "merf_scene_free", "merf_scene_device_bytes",
-           "merf_render", "merf_render_aux", "merf_render_host", "merf_trace", "merf_set_device_budget",
+           "merf_render", "merf_render_aux", "merf_render_host", "merf_render_host_noalloc", "merf_trace",
+           "merf_set_device_budget",
            "merf_last_error", "merf_version")
 
 
@@ -65,13 +67,14 @@ def lib():
         L.merf_render.argtypes = [vp, vp, i32, i32, i32, vp, ct.POINTER(Opts), vp]
         L.merf_render_aux.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, ct.POINTER(Opts), vp]
         L.merf_render_host.argtypes = [vp, vp, i32, i32, i32, vp, vp, ct.POINTER(Opts), vp]
+        L.merf_render_host_noalloc.argtypes = [vp, vp, i32, i32, i32, vp, ct.POINTER(Opts), vp]
         L.merf_trace.argtypes = [vp, vp, i32, i32, i32, vp, i32, vp, ct.POINTER(Opts), vp]
         L.merf_set_device_budget.argtypes = [ct.c_size_t]
         L.merf_set_device_budget.restype = None
         L.merf_last_error.restype = ct.c_char_p
         L.merf_version.restype = ct.c_char_p
         for name in ("merf_scene_upload", "merf_scene_upload_dense", "merf_render", "merf_render_aux",
-                     "merf_render_host", "merf_trace"):
+                     "merf_render_host", "merf_render_host_noalloc", "merf_trace"):
             getattr(L, name).restype = ct.c_int
         _lib = L
     return _lib
@@ -194,6 +197,22 @@ def render_host(scene: Scene, cams: np.ndarray, W: int, H: int, step: float, sta
     _check(lib().merf_render_host(scene.handle, _np_ptr(cams), n, W, H,
                                   _dev_ptr(staging, torch.float32, n * H * W * 3, "staging"),
                                   ct.c_void_p(host_out.data_ptr()), ct.byref(o), _stream(stream)))
+    return host_out
+
+
+def render_host_noalloc(scene: Scene, cams: np.ndarray, W: int, H: int, step: float, host_out: torch.Tensor,
+                        t_term: float = 2e-4, early_term: bool = True, precision: int = PREC_FP32,
+                        stream=None) -> torch.Tensor:
+    """Render into host memory through the library's fixed staging area (no device allocation
+    by the caller or the library; at most NOALLOC_STAGING_BYTES of image per call)."""
+    cams = cameras(cams)
+    n = cams.shape[0]
+    if host_out.is_cuda or host_out.dtype != torch.float32 or not host_out.is_contiguous() or \
+            host_out.numel() != n * H * W * 3:
+        raise ValueError("host_out must be a contiguous host float32 tensor [n, H, W, 3]")
+    o = opts(step, t_term, early_term, precision)
+    _check(lib().merf_render_host_noalloc(scene.handle, _np_ptr(cams), n, W, H, ct.c_void_p(host_out.data_ptr()),
+                                          ct.byref(o), _stream(stream)))
     return host_out
 
 
