@@ -21,6 +21,8 @@
 // [0, N-2]), so no lookup leaves the array.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -188,6 +190,96 @@ __device__ __forceinline__ void appearance_u8(const Taps &t, float out[7])
     out[4] = channel_u8<5>(t);
     out[5] = channel_u8<6>(t);
     out[6] = channel_u8<7>(t);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Reduced-precision appearance (the precision form).  Each tap's seven appearance bytes become
+// four half2 values 1024 + byte, one byte permute each (exact: the half 0x64XX is 1024 + XX).
+// Within each source (grid, P_x, P_y, P_z) every tap is taken relative to the source's first
+// tap: the difference of two such halves is an exact integer in [-255, 255], so the 16-bit
+// arithmetic only carries the interpolation corrections sum_i w_i (b_i - b_first), accumulated
+// in half2 (FP16) or bfloat162 (BF16, which also holds those integers exactly) with weights
+// rounded to that type.  The first taps' values and the dequantisation stay in FP32:
+//     K_c = W_V b_first,V + b_first,Px + b_first,Py + b_first,Pz + sum of corrections.
+
+template <int pair>   // appearance channel pairs (1,2), (3,3), (4,5), (6,7)
+__device__ __forceinline__ __half2 magic_h2(uint2 v)
+{
+    const uint32_t u = pair == 0 ? __byte_perm(v.x, 0x64646464u, 0x4241u)
+                     : pair == 1 ? __byte_perm(v.x, 0x64646464u, 0x4343u)
+                     : pair == 2 ? __byte_perm(v.y, 0x64646464u, 0x4140u)
+                                 : __byte_perm(v.y, 0x64646464u, 0x4342u);
+    __half2 h;
+    memcpy(&h, &u, 4);
+    return h;
+}
+
+template <int kPrec, int pair>   // kPrec 1: FP16, 2: BF16
+__device__ __forceinline__ float2 lp_pair(const Taps &t, const float w[20], float2 &first_v, float2 &first_p)
+{
+    const __half2 mag = __float2half2_rn(1024.0f);
+    __half2 first[4];
+    float2 corr;
+    if constexpr (kPrec == 1) {
+        __half2 acc = __float2half2_rn(0.0f);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int b = s == 0 ? 0 : 4 + 4 * s, n = s == 0 ? 8 : 4;
+            first[s] = magic_h2<pair>(t.v[b]);
+#pragma unroll
+            for (int i = 1; i < n; ++i)
+                acc = __hfma2(__float2half2_rn(w[b + i]), __hsub2(magic_h2<pair>(t.v[b + i]), first[s]), acc);
+        }
+        corr = __half22float2(acc);
+    } else {
+        __nv_bfloat162 acc = __float2bfloat162_rn(0.0f);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int b = s == 0 ? 0 : 4 + 4 * s, n = s == 0 ? 8 : 4;
+            first[s] = magic_h2<pair>(t.v[b]);
+#pragma unroll
+            for (int i = 1; i < n; ++i) {
+                const __nv_bfloat162 dd =
+                    __float22bfloat162_rn(__half22float2(__hsub2(magic_h2<pair>(t.v[b + i]), first[s])));
+                acc = __hfma2(__float2bfloat162_rn(w[b + i]), dd, acc);
+            }
+        }
+        corr = __bfloat1622float2(acc);
+    }
+    first_v = __half22float2(__hsub2(first[0], mag));
+    // the three plane first taps summed exactly in half (integers <= 765)
+    first_p = __half22float2(__hadd2(__hadd2(__hsub2(first[1], mag), __hsub2(first[2], mag)), __hsub2(first[3], mag)));
+    return corr;
+}
+
+template <int kPrec>
+__device__ __forceinline__ void appearance_lp(const Taps &t, float out[7])
+{
+    float w[20];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) w[c] = grid_w(t, c);
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) w[8 + 4 * q + c] = plane_w(t, q, c);
+    float K[8];
+    float2 fv, fp, cr;
+    cr = lp_pair<kPrec, 0>(t, w, fv, fp);
+    K[0] = fmaf(t.wv, fv.x, fp.x) + cr.x; K[1] = fmaf(t.wv, fv.y, fp.y) + cr.y;
+    cr = lp_pair<kPrec, 1>(t, w, fv, fp);
+    K[2] = fmaf(t.wv, fv.x, fp.x) + cr.x; K[3] = K[2];
+    cr = lp_pair<kPrec, 2>(t, w, fv, fp);
+    K[4] = fmaf(t.wv, fv.x, fp.x) + cr.x; K[5] = fmaf(t.wv, fv.y, fp.y) + cr.y;
+    cr = lp_pair<kPrec, 3>(t, w, fv, fp);
+    K[6] = fmaf(t.wv, fv.x, fp.x) + cr.x; K[7] = fmaf(t.wv, fv.y, fp.y) + cr.y;
+    const float off = 7.0f * (t.wv + 3.0f), sc = 14.0f / 255.0f;
+    out[0] = K[0] * sc - off;   // channel 1
+    out[1] = K[1] * sc - off;   // channel 2
+    out[2] = K[2] * sc - off;   // channel 3
+    out[3] = K[4] * sc - off;   // channel 4
+    out[4] = K[5] * sc - off;   // channel 5
+    out[5] = K[6] * sc - off;   // channel 6
+    out[6] = K[7] * sc - off;   // channel 7
 }
 
 // Dense float storage: all eight channels of all 20 taps, summed.

@@ -180,8 +180,8 @@ merf_status check_opts(const merf_render_opts *o)
     if (o->early_term != 0 && o->early_term != 1)
         return fail(MERF_ERR_INVALID_ARG, "early_term must be 0 or 1");
     if (o->reserved != 0) return fail(MERF_ERR_INVALID_ARG, "reserved must be 0");
-    if (o->precision != MERF_PREC_FP32)
-        return fail(MERF_ERR_UNSUPPORTED, "precision %d is not available in this build", o->precision);
+    if (o->precision != MERF_PREC_FP32 && o->precision != MERF_PREC_FP16 && o->precision != MERF_PREC_BF16)
+        return fail(MERF_ERR_INVALID_ARG, "precision %d is not a MERF_PREC_* value", o->precision);
     return MERF_OK;
 }
 
@@ -240,6 +240,8 @@ merf_status launch_render(const merf_scene *s, const merf_camera *cams, int n, i
                           float *aux, unsigned long long *counters, const merf_render_opts *o,
                           cudaStream_t st)
 {
+    if (o->precision != MERF_PREC_FP32 && s->desc.storage != MERF_STORAGE_U8_SPARSE)
+        return fail(MERF_ERR_UNSUPPORTED, "reduced precision needs uint8 block-sparse storage");
     merf::RenderParams P = make_params(s, o, W, H);
     P.out = out;
     P.aux = aux;
@@ -250,10 +252,14 @@ merf_status launch_render(const merf_scene *s, const merf_camera *cams, int n, i
         P.cam0 = c0;
         for (int c = 0; c < nc; ++c) memcpy(P.cams.m[c], &cams[c0 + c], sizeof(merf_camera));
         const dim3 grid((W + merf::kTileW - 1) / merf::kTileW, (H + merf::kTileH - 1) / merf::kTileH, nc);
-        if (s->desc.storage == MERF_STORAGE_U8_SPARSE)
-            merf::render_kernel<0><<<grid, block, 0, st>>>(P);
+        if (s->desc.storage == MERF_STORAGE_F32_DENSE)
+            merf::render_kernel<1, 0><<<grid, block, 0, st>>>(P);
+        else if (o->precision == MERF_PREC_FP16)
+            merf::render_kernel<0, 1><<<grid, block, 0, st>>>(P);
+        else if (o->precision == MERF_PREC_BF16)
+            merf::render_kernel<0, 2><<<grid, block, 0, st>>>(P);
         else
-            merf::render_kernel<1><<<grid, block, 0, st>>>(P);
+            merf::render_kernel<0, 0><<<grid, block, 0, st>>>(P);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return fail(MERF_ERR_CUDA, "render launch: %s", cudaGetErrorString(e));
     }

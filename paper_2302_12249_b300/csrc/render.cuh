@@ -86,6 +86,178 @@ __device__ __forceinline__ void mlp_f32(const float *w, const float cd[3], const
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// The deferred MLP on tensor cores (precision form): one warp evaluates its 32 pixels with
+// mma.sync m16n8k16 (FP16 or BF16 operands, FP32 accumulation).  Layer 1 is [32 x 48] x [48 x 16]
+// (34 inputs zero-padded to 48), layer 2 [32 x 16] x [16 x 16], layer 3 [32 x 16] x [16 x 8]
+// (3 outputs zero-padded to 8).  A layer's FP32 accumulator fragments, after bias and ReLU, are
+// packed directly into the next layer's A fragments (the m16n8 C layout of two adjacent n-tiles
+// is the m16k16 A layout), so only the inputs and outputs pass through shared memory.
+
+constexpr int kW0Stride = 28, kW1Stride = 12, kXStride = 28;   // 32-bit words per row (padded)
+
+struct MlpTC {
+    uint32_t w0[16 * kW0Stride];   // W0^T [n][k], k < 48, 16-bit pairs
+    uint32_t w1[16 * kW1Stride];   // W1^T [n][k], k < 16
+    uint32_t w2[8 * kW1Stride];    // W2^T [n][k], n < 3 used
+    float b0[16], b1[16], b2[8];
+    uint32_t x[kThreads / 32][32 * kXStride];   // per-warp input rows
+};
+
+template <int kPrec>
+__device__ __forceinline__ uint32_t pack16(float lo, float hi)
+{
+    uint32_t u;
+    if constexpr (kPrec == 1) {
+        const __half2 h = __floats2half2_rn(lo, hi);
+        memcpy(&u, &h, 4);
+    } else {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        memcpy(&u, &h, 4);
+    }
+    return u;
+}
+
+template <int kPrec>
+__device__ __forceinline__ void mma16816(float d[4], const uint32_t a[4], uint32_t b0, uint32_t b1)
+{
+    if constexpr (kPrec == 1)
+        asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                     "{%0,%1,%2,%3};\n"
+                     : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                     : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    else
+        asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                     "{%0,%1,%2,%3};\n"
+                     : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                     : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Stage the scene's FP32 weights as transposed 16-bit tiles (whole CTA, before a barrier).
+template <int kPrec>
+__device__ __forceinline__ void mlp_tc_load(MlpTC &ms, const float *w)
+{
+    const float *W0 = w, *B0 = w + 544, *W1 = w + 560, *B1 = w + 816, *W2 = w + 832, *B2 = w + 880;
+    for (int e = threadIdx.x; e < 16 * 24; e += kThreads) {
+        const int n = e / 24, kk = 2 * (e % 24);
+        const float a = kk < 34 ? __ldg(W0 + kk * 16 + n) : 0.0f;
+        const float b = kk + 1 < 34 ? __ldg(W0 + (kk + 1) * 16 + n) : 0.0f;
+        ms.w0[n * kW0Stride + e % 24] = pack16<kPrec>(a, b);
+    }
+    for (int e = threadIdx.x; e < 16 * 8; e += kThreads) {
+        const int n = e / 8, kk = 2 * (e % 8);
+        ms.w1[n * kW1Stride + e % 8] = pack16<kPrec>(__ldg(W1 + kk * 16 + n), __ldg(W1 + (kk + 1) * 16 + n));
+    }
+    for (int e = threadIdx.x; e < 8 * 8; e += kThreads) {
+        const int n = e / 8, kk = 2 * (e % 8);
+        const float a = n < 3 ? __ldg(W2 + kk * 3 + n) : 0.0f, b = n < 3 ? __ldg(W2 + (kk + 1) * 3 + n) : 0.0f;
+        ms.w2[n * kW1Stride + e % 8] = pack16<kPrec>(a, b);
+    }
+    for (int e = threadIdx.x; e < 16; e += kThreads) {
+        ms.b0[e] = __ldg(B0 + e);
+        ms.b1[e] = __ldg(B1 + e);
+        if (e < 8) ms.b2[e] = e < 3 ? __ldg(B2 + e) : 0.0f;
+    }
+}
+
+template <int kPrec>
+__device__ __forceinline__ void relu_pack(const float c0[4], const float c1[4], uint32_t a[4])
+{
+    a[0] = pack16<kPrec>(fmaxf(c0[0], 0.0f), fmaxf(c0[1], 0.0f));
+    a[1] = pack16<kPrec>(fmaxf(c0[2], 0.0f), fmaxf(c0[3], 0.0f));
+    a[2] = pack16<kPrec>(fmaxf(c1[0], 0.0f), fmaxf(c1[1], 0.0f));
+    a[3] = pack16<kPrec>(fmaxf(c1[2], 0.0f), fmaxf(c1[3], 0.0f));
+}
+
+// All 32 lanes of the warp call this together (lanes without a pixel pass zeros).
+template <int kPrec>
+__device__ __forceinline__ void mlp_tc(MlpTC &ms, const float cd[3], const float f[4], const float d[3],
+                                       float out[3])
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+    uint32_t *xs = ms.x[threadIdx.x >> 5];
+    float x[48];
+    x[0] = cd[0]; x[1] = cd[1]; x[2] = cd[2];
+    x[3] = f[0]; x[4] = f[1]; x[5] = f[2]; x[6] = f[3];
+    x[7] = d[0]; x[8] = d[1]; x[9] = d[2];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        const float fr = (float)(1 << l);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float sn, cs;
+            sincosf(fr * d[k], &sn, &cs);
+            x[10 + 6 * l + k] = sn;
+            x[13 + 6 * l + k] = cs;
+        }
+    }
+#pragma unroll
+    for (int k = 34; k < 48; ++k) x[k] = 0.0f;
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 24; ++j) xs[lane * kXStride + j] = pack16<kPrec>(x[2 * j], x[2 * j + 1]);
+    __syncwarp();
+
+    float acc[2][2][4];
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            acc[t][u][0] = acc[t][u][2] = ms.b0[8 * u + 2 * c];
+            acc[t][u][1] = acc[t][u][3] = ms.b0[8 * u + 2 * c + 1];
+        }
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl)
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const uint32_t a[4] = {xs[(16 * t + g) * kXStride + 8 * sl + c],
+                                   xs[(16 * t + g + 8) * kXStride + 8 * sl + c],
+                                   xs[(16 * t + g) * kXStride + 8 * sl + 4 + c],
+                                   xs[(16 * t + g + 8) * kXStride + 8 * sl + 4 + c]};
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+                mma16816<kPrec>(acc[t][u], a, ms.w0[(8 * u + g) * kW0Stride + 8 * sl + c],
+                                ms.w0[(8 * u + g) * kW0Stride + 8 * sl + 4 + c]);
+        }
+    float acc2[2][2][4];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        uint32_t a[4];
+        relu_pack<kPrec>(acc[t][0], acc[t][1], a);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            acc2[t][u][0] = acc2[t][u][2] = ms.b1[8 * u + 2 * c];
+            acc2[t][u][1] = acc2[t][u][3] = ms.b1[8 * u + 2 * c + 1];
+            mma16816<kPrec>(acc2[t][u], a, ms.w1[(8 * u + g) * kW1Stride + c], ms.w1[(8 * u + g) * kW1Stride + 4 + c]);
+        }
+    }
+    float acc3[2][4];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        uint32_t a[4];
+        relu_pack<kPrec>(acc2[t][0], acc2[t][1], a);
+        acc3[t][0] = acc3[t][2] = ms.b2[2 * c];
+        acc3[t][1] = acc3[t][3] = ms.b2[2 * c + 1];
+        mma16816<kPrec>(acc3[t], a, ms.w2[g * kW1Stride + c], ms.w2[g * kW1Stride + 4 + c]);
+    }
+    // the 32 x 3 outputs go back to their pixels through shared memory
+    __syncwarp();
+    float *os = reinterpret_cast<float *>(xs);
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+        if (c < 2) {
+            os[(16 * t + g) * 4 + 2 * c] = acc3[t][0];
+            os[(16 * t + g) * 4 + 2 * c + 1] = acc3[t][1];
+            os[(16 * t + g + 8) * 4 + 2 * c] = acc3[t][2];
+            os[(16 * t + g + 8) * 4 + 2 * c + 1] = acc3[t][3];
+        }
+    __syncwarp();
+    out[0] = os[lane * 4 + 0];
+    out[1] = os[lane * 4 + 1];
+    out[2] = os[lane * 4 + 2];
+    __syncwarp();
+}
+
 __device__ __forceinline__ void pixel_of_thread(int &i, int &j)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -93,27 +265,32 @@ __device__ __forceinline__ void pixel_of_thread(int &i, int &j)
     j = blockIdx.y * kTileH + (warp >> 1) * 4 + (lane >> 3);
 }
 
-template <int kStorage>   // 0: uint8 block-sparse, 1: float32 dense
+template <int kStorage, int kPrec>   // storage 0: uint8 block-sparse, 1: float32 dense;
+                                     // precision 0: FP32, 1: FP16, 2: BF16 (uint8 storage only)
 __global__ void __launch_bounds__(kThreads) render_kernel(const __grid_constant__ RenderParams P)
 {
-    __shared__ float wsm[kMlpParams];
-    for (int t = threadIdx.x; t < kMlpParams; t += kThreads) wsm[t] = __ldg(P.mlp + t);
+    __shared__ float wsm[kPrec == 0 ? kMlpParams : 1];
+    __shared__ MlpTC mtc[1];
+    if constexpr (kPrec == 0) {
+        for (int t = threadIdx.x; t < kMlpParams; t += kThreads) wsm[t] = __ldg(P.mlp + t);
+    } else {
+        mlp_tc_load<kPrec>(mtc[0], P.mlp);
+    }
     __syncthreads();
 
     int i, j;
     pixel_of_thread(i, j);
     const int cl = blockIdx.z;
     const bool inside = (i < P.W) && (j < P.H);
-    int neval = 0, napp = 0, nlat = 0;
+    int neval = 0, napp = 0, nlat = 0, term = 0;
+    float T = 1.0f, cd[3] = {0.0f, 0.0f, 0.0f}, F[4] = {0.0f, 0.0f, 0.0f, 0.0f}, d[3] = {0.0f, 0.0f, 1.0f};
     if (inside) {
         const float *cam = P.cams.m[cl];
-        float o[3], d[3];
+        float o[3];
         ray_f32(cam, i, j, o, d);
         Walker wk;
         wk.init(o, d, P.step);
         nlat = wk.nlat;
-        float T = 1.0f, cd[3] = {0.0f, 0.0f, 0.0f}, F[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        int term = 0;
         int run_end = 0;
         for (;;) {
             if (wk.k >= run_end && !wk.next_run(P.occ, run_end)) break;
@@ -121,7 +298,7 @@ __global__ void __launch_bounds__(kThreads) render_kernel(const __grid_constant_
             wk.position(wk.k, p0, p1, p2);
             float dens, app[7];
             Taps tp;
-            if (kStorage == 0) {
+            if constexpr (kStorage == 0) {
                 gather_u8(P.fv, p0, p1, p2, tp);
                 dens = density_u8(tp);
             } else {
@@ -137,7 +314,10 @@ __global__ void __launch_bounds__(kThreads) render_kernel(const __grid_constant_
             ++neval;
             if (alpha > 0.0f) {
                 ++napp;
-                if (kStorage == 0) appearance_u8(tp, app);
+                if constexpr (kStorage == 0) {
+                    if constexpr (kPrec == 0) appearance_u8(tp, app);
+                    else appearance_lp<kPrec>(tp, app);
+                }
                 const float wgt = alpha * T;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) cd[c] = fmaf(wgt, sigmoid_f(app[c]), cd[c]);
@@ -148,8 +328,14 @@ __global__ void __launch_bounds__(kThreads) render_kernel(const __grid_constant_
             }
             ++wk.k;
         }
-        float h[3];
-        mlp_f32(wsm, cd, F, d, h);
+    }
+    float h[3];
+    if constexpr (kPrec == 0) {
+        if (inside) mlp_f32(wsm, cd, F, d, h);
+    } else {
+        mlp_tc<kPrec>(mtc[0], cd, F, d, h);     // whole warp, tensor cores
+    }
+    if (inside) {
         const size_t pix = ((size_t)(P.cam0 + cl) * P.H + j) * P.W + i;
         P.out[pix * 3 + 0] = cd[0] + h[0];
         P.out[pix * 3 + 1] = cd[1] + h[1];
