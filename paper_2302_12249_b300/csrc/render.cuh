@@ -96,12 +96,15 @@ __device__ __forceinline__ void mlp_f32(const float *w, const float cd[3], const
 
 constexpr int kW0Stride = 28, kW1Stride = 12, kXStride = 28;   // 32-bit words per row (padded)
 
+// BF16 keeps only 8 significant bits, so in that mode every operand is carried as an unevaluated
+// sum hi + lo of two bfloat16 values and each product takes three tensor-core passes
+// (hi*hi + lo*hi + hi*lo, all accumulated in FP32); FP16 uses one pass.
 struct MlpTC {
-    uint32_t w0[16 * kW0Stride];   // W0^T [n][k], k < 48, 16-bit pairs
-    uint32_t w1[16 * kW1Stride];   // W1^T [n][k], k < 16
-    uint32_t w2[8 * kW1Stride];    // W2^T [n][k], n < 3 used
+    uint32_t w0[2][16 * kW0Stride];   // W0^T [n][k], k < 48, 16-bit pairs; [1]: BF16 low parts
+    uint32_t w1[2][16 * kW1Stride];   // W1^T [n][k], k < 16
+    uint32_t w2[2][8 * kW1Stride];    // W2^T [n][k], n < 3 used
     float b0[16], b1[16], b2[8];
-    uint32_t x[kThreads / 32][32 * kXStride];   // per-warp input rows
+    uint32_t x[2][kThreads / 32][32 * kXStride];   // per-warp input rows; [1]: BF16 low parts
 };
 
 template <int kPrec>
@@ -116,6 +119,18 @@ __device__ __forceinline__ uint32_t pack16(float lo, float hi)
         memcpy(&u, &h, 4);
     }
     return u;
+}
+
+// low part of a BF16 split: lo = bf16(v - float(bf16(v)))
+__device__ __forceinline__ float bf16_rest(float v)
+{
+    return v - __bfloat162float(__float2bfloat16_rn(v));
+}
+
+template <int kPrec>
+__device__ __forceinline__ uint32_t pack16_lo(float lo, float hi)
+{
+    return pack16<kPrec>(bf16_rest(lo), bf16_rest(hi));
 }
 
 template <int kPrec>
@@ -142,16 +157,20 @@ __device__ __forceinline__ void mlp_tc_load(MlpTC &ms, const float *w)
         const int n = e / 24, kk = 2 * (e % 24);
         const float a = kk < 34 ? __ldg(W0 + kk * 16 + n) : 0.0f;
         const float b = kk + 1 < 34 ? __ldg(W0 + (kk + 1) * 16 + n) : 0.0f;
-        ms.w0[n * kW0Stride + e % 24] = pack16<kPrec>(a, b);
+        ms.w0[0][n * kW0Stride + e % 24] = pack16<kPrec>(a, b);
+        if (kPrec == 2) ms.w0[1][n * kW0Stride + e % 24] = pack16_lo<kPrec>(a, b);
     }
     for (int e = threadIdx.x; e < 16 * 8; e += kThreads) {
         const int n = e / 8, kk = 2 * (e % 8);
-        ms.w1[n * kW1Stride + e % 8] = pack16<kPrec>(__ldg(W1 + kk * 16 + n), __ldg(W1 + (kk + 1) * 16 + n));
+        const float a = __ldg(W1 + kk * 16 + n), b = __ldg(W1 + (kk + 1) * 16 + n);
+        ms.w1[0][n * kW1Stride + e % 8] = pack16<kPrec>(a, b);
+        if (kPrec == 2) ms.w1[1][n * kW1Stride + e % 8] = pack16_lo<kPrec>(a, b);
     }
     for (int e = threadIdx.x; e < 8 * 8; e += kThreads) {
         const int n = e / 8, kk = 2 * (e % 8);
         const float a = n < 3 ? __ldg(W2 + kk * 3 + n) : 0.0f, b = n < 3 ? __ldg(W2 + (kk + 1) * 3 + n) : 0.0f;
-        ms.w2[n * kW1Stride + e % 8] = pack16<kPrec>(a, b);
+        ms.w2[0][n * kW1Stride + e % 8] = pack16<kPrec>(a, b);
+        if (kPrec == 2) ms.w2[1][n * kW1Stride + e % 8] = pack16_lo<kPrec>(a, b);
     }
     for (int e = threadIdx.x; e < 16; e += kThreads) {
         ms.b0[e] = __ldg(B0 + e);
@@ -161,12 +180,27 @@ __device__ __forceinline__ void mlp_tc_load(MlpTC &ms, const float *w)
 }
 
 template <int kPrec>
-__device__ __forceinline__ void relu_pack(const float c0[4], const float c1[4], uint32_t a[4])
+__device__ __forceinline__ void relu_pack(const float c0[4], const float c1[4], uint32_t a[4], uint32_t al[4])
 {
-    a[0] = pack16<kPrec>(fmaxf(c0[0], 0.0f), fmaxf(c0[1], 0.0f));
-    a[1] = pack16<kPrec>(fmaxf(c0[2], 0.0f), fmaxf(c0[3], 0.0f));
-    a[2] = pack16<kPrec>(fmaxf(c1[0], 0.0f), fmaxf(c1[1], 0.0f));
-    a[3] = pack16<kPrec>(fmaxf(c1[2], 0.0f), fmaxf(c1[3], 0.0f));
+    const float v[8] = {fmaxf(c0[0], 0.0f), fmaxf(c0[1], 0.0f), fmaxf(c0[2], 0.0f), fmaxf(c0[3], 0.0f),
+                        fmaxf(c1[0], 0.0f), fmaxf(c1[1], 0.0f), fmaxf(c1[2], 0.0f), fmaxf(c1[3], 0.0f)};
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        a[r] = pack16<kPrec>(v[2 * r], v[2 * r + 1]);
+        if (kPrec == 2) al[r] = pack16_lo<kPrec>(v[2 * r], v[2 * r + 1]);
+    }
+}
+
+// D += A B, with the BF16 split when kPrec == 2 (a/b: high parts, al/bl: low parts)
+template <int kPrec>
+__device__ __forceinline__ void mma_acc(float d[4], const uint32_t a[4], const uint32_t al[4], uint32_t b0,
+                                        uint32_t b1, uint32_t bl0, uint32_t bl1)
+{
+    mma16816<kPrec>(d, a, b0, b1);
+    if constexpr (kPrec == 2) {
+        mma16816<kPrec>(d, al, b0, b1);
+        mma16816<kPrec>(d, a, bl0, bl1);
+    }
 }
 
 // All 32 lanes of the warp call this together (lanes without a pixel pass zeros).
@@ -175,7 +209,8 @@ __device__ __forceinline__ void mlp_tc(MlpTC &ms, const float cd[3], const float
                                        float out[3])
 {
     const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
-    uint32_t *xs = ms.x[threadIdx.x >> 5];
+    uint32_t *xs = ms.x[0][threadIdx.x >> 5];
+    uint32_t *xl = ms.x[1][threadIdx.x >> 5];
     float x[48];
     x[0] = cd[0]; x[1] = cd[1]; x[2] = cd[2];
     x[3] = f[0]; x[4] = f[1]; x[5] = f[2]; x[6] = f[3];
@@ -195,7 +230,10 @@ __device__ __forceinline__ void mlp_tc(MlpTC &ms, const float cd[3], const float
     for (int k = 34; k < 48; ++k) x[k] = 0.0f;
     __syncwarp();
 #pragma unroll
-    for (int j = 0; j < 24; ++j) xs[lane * kXStride + j] = pack16<kPrec>(x[2 * j], x[2 * j + 1]);
+    for (int j = 0; j < 24; ++j) {
+        xs[lane * kXStride + j] = pack16<kPrec>(x[2 * j], x[2 * j + 1]);
+        if (kPrec == 2) xl[lane * kXStride + j] = pack16_lo<kPrec>(x[2 * j], x[2 * j + 1]);
+    }
     __syncwarp();
 
     float acc[2][2][4];
@@ -210,35 +248,38 @@ __device__ __forceinline__ void mlp_tc(MlpTC &ms, const float cd[3], const float
     for (int sl = 0; sl < 3; ++sl)
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
-            const uint32_t a[4] = {xs[(16 * t + g) * kXStride + 8 * sl + c],
-                                   xs[(16 * t + g + 8) * kXStride + 8 * sl + c],
-                                   xs[(16 * t + g) * kXStride + 8 * sl + 4 + c],
-                                   xs[(16 * t + g + 8) * kXStride + 8 * sl + 4 + c]};
+            const int r0 = (16 * t + g) * kXStride + 8 * sl + c, r1 = r0 + 8 * kXStride;
+            const uint32_t a[4] = {xs[r0], xs[r1], xs[r0 + 4], xs[r1 + 4]};
+            uint32_t al[4] = {0u, 0u, 0u, 0u};
+            if (kPrec == 2) { al[0] = xl[r0]; al[1] = xl[r1]; al[2] = xl[r0 + 4]; al[3] = xl[r1 + 4]; }
 #pragma unroll
-            for (int u = 0; u < 2; ++u)
-                mma16816<kPrec>(acc[t][u], a, ms.w0[(8 * u + g) * kW0Stride + 8 * sl + c],
-                                ms.w0[(8 * u + g) * kW0Stride + 8 * sl + 4 + c]);
+            for (int u = 0; u < 2; ++u) {
+                const int wi = (8 * u + g) * kW0Stride + 8 * sl + c;
+                mma_acc<kPrec>(acc[t][u], a, al, ms.w0[0][wi], ms.w0[0][wi + 4], ms.w0[1][wi], ms.w0[1][wi + 4]);
+            }
         }
     float acc2[2][2][4];
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
-        uint32_t a[4];
-        relu_pack<kPrec>(acc[t][0], acc[t][1], a);
+        uint32_t a[4], al[4];
+        relu_pack<kPrec>(acc[t][0], acc[t][1], a, al);
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             acc2[t][u][0] = acc2[t][u][2] = ms.b1[8 * u + 2 * c];
             acc2[t][u][1] = acc2[t][u][3] = ms.b1[8 * u + 2 * c + 1];
-            mma16816<kPrec>(acc2[t][u], a, ms.w1[(8 * u + g) * kW1Stride + c], ms.w1[(8 * u + g) * kW1Stride + 4 + c]);
+            const int wi = (8 * u + g) * kW1Stride + c;
+            mma_acc<kPrec>(acc2[t][u], a, al, ms.w1[0][wi], ms.w1[0][wi + 4], ms.w1[1][wi], ms.w1[1][wi + 4]);
         }
     }
     float acc3[2][4];
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
-        uint32_t a[4];
-        relu_pack<kPrec>(acc2[t][0], acc2[t][1], a);
+        uint32_t a[4], al[4];
+        relu_pack<kPrec>(acc2[t][0], acc2[t][1], a, al);
         acc3[t][0] = acc3[t][2] = ms.b2[2 * c];
         acc3[t][1] = acc3[t][3] = ms.b2[2 * c + 1];
-        mma16816<kPrec>(acc3[t], a, ms.w2[g * kW1Stride + c], ms.w2[g * kW1Stride + 4 + c]);
+        const int wi = g * kW1Stride + c;
+        mma_acc<kPrec>(acc3[t], a, al, ms.w2[0][wi], ms.w2[0][wi + 4], ms.w2[1][wi], ms.w2[1][wi + 4]);
     }
     // the 32 x 3 outputs go back to their pixels through shared memory
     __syncwarp();

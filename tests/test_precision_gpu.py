@@ -1,0 +1,112 @@
+"""GPU accuracy of the precision form (FP16 / BF16 appearance arithmetic and tensor-core MLP)
+against the FP64 oracle: at most 2e-3 per channel and PSNR above 50 dB.  Density, opacity,
+transmittance, compositing and the traversal stay in FP32, so they must match the FP32 path."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2302_12249_b300 import merf, synth
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+CHANNEL_TOL = 2e-3
+PSNR_MIN = 50.0
+PRECS = [pytest.param(merf.PREC_FP16, id="fp16"), pytest.param(merf.PREC_BF16, id="bf16")]
+
+
+def _render(gs, cams, W, H, step, prec):
+    n = cams.shape[0]
+    aux = torch.zeros((n, H, W, merf.AUX_SIZE), dtype=torch.float32, device="cuda")
+    out = merf.render(gs, cams, W, H, step, precision=prec, aux=aux)
+    torch.cuda.synchronize()
+    return out.reshape(-1, 3).double().cpu().numpy(), aux.reshape(-1, merf.AUX_SIZE).double().cpu().numpy()
+
+
+def _closest(rgb, lo, hi):
+    """Per pixel, the oracle variant (termination threshold -0.1 % / +0.1 %) nearer to rgb."""
+    e_lo = np.abs(rgb - lo[:, 0:3]).max(axis=1)
+    e_hi = np.abs(rgb - hi[:, 0:3]).max(axis=1)
+    return np.where((e_lo <= e_hi)[:, None], lo[:, 0:3], hi[:, 0:3])
+
+
+def _psnr(a, b):
+    mse = float(np.mean((a - b) ** 2))
+    return math.inf if mse == 0 else 10.0 * math.log10(1.0 / mse)
+
+
+@pytest.fixture(scope="module")
+def tiny(tiny_scene):
+    return merf.Scene(tiny_scene), oracle.OracleScene(tiny_scene)
+
+
+@pytest.fixture(scope="module")
+def paper():
+    sc = synth.make_scene("paper")
+    return merf.Scene(sc), oracle.OracleScene(sc)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_tiny_image_error_bounds(tiny, prec):
+    gs, osc = tiny
+    cams = synth.config_cameras("tiny", W=64, H=64, n=2)
+    rgb, _ = _render(gs, cams, 64, 64, 1 / 64, prec)
+    lo, hi = parity.oracle_rgb(osc, cams, 64, 64, 1 / 64)
+    ref = _closest(rgb, lo, hi)
+    assert np.abs(rgb - ref).max() <= CHANNEL_TOL
+    assert _psnr(rgb, ref) > PSNR_MIN
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_paper_scale_sampled_error_bounds(paper, prec):
+    gs, osc = paper
+    cams = synth.config_cameras("paper")
+    W, H = 1920, 1080
+    out = merf.render(gs, cams, W, H, 1 / 256, precision=prec)
+    torch.cuda.synchronize()
+    pix, lin = parity.pick_pixels(cams.shape[0], W, H, 3000, seed=1)
+    rgb = out.reshape(-1, 3)[torch.from_numpy(lin).cuda()].double().cpu().numpy()
+    lo, hi = parity.oracle_rgb(osc, cams, W, H, 1 / 256, pix=pix)
+    ref = _closest(rgb, lo, hi)
+    assert np.abs(rgb - ref).max() <= CHANNEL_TOL
+    assert _psnr(rgb, ref) > PSNR_MIN
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_density_and_traversal_unchanged(tiny, prec):
+    """Only appearance and the MLP change precision: evaluated samples, opacity and hence
+    transmittance are those of the FP32 path."""
+    gs, _ = tiny
+    cams = synth.config_cameras("tiny", W=48, H=40)
+    _, a32 = _render(gs, cams, 48, 40, 1 / 64, merf.PREC_FP32)
+    _, alp = _render(gs, cams, 48, 40, 1 / 64, prec)
+    np.testing.assert_array_equal(alp[:, merf.AUX_NEVAL], a32[:, merf.AUX_NEVAL])
+    np.testing.assert_allclose(alp[:, merf.AUX_T], a32[:, merf.AUX_T], rtol=0, atol=1e-6)
+
+
+@pytest.mark.parametrize("prec,tol", [pytest.param(merf.PREC_FP16, 1e-3, id="fp16"),
+                                      pytest.param(merf.PREC_BF16, 2e-3, id="bf16")])
+def test_tensor_core_mlp_against_oracle_mlp(tiny, tiny_scene, prec, tol):
+    """h = C - C_d from the kernel against the oracle's FP64 MLP on the kernel's own C_d, F."""
+    gs, _ = tiny
+    W, H = 40, 24
+    cams = synth.config_cameras("tiny", W=W, H=H)
+    rgb, aux = _render(gs, cams, W, H, 1 / 64, prec)
+    worst = 0.0
+    for r in range(0, W * H, 7):
+        _, d = oracle.ray(cams[0], r % W, r // W)
+        h = oracle.mlp(tiny_scene.mlp, aux[r, merf.AUX_CD:merf.AUX_CD + 3], aux[r, merf.AUX_F:merf.AUX_F + 4], d)
+        worst = max(worst, float(np.abs(rgb[r] - aux[r, merf.AUX_CD:merf.AUX_CD + 3] - h).max()))
+    assert worst <= tol, worst
+
+
+def test_reduced_precision_rejected_for_dense_storage():
+    sc = synth.make_scene("dense128")
+    gs = merf.Scene(sc)
+    cams = synth.config_cameras("dense128", W=8, H=8, n=1)
+    with pytest.raises(merf.MerfError) as e:
+        merf.render(gs, cams, 8, 8, sc.cfg.step, precision=merf.PREC_FP16)
+    assert e.value.status == merf.ERR_UNSUPPORTED
