@@ -119,6 +119,46 @@ def _cpu_baseline(scene, cams, seconds: float = 12.0):
             "sample": f"{rays} random pixel rays of the 8 x 1920x1080 frames ({dt:.1f} s, FP64, {threads} threads)"}
 
 
+def _precision_form(gs, scene, n_cams=64, steps=2, n_pix=2000):
+    """Precision form: the same scene rendered from 64 ring cameras at 1920x1080 in FP32, FP16 and
+    BF16 (uint8 features, appearance arithmetic and deferred MLP in 16 bits on tensor cores,
+    density/transmittance/compositing in FP32).  Time per step and, on sampled pixels, the
+    error against the FP64 oracle (max |dRGB| per channel and PSNR)."""
+    import torch
+    import oracle
+    from paper_2302_12249_b300 import merf, synth
+    cams = synth.ring_cameras(n_cams, W_IMG, H_IMG, radius=1.5, seed=synth.SEED_CAMERA + 1)
+    out = torch.empty((n_cams, H_IMG, W_IMG, 3), dtype=torch.float32, device="cuda")
+    rng = np.random.default_rng(99)
+    pix = np.stack([rng.integers(0, n_cams, n_pix), rng.integers(0, W_IMG, n_pix),
+                    rng.integers(0, H_IMG, n_pix)], 1).astype(np.int32)
+    lin = torch.from_numpy((pix[:, 0].astype(np.int64) * H_IMG + pix[:, 2]) * W_IMG + pix[:, 1]).cuda()
+    osc = oracle.OracleScene(scene)
+    lo = oracle.render(osc, cams, W_IMG, H_IMG, STEP, pix=pix, t_term=2e-4 * 0.999)[:, 0:3]
+    hi = oracle.render(osc, cams, W_IMG, H_IMG, STEP, pix=pix, t_term=2e-4 * 1.001)[:, 0:3]
+    res = {}
+    for name, prec in (("fp32", merf.PREC_FP32), ("fp16", merf.PREC_FP16), ("bf16", merf.PREC_BF16)):
+        merf.render(gs, cams, W_IMG, H_IMG, STEP, out=out, precision=prec)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            merf.render(gs, cams, W_IMG, H_IMG, STEP, out=out, precision=prec)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        rgb = out.reshape(-1, 3)[lin].double().cpu().numpy()
+        e_lo, e_hi = np.abs(rgb - lo).max(axis=1), np.abs(rgb - hi).max(axis=1)
+        ref = np.where((e_lo <= e_hi)[:, None], lo, hi)
+        mse = float(np.mean((rgb - ref) ** 2))
+        res[name] = {"ms_per_step": ms, "mrays_per_s": n_cams * W_IMG * H_IMG / (ms / 1e3) / 1e6,
+                     "max_abs_err": float(np.abs(rgb - ref).max()),
+                     "psnr_db": (10 * math.log10(1.0 / mse)) if mse > 0 else None}
+    res["workload"] = f"{n_cams} ring cameras x 1920x1080, {steps} timed steps each; error on {n_pix} sampled pixels"
+    res["fp16_speedup_vs_fp32"] = res["fp32"]["ms_per_step"] / res["fp16"]["ms_per_step"]
+    return res
+
+
 def run_reference(args):
     dist, rank, world, _ = _dist()
     if rank != 0:
@@ -233,6 +273,9 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = _cpu_baseline(scene, cams)
+    precision = None
+    if rank == 0 and world == 1 and not args.no_precision:
+        precision = _precision_form(gs, scene)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -250,12 +293,14 @@ def run_ours(args):
                          "algorithmic_bytes_per_ray": alg_bytes / c[merf.CNT_RAYS]},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": None,
-                             "kernel": "render_kernel<0>", "kernel_ms": mean_kern_ms,
+                             "kernel": "render_kernel<0,0> (FP32)", "kernel_ms": mean_kern_ms,
                              "peak_source": peak_src},
                 "gpu_launches": args.steps,
                 "e2e": e2e, "clocks": ck}
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        if precision is not None:
+            line["precision_form"] = precision
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -271,6 +316,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cams", type=int, default=N_CAMS, help="cameras per step (profiling cases)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-output measurement (profiling)")
+    ap.add_argument("--no-precision", action="store_true", help="skip the FP16/BF16 comparison (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

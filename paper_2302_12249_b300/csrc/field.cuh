@@ -214,8 +214,31 @@ __device__ __forceinline__ __half2 magic_h2(uint2 v)
     return h;
 }
 
+// 16-bit weights of the 20 taps, both halves of each pair equal (converted once per sample)
+template <int kPrec>
+struct LpWeights {
+    uint32_t w[20];
+};
+
+template <int kPrec>
+__device__ __forceinline__ void lp_weights(const Taps &t, LpWeights<kPrec> &lw)
+{
+#pragma unroll
+    for (int i = 0; i < 20; ++i) {
+        const float v = i < 8 ? grid_w(t, i) : plane_w(t, (i - 8) >> 2, (i - 8) & 3);
+        if constexpr (kPrec == 1) {
+            const __half2 h = __float2half2_rn(v);
+            memcpy(&lw.w[i], &h, 4);
+        } else {
+            const __nv_bfloat162 h = __float2bfloat162_rn(v);
+            memcpy(&lw.w[i], &h, 4);
+        }
+    }
+}
+
 template <int kPrec, int pair>   // kPrec 1: FP16, 2: BF16
-__device__ __forceinline__ float2 lp_pair(const Taps &t, const float w[20], float2 &first_v, float2 &first_p)
+__device__ __forceinline__ float2 lp_pair(const Taps &t, const LpWeights<kPrec> &lw, float2 &first_v,
+                                          float2 &first_p)
 {
     const __half2 mag = __float2half2_rn(1024.0f);
     __half2 first[4];
@@ -227,8 +250,11 @@ __device__ __forceinline__ float2 lp_pair(const Taps &t, const float w[20], floa
             const int b = s == 0 ? 0 : 4 + 4 * s, n = s == 0 ? 8 : 4;
             first[s] = magic_h2<pair>(t.v[b]);
 #pragma unroll
-            for (int i = 1; i < n; ++i)
-                acc = __hfma2(__float2half2_rn(w[b + i]), __hsub2(magic_h2<pair>(t.v[b + i]), first[s]), acc);
+            for (int i = 1; i < n; ++i) {
+                __half2 w;
+                memcpy(&w, &lw.w[b + i], 4);
+                acc = __hfma2(w, __hsub2(magic_h2<pair>(t.v[b + i]), first[s]), acc);
+            }
         }
         corr = __half22float2(acc);
     } else {
@@ -239,9 +265,12 @@ __device__ __forceinline__ float2 lp_pair(const Taps &t, const float w[20], floa
             first[s] = magic_h2<pair>(t.v[b]);
 #pragma unroll
             for (int i = 1; i < n; ++i) {
+                __nv_bfloat162 w;
+                memcpy(&w, &lw.w[b + i], 4);
+                // the difference is an exact integer in [-255, 255], exact in bfloat16 too
                 const __nv_bfloat162 dd =
                     __float22bfloat162_rn(__half22float2(__hsub2(magic_h2<pair>(t.v[b + i]), first[s])));
-                acc = __hfma2(__float2bfloat162_rn(w[b + i]), dd, acc);
+                acc = __hfma2(w, dd, acc);
             }
         }
         corr = __bfloat1622float2(acc);
@@ -255,22 +284,17 @@ __device__ __forceinline__ float2 lp_pair(const Taps &t, const float w[20], floa
 template <int kPrec>
 __device__ __forceinline__ void appearance_lp(const Taps &t, float out[7])
 {
-    float w[20];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) w[c] = grid_w(t, c);
-#pragma unroll
-    for (int q = 0; q < 3; ++q)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) w[8 + 4 * q + c] = plane_w(t, q, c);
+    LpWeights<kPrec> lw;
+    lp_weights<kPrec>(t, lw);
     float K[8];
     float2 fv, fp, cr;
-    cr = lp_pair<kPrec, 0>(t, w, fv, fp);
+    cr = lp_pair<kPrec, 0>(t, lw, fv, fp);
     K[0] = fmaf(t.wv, fv.x, fp.x) + cr.x; K[1] = fmaf(t.wv, fv.y, fp.y) + cr.y;
-    cr = lp_pair<kPrec, 1>(t, w, fv, fp);
+    cr = lp_pair<kPrec, 1>(t, lw, fv, fp);
     K[2] = fmaf(t.wv, fv.x, fp.x) + cr.x; K[3] = K[2];
-    cr = lp_pair<kPrec, 2>(t, w, fv, fp);
+    cr = lp_pair<kPrec, 2>(t, lw, fv, fp);
     K[4] = fmaf(t.wv, fv.x, fp.x) + cr.x; K[5] = fmaf(t.wv, fv.y, fp.y) + cr.y;
-    cr = lp_pair<kPrec, 3>(t, w, fv, fp);
+    cr = lp_pair<kPrec, 3>(t, lw, fv, fp);
     K[6] = fmaf(t.wv, fv.x, fp.x) + cr.x; K[7] = fmaf(t.wv, fv.y, fp.y) + cr.y;
     const float off = 7.0f * (t.wv + 3.0f), sc = 14.0f / 255.0f;
     out[0] = K[0] * sc - off;   // channel 1
