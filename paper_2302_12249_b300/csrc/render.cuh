@@ -306,100 +306,139 @@ __device__ __forceinline__ void pixel_of_thread(int &i, int &j)
     j = blockIdx.y * kTileH + (warp >> 1) * 4 + (lane >> 3);
 }
 
+// Result of marching one ray (before the deferred MLP).
+struct RayState {
+    float cd[3], F[4], T, d[3];
+    int nlat, neval, napp, term;
+};
+
+// March one pixel ray: traversal, gather, activations and front-to-back compositing.
+template <int kStorage, int kPrec>
+__device__ __forceinline__ void march_ray(const FieldView &fv, const OccView &occ, const float *cam, int i, int j,
+                                          float step, float t_term, int early_term, RayState &r)
+{
+    float o[3];
+    ray_f32(cam, i, j, o, r.d);
+    Walker wk;
+    wk.init(o, r.d, step);
+    r.nlat = wk.nlat;
+    int run_end = 0;
+    for (;;) {
+        if (wk.k >= run_end && !wk.next_run(occ, run_end)) break;
+        float p0, p1, p2;
+        wk.position(wk.k, p0, p1, p2);
+        float dens, app[7];
+        Taps tp;
+        if constexpr (kStorage == 0) {
+            gather_u8(fv, p0, p1, p2, tp);
+            dens = density_u8(tp);
+        } else {
+            float all[8];
+            field_f32(fv, p0, p1, p2, all);
+            dens = all[0];
+#pragma unroll
+            for (int c = 0; c < 7; ++c) app[c] = all[1 + c];
+        }
+        const float tau = __expf(dens);
+        const float dw = wk.delta_world(wk.k);
+        const float alpha = 1.0f - __expf(-tau * dw);
+        ++r.neval;
+        if (alpha > 0.0f) {
+            ++r.napp;
+            if constexpr (kStorage == 0) {
+                if constexpr (kPrec == 0) appearance_u8(tp, app);
+                else appearance_lp<kPrec>(tp, app);
+            }
+            const float wgt = alpha * r.T;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) r.cd[c] = fmaf(wgt, sigmoid_f(app[c]), r.cd[c]);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) r.F[c] = fmaf(wgt, sigmoid_f(app[3 + c]), r.F[c]);
+            r.T = r.T * (1.0f - alpha);
+            if (early_term && r.T < t_term) { r.term = 1; break; }
+        }
+        ++wk.k;
+    }
+}
+
+__device__ __forceinline__ void ray_state_init(RayState &r)
+{
+    r.cd[0] = r.cd[1] = r.cd[2] = 0.0f;
+    r.F[0] = r.F[1] = r.F[2] = r.F[3] = 0.0f;
+    r.T = 1.0f;
+    r.d[0] = 0.0f; r.d[1] = 0.0f; r.d[2] = 1.0f;
+    r.nlat = r.neval = r.napp = r.term = 0;
+}
+
+// Shared-memory weights of the deferred MLP for one precision.
+template <int kPrec>
+struct MlpSmem;
+template <>
+struct MlpSmem<0> {
+    float w[kMlpParams];
+    __device__ __forceinline__ void load(const float *mlp)
+    {
+        for (int t = threadIdx.x; t < kMlpParams; t += kThreads) w[t] = __ldg(mlp + t);
+    }
+};
+template <int kPrec>
+struct MlpSmem {
+    MlpTC tc;
+    __device__ __forceinline__ void load(const float *mlp) { mlp_tc_load<kPrec>(tc, mlp); }
+};
+
+// h(C_d, F, d) for every thread of the warp (all lanes call; `live` lanes own a pixel).
+template <int kPrec>
+__device__ __forceinline__ void deferred_mlp(MlpSmem<kPrec> &ms, const RayState &r, bool live, float h[3])
+{
+    if constexpr (kPrec == 0) {
+        if (live) mlp_f32(ms.w, r.cd, r.F, r.d, h);
+    } else {
+        mlp_tc<kPrec>(ms.tc, r.cd, r.F, r.d, h);     // whole warp, tensor cores
+    }
+}
+
 template <int kStorage, int kPrec>   // storage 0: uint8 block-sparse, 1: float32 dense;
                                      // precision 0: FP32, 1: FP16, 2: BF16 (uint8 storage only)
-__global__ void __launch_bounds__(kThreads) render_kernel(const __grid_constant__ RenderParams P)
+__global__ void __launch_bounds__(kThreads, 4) render_kernel(const __grid_constant__ RenderParams P)
 {
-    __shared__ float wsm[kPrec == 0 ? kMlpParams : 1];
-    __shared__ MlpTC mtc[1];
-    if constexpr (kPrec == 0) {
-        for (int t = threadIdx.x; t < kMlpParams; t += kThreads) wsm[t] = __ldg(P.mlp + t);
-    } else {
-        mlp_tc_load<kPrec>(mtc[0], P.mlp);
-    }
+    __shared__ MlpSmem<kPrec> ms;
+    ms.load(P.mlp);
     __syncthreads();
 
     int i, j;
     pixel_of_thread(i, j);
     const int cl = blockIdx.z;
     const bool inside = (i < P.W) && (j < P.H);
-    int neval = 0, napp = 0, nlat = 0, term = 0;
-    float T = 1.0f, cd[3] = {0.0f, 0.0f, 0.0f}, F[4] = {0.0f, 0.0f, 0.0f, 0.0f}, d[3] = {0.0f, 0.0f, 1.0f};
-    if (inside) {
-        const float *cam = P.cams.m[cl];
-        float o[3];
-        ray_f32(cam, i, j, o, d);
-        Walker wk;
-        wk.init(o, d, P.step);
-        nlat = wk.nlat;
-        int run_end = 0;
-        for (;;) {
-            if (wk.k >= run_end && !wk.next_run(P.occ, run_end)) break;
-            float p0, p1, p2;
-            wk.position(wk.k, p0, p1, p2);
-            float dens, app[7];
-            Taps tp;
-            if constexpr (kStorage == 0) {
-                gather_u8(P.fv, p0, p1, p2, tp);
-                dens = density_u8(tp);
-            } else {
-                float all[8];
-                field_f32(P.fv, p0, p1, p2, all);
-                dens = all[0];
-#pragma unroll
-                for (int c = 0; c < 7; ++c) app[c] = all[1 + c];
-            }
-            const float tau = __expf(dens);
-            const float dw = wk.delta_world(wk.k);
-            const float alpha = 1.0f - __expf(-tau * dw);
-            ++neval;
-            if (alpha > 0.0f) {
-                ++napp;
-                if constexpr (kStorage == 0) {
-                    if constexpr (kPrec == 0) appearance_u8(tp, app);
-                    else appearance_lp<kPrec>(tp, app);
-                }
-                const float wgt = alpha * T;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) cd[c] = fmaf(wgt, sigmoid_f(app[c]), cd[c]);
-#pragma unroll
-                for (int c = 0; c < 4; ++c) F[c] = fmaf(wgt, sigmoid_f(app[3 + c]), F[c]);
-                T = T * (1.0f - alpha);
-                if (P.early_term && T < P.t_term) { term = 1; break; }
-            }
-            ++wk.k;
-        }
-    }
+    RayState r;
+    ray_state_init(r);
+    if (inside) march_ray<kStorage, kPrec>(P.fv, P.occ, P.cams.m[cl], i, j, P.step, P.t_term, P.early_term, r);
     float h[3];
-    if constexpr (kPrec == 0) {
-        if (inside) mlp_f32(wsm, cd, F, d, h);
-    } else {
-        mlp_tc<kPrec>(mtc[0], cd, F, d, h);     // whole warp, tensor cores
-    }
+    deferred_mlp<kPrec>(ms, r, inside, h);
     if (inside) {
         const size_t pix = ((size_t)(P.cam0 + cl) * P.H + j) * P.W + i;
-        P.out[pix * 3 + 0] = cd[0] + h[0];
-        P.out[pix * 3 + 1] = cd[1] + h[1];
-        P.out[pix * 3 + 2] = cd[2] + h[2];
+        P.out[pix * 3 + 0] = r.cd[0] + h[0];
+        P.out[pix * 3 + 1] = r.cd[1] + h[1];
+        P.out[pix * 3 + 2] = r.cd[2] + h[2];
         if (P.aux) {
             float *a = P.aux + pix * kAuxSize;
-            a[0] = cd[0]; a[1] = cd[1]; a[2] = cd[2];
-            a[3] = F[0]; a[4] = F[1]; a[5] = F[2]; a[6] = F[3];
-            a[7] = T;
-            a[8] = (float)nlat; a[9] = (float)neval; a[10] = (float)napp; a[11] = (float)term;
+            a[0] = r.cd[0]; a[1] = r.cd[1]; a[2] = r.cd[2];
+            a[3] = r.F[0]; a[4] = r.F[1]; a[5] = r.F[2]; a[6] = r.F[3];
+            a[7] = r.T;
+            a[8] = (float)r.nlat; a[9] = (float)r.neval; a[10] = (float)r.napp; a[11] = (float)r.term;
         }
     }
     if (P.counters) {
-        unsigned long long r = inside ? 1ull : 0ull, l = nlat, e = neval, a = napp;
+        unsigned long long cr = inside ? 1ull : 0ull, l = r.nlat, e = r.neval, a = r.napp;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
-            r += __shfl_down_sync(0xffffffffu, r, off);
+            cr += __shfl_down_sync(0xffffffffu, cr, off);
             l += __shfl_down_sync(0xffffffffu, l, off);
             e += __shfl_down_sync(0xffffffffu, e, off);
             a += __shfl_down_sync(0xffffffffu, a, off);
         }
         if ((threadIdx.x & 31) == 0) {
-            atomicAdd(P.counters + 0, r);
+            atomicAdd(P.counters + 0, cr);
             atomicAdd(P.counters + 1, l);
             atomicAdd(P.counters + 2, e);
             atomicAdd(P.counters + 3, a);
