@@ -174,6 +174,63 @@ merf_status merf_trace(const merf_scene *scene, const merf_camera *cams, int n_c
                        int H, uint32_t *mask, int words, int32_t *n_lattice,
                        const merf_render_opts *opts, void *stream);
 
+/* ----------------------------------------------------------------------------------------
+ * Serving: a render server holding several resident scenes and batching requests of mixed
+ * scenes and resolutions continuously.  The paper renders one view at a time in a browser; this
+ * is the serving form built around its renderer (Sec. 5).
+ *
+ * A server thread admits submitted requests in arrival order when the request's output image
+ * fits in the free part of the server's device output pool (admission by memory), then packs
+ * pixel tiles (16 x 8) of all admitted requests -- oldest first, across scenes and resolutions --
+ * into iterations of at most max_tiles_per_iter tiles.  Each iteration is one launch of a captured
+ * CUDA graph: work-list upload, counter reset, and a persistent kernel whose CTAs take tiles from
+ * the list with an atomic counter.  Two iterations are kept in flight, so requests that arrive
+ * while the GPU is busy join the next iteration and their tiles share launches with the
+ * requests already running.  A finished request's image is copied to its host buffer on a copy
+ * stream; it completes when that copy has landed.  No device-side wait exists: every kernel
+ * terminates on its own once the tile list is exhausted. */
+typedef struct merf_server merf_server;
+
+typedef struct merf_server_opts {
+    size_t pool_bytes;            /* device output pool (admission limit), >= one request */
+    int32_t max_tiles_per_iter;   /* tiles of 16 x 8 pixels per iteration, 1 .. 65536 */
+    int32_t precision;            /* MERF_PREC_*, as in merf_render_opts */
+    float step;                   /* lattice step, as in merf_render_opts */
+    float t_term;                 /* early-termination threshold */
+    int32_t early_term;
+    int32_t reserved;             /* must be 0 */
+} merf_server_opts;
+
+typedef struct merf_server_stats {
+    unsigned long long submitted, completed, rays, iterations, tiles;
+    size_t pool_bytes, peak_pool_bytes;   /* pool size and its peak reservation */
+    int32_t peak_admitted;                /* most requests admitted at once */
+    int32_t reserved;
+} merf_server_stats;
+
+/* Create a server over n_scenes (1..8) scenes uploaded with merf_scene_upload (uint8 storage) on
+ * the current device; the scenes must outlive the server.  Allocates the output pool, the
+ * work-list buffers and two captured graphs, and starts the server thread. */
+merf_status merf_server_create(const merf_scene *const *scenes, int n_scenes, const merf_server_opts *opts,
+                               merf_server **out);
+
+/* Submit one request: render scene `scene` from camera *cam (host, copied) at W x H into h_out
+ * (host float32 [H][W][3], page-locked for the copy to be asynchronous; written when the request
+ * completes).  Returns at once with *req_id.  MERF_ERR_OOM if the image alone exceeds the pool. */
+merf_status merf_server_submit(merf_server *srv, int scene, const merf_camera *cam, int W, int H, float *h_out,
+                               uint64_t *req_id);
+
+/* Block until request req_id completes (or timeout_s elapses: MERF_ERR_TIMEOUT, the request
+ * stays pending and may be waited for again).  On completion *latency_s (may be NULL) receives
+ * the time from submission to the image being in host memory, and the request is released: wait
+ * once per request. */
+merf_status merf_server_wait(merf_server *srv, uint64_t req_id, double timeout_s, double *latency_s);
+
+merf_status merf_server_get_stats(merf_server *srv, merf_server_stats *out);
+
+/* Finish every submitted request, stop the thread and release the server (NULL is ignored). */
+void merf_server_destroy(merf_server *srv);
+
 /* Device-memory budget for merf_scene_upload* (bytes; 0 = unlimited, the default). */
 void merf_set_device_budget(size_t bytes);
 

@@ -13,14 +13,7 @@
 
 #include "merf.h"
 #include "render.cuh"
-
-struct merf_scene {
-    merf_scene_desc desc;
-    int device;
-    void *index_grid = nullptr, *atlas = nullptr, *planes = nullptr, *mlp = nullptr;
-    void *occ[MERF_MAX_OCC_LEVELS] = {};
-    size_t bytes = 0;
-};
+#include "scene.h"
 
 namespace {
 
@@ -45,13 +38,6 @@ merf_status ok()
 }
 
 bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
-
-int log2i(int v)
-{
-    int r = 0;
-    while ((1 << r) < v) ++r;
-    return r;
-}
 
 merf_status check_desc(const merf_scene_desc *d, int storage)
 {
@@ -207,26 +193,7 @@ merf::RenderParams make_params(const merf_scene *s, const merf_render_opts *o, i
 {
     merf::RenderParams P;
     memset(&P, 0, sizeof P);
-    const merf_scene_desc &d = s->desc;
-    P.fv.L = d.grid_res;
-    P.fv.R = d.plane_res;
-    if (d.storage == MERF_STORAGE_U8_SPARSE) {
-        P.fv.B = d.block_size;
-        P.fv.log2B = log2i(d.block_size);
-        P.fv.nb = d.grid_res / d.block_size;
-        P.fv.index_grid = (const int32_t *)s->index_grid;
-        P.fv.atlas = (const uint2 *)s->atlas;
-        P.fv.planes = (const uint2 *)s->planes;
-    } else {
-        P.fv.grid_f32 = (const float4 *)s->atlas;
-        P.fv.planes_f32 = (const float4 *)s->planes;
-    }
-    P.occ.n = d.n_occ_levels;
-    for (int l = 0; l < d.n_occ_levels; ++l) {
-        P.occ.level[l] = (const uint8_t *)s->occ[l];
-        P.occ.res[l] = d.occ_res[l];
-        P.occ.shift[l] = log2i(d.occ_res[0] / d.occ_res[l]);
-    }
+    merf::scene_views(s, P.fv, P.occ);
     P.mlp = (const float *)s->mlp;
     P.W = W;
     P.H = H;
@@ -267,6 +234,20 @@ merf_status launch_render(const merf_scene *s, const merf_camera *cams, int n, i
 }
 
 }  // namespace
+
+namespace merf {
+merf_status set_error(merf_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+merf_status clear_error() { return ok(); }
+}  // namespace merf
 
 extern "C" {
 

@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(kThreads, 4) render_kernel(const __grid_consta
 }
 
 // Traversal only (no gather, no termination): the set of evaluated lattice samples per ray.
-__global__ void __launch_bounds__(kThreads) trace_kernel(const __grid_constant__ RenderParams P)
+static __global__ void __launch_bounds__(kThreads) trace_kernel(const __grid_constant__ RenderParams P)
 {
     int i, j;
     pixel_of_thread(i, j);

@@ -26,7 +26,8 @@ CNT_RAYS, CNT_LATTICE, CNT_EVAL, CNT_APPEAR = 0, 1, 2, 3
 
 EXPORTS = ("merf_scene_upload", "merf_scene_upload_dense", "merf_scene_free", "merf_scene_device_bytes",
            "merf_render", "merf_render_aux", "merf_render_host", "merf_render_host_noalloc", "merf_trace",
-           "merf_set_device_budget",
+           "merf_set_device_budget", "merf_server_create", "merf_server_submit", "merf_server_wait",
+           "merf_server_get_stats", "merf_server_destroy",
            "merf_last_error", "merf_version")
 
 
@@ -46,6 +47,17 @@ class Desc(ct.Structure):
 class Opts(ct.Structure):
     _fields_ = [("step", ct.c_float), ("t_term", ct.c_float), ("precision", ct.c_int32),
                 ("early_term", ct.c_int32), ("reserved", ct.c_int32)]
+
+
+class ServerOpts(ct.Structure):
+    _fields_ = [("pool_bytes", ct.c_size_t), ("max_tiles_per_iter", ct.c_int32), ("precision", ct.c_int32),
+                ("step", ct.c_float), ("t_term", ct.c_float), ("early_term", ct.c_int32), ("reserved", ct.c_int32)]
+
+
+class ServerStats(ct.Structure):
+    _fields_ = [("submitted", ct.c_ulonglong), ("completed", ct.c_ulonglong), ("rays", ct.c_ulonglong),
+                ("iterations", ct.c_ulonglong), ("tiles", ct.c_ulonglong), ("pool_bytes", ct.c_size_t),
+                ("peak_pool_bytes", ct.c_size_t), ("peak_admitted", ct.c_int32), ("reserved", ct.c_int32)]
 
 
 _lib = None
@@ -71,6 +83,14 @@ def lib():
         L.merf_trace.argtypes = [vp, vp, i32, i32, i32, vp, i32, vp, ct.POINTER(Opts), vp]
         L.merf_set_device_budget.argtypes = [ct.c_size_t]
         L.merf_set_device_budget.restype = None
+        L.merf_server_create.argtypes = [vp, i32, ct.POINTER(ServerOpts), ct.POINTER(vp)]
+        L.merf_server_submit.argtypes = [vp, i32, vp, i32, i32, vp, ct.POINTER(ct.c_uint64)]
+        L.merf_server_wait.argtypes = [vp, ct.c_uint64, ct.c_double, ct.POINTER(ct.c_double)]
+        L.merf_server_get_stats.argtypes = [vp, ct.POINTER(ServerStats)]
+        L.merf_server_destroy.argtypes = [vp]
+        L.merf_server_destroy.restype = None
+        for name in ("merf_server_create", "merf_server_submit", "merf_server_wait", "merf_server_get_stats"):
+            getattr(L, name).restype = ct.c_int
         L.merf_last_error.restype = ct.c_char_p
         L.merf_version.restype = ct.c_char_p
         for name in ("merf_scene_upload", "merf_scene_upload_dense", "merf_render", "merf_render_aux",
@@ -234,3 +254,56 @@ def set_device_budget(nbytes: int):
 
 def version() -> str:
     return lib().merf_version().decode()
+
+
+class Server:
+    """Continuous-batching render server over resident scenes (the library's server thread does
+    admission, batching and launches; this class only marshals arguments)."""
+
+    def __init__(self, scenes: Sequence[Scene], pool_bytes: int, step: float, max_tiles_per_iter: int = 16384,
+                 precision: int = PREC_FP16, t_term: float = 2e-4, early_term: bool = True):
+        self.scenes = list(scenes)
+        arr = (ct.c_void_p * len(self.scenes))(*[sc.handle.value for sc in self.scenes])
+        o = ServerOpts(pool_bytes=int(pool_bytes), max_tiles_per_iter=int(max_tiles_per_iter), precision=precision,
+                       step=step, t_term=t_term, early_term=int(early_term), reserved=0)
+        h = ct.c_void_p()
+        _check(lib().merf_server_create(ct.cast(arr, ct.c_void_p), len(self.scenes), ct.byref(o), ct.byref(h)))
+        self.handle = h
+        self._outs = {}
+
+    def submit(self, scene: int, cam: np.ndarray, W: int, H: int, host_out: torch.Tensor) -> int:
+        if host_out.is_cuda or host_out.dtype != torch.float32 or not host_out.is_contiguous() or \
+                host_out.numel() != W * H * 3:
+            raise ValueError("host_out must be a contiguous host float32 tensor of H*W*3 elements")
+        cam = np.ascontiguousarray(cam, dtype=np.float32).reshape(16)
+        rid = ct.c_uint64()
+        _check(lib().merf_server_submit(self.handle, int(scene), _np_ptr(cam), W, H, ct.c_void_p(host_out.data_ptr()),
+                                        ct.byref(rid)))
+        self._outs[rid.value] = host_out
+        return rid.value
+
+    def wait(self, rid: int, timeout: float = 60.0) -> float:
+        lat = ct.c_double()
+        st = lib().merf_server_wait(self.handle, ct.c_uint64(rid), float(timeout), ct.byref(lat))
+        if st == ERR_TIMEOUT:
+            raise TimeoutError(lib().merf_last_error().decode())
+        self._outs.pop(rid, None)
+        _check(st)
+        return lat.value
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(lib().merf_server_get_stats(self.handle, ct.byref(s)))
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_ if k != "reserved"}
+
+    def close(self):
+        if self.handle:
+            lib().merf_server_destroy(self.handle)
+            self.handle = ct.c_void_p()
+            self._outs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,103 @@
+"""GPU tests of the serving form: continuous batching of mixed requests over resident scenes."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2302_12249_b300 import merf, synth
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def scenes(tiny_scene):
+    other = synth.make_scene("tiny", seed=1007, mlp_seed=3007)
+    return [merf.Scene(tiny_scene), merf.Scene(other)]
+
+
+def _host(W, H):
+    return torch.empty((H, W, 3), dtype=torch.float32, pin_memory=True)
+
+
+def _reference(scene, cam, W, H, prec):
+    return merf.render(scene, cam[None], W, H, 1 / 64, precision=prec)[0].cpu()
+
+
+@pytest.mark.parametrize("prec", [merf.PREC_FP16, merf.PREC_FP32])
+def test_single_request_equals_render(scenes, prec):
+    srv = merf.Server(scenes, pool_bytes=1 << 24, step=1 / 64, precision=prec)
+    cam = synth.config_cameras("tiny", W=50, H=37)[0]
+    out = _host(50, 37)
+    rid = srv.submit(0, cam, 50, 37, out)
+    lat = srv.wait(rid)
+    srv.close()
+    assert lat > 0
+    assert (out - _reference(scenes[0], cam, 50, 37, prec)).abs().max().item() <= parity.RGB_TOL
+
+
+def test_same_alone_and_in_the_mix(scenes):
+    """A request's image does not depend on what shares its iterations."""
+    cam = synth.sphere_cameras(1, 61, 45, radius=2.6, seed=51)[0]
+    srv = merf.Server(scenes, pool_bytes=1 << 24, step=1 / 64, max_tiles_per_iter=40)
+    alone = _host(61, 45)
+    srv.wait(srv.submit(1, cam, 61, 45, alone))
+    rng = np.random.default_rng(3)
+    ids, outs = [], []
+    sizes = [(16, 16), (64, 36), (33, 70), (128, 72), (7, 5)]
+    for k in range(24):
+        W, H = sizes[k % len(sizes)]
+        c = synth.sphere_cameras(1, W, H, radius=rng.uniform(1.2, 3.0), seed=100 + k)[0]
+        o = _host(W, H)
+        ids.append(srv.submit(int(rng.integers(0, 2)), c, W, H, o))
+        outs.append((o, int(0), c, W, H))
+        if k == 11:
+            mixed = _host(61, 45)
+            target = srv.submit(1, cam, 61, 45, mixed)
+    for rid in ids + [target]:
+        srv.wait(rid)
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == st["submitted"] == 26
+    assert st["iterations"] > 3
+    assert (mixed - alone).abs().max().item() <= parity.RGB_TOL
+    assert (alone - _reference(scenes[1], cam, 61, 45, merf.PREC_FP16)).abs().max().item() <= parity.RGB_TOL
+
+
+def test_admission_is_limited_by_pool_memory(scenes):
+    W, H = 64, 48
+    img = W * H * 3 * 4
+    srv = merf.Server(scenes, pool_bytes=2 * img + 4096, step=1 / 64, max_tiles_per_iter=16)
+    cams = synth.sphere_cameras(8, W, H, radius=2.5, seed=77)
+    outs = [_host(W, H) for _ in range(8)]
+    ids = [srv.submit(k % 2, cams[k], W, H, outs[k]) for k in range(8)]
+    for rid in ids:
+        srv.wait(rid)
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == 8
+    assert st["peak_admitted"] <= 2
+    assert st["peak_pool_bytes"] <= st["pool_bytes"]
+    for k in range(8):
+        ref = _reference(scenes[k % 2], cams[k], W, H, merf.PREC_FP16)
+        assert (outs[k] - ref).abs().max().item() <= parity.RGB_TOL
+
+
+def test_request_larger_than_pool_is_refused(scenes):
+    srv = merf.Server(scenes, pool_bytes=1 << 16, step=1 / 64)
+    cam = synth.config_cameras("tiny", W=128, H=128)[0]
+    with pytest.raises(merf.MerfError) as e:
+        srv.submit(0, cam, 128, 128, _host(128, 128))
+    srv.close()
+    assert e.value.status == merf.ERR_OOM
+
+
+def test_wait_timeout_then_completion(scenes):
+    srv = merf.Server(scenes, pool_bytes=1 << 26, step=1 / 64, max_tiles_per_iter=4)
+    cam = synth.config_cameras("tiny", W=640, H=480)[0]
+    out = _host(640, 480)
+    rid = srv.submit(0, cam, 640, 480, out)
+    with pytest.raises(TimeoutError):
+        srv.wait(rid, timeout=0.0)
+    srv.wait(rid, timeout=120.0)
+    srv.close()
+    assert (out - _reference(scenes[0], cam, 640, 480, merf.PREC_FP16)).abs().max().item() <= parity.RGB_TOL
