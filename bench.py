@@ -159,6 +159,86 @@ def _precision_form(gs, scene, n_cams=64, steps=2, n_pix=2000):
     return res
 
 
+SERVE_RES = [(256, 256), (640, 360), (1280, 720), (1920, 1080)]
+
+
+def _serving(gs_first, n_requests: int, rate: float = 200.0, seed_arrivals: int = 4000):
+    """Serving form: four resident paper-scale scenes, Poisson arrivals, random scene and orbit
+    camera, resolution uniform over SERVE_RES, FP16 continuous batching.  Latency is measured by the
+    library from submission to the image being in host memory."""
+    import queue
+    import threading
+    import torch
+    from paper_2302_12249_b300 import merf, synth
+    scenes = [gs_first] + [merf.Scene(synth.make_scene("paper", seed=synth.SEED_SCENE + k)) for k in (1, 2, 3)]
+    free_b, total_b = torch.cuda.mem_get_info()
+    pool = int(min(4 << 30, free_b // 4))
+    srv = merf.Server(scenes, pool_bytes=pool, step=STEP, max_tiles_per_iter=16384, precision=merf.PREC_FP16)
+    rng = np.random.default_rng(seed_arrivals)
+    gaps = rng.exponential(1.0 / rate, size=n_requests)
+    which = rng.integers(0, len(scenes), size=n_requests)
+    res = rng.integers(0, len(SERVE_RES), size=n_requests)
+    radius = rng.uniform(1.2, 3.0, size=n_requests)
+    az = rng.uniform(0, 2 * math.pi, size=n_requests)
+    el = np.radians(rng.uniform(-30, 30, size=n_requests))
+    bufs = {r: queue.Queue() for r in range(len(SERVE_RES))}
+    for r, (W, H) in enumerate(SERVE_RES):
+        for _ in range(48):
+            bufs[r].put(torch.empty((H, W, 3), dtype=torch.float32, pin_memory=True))
+    # warm-up: one request per resolution
+    for r, (W, H) in enumerate(SERVE_RES):
+        b = bufs[r].get()
+        cam = synth.camera_record(synth.look_at([2.0, 0.0, 0.3]), W, H)
+        srv.wait(srv.submit(0, cam, W, H, b))
+        bufs[r].put(b)
+    submitted = queue.Queue()
+    lat = np.zeros(n_requests)
+    lags = np.zeros(n_requests)
+    blocked = [0]
+
+    def collector():
+        for k in range(n_requests):
+            rid, r, b = submitted.get()
+            lat[k] = srv.wait(rid, timeout=600.0)
+            bufs[r].put(b)
+
+    th = threading.Thread(target=collector)
+    th.start()
+    t0 = time.perf_counter()
+    t_next = t0
+    for k in range(n_requests):
+        t_next += gaps[k]
+        dt = t_next - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        lags[k] = time.perf_counter() - t_next
+        r = int(res[k])
+        W, H = SERVE_RES[r]
+        if bufs[r].empty():
+            blocked[0] += 1
+        b = bufs[r].get()
+        eye = radius[k] * np.array([math.cos(el[k]) * math.cos(az[k]), math.cos(el[k]) * math.sin(az[k]), math.sin(el[k])])
+        cam = synth.camera_record(synth.look_at(eye), W, H)
+        submitted.put((srv.submit(int(which[k]), cam, W, H, b), r, b))
+    th.join()
+    t_end = time.perf_counter()
+    st = srv.stats()
+    srv.close()
+    rays = sum(SERVE_RES[int(r)][0] * SERVE_RES[int(r)][1] for r in res)
+    for sc in scenes[1:]:
+        sc.close()
+    return {"requests": n_requests, "arrival_rate_per_s": rate, "precision": "fp16",
+            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "mean_ms": float(lat.mean() * 1e3), "max_ms": float(lat.max() * 1e3),
+            "aggregate_mrays_per_s": rays / (t_end - t0) / 1e6, "offered_mrays_per_s": rays / gaps.sum() / 1e6,
+            "wall_s": t_end - t0, "iterations": st["iterations"], "peak_admitted": st["peak_admitted"],
+            "pool_mb": st["pool_bytes"] / 1e6, "peak_pool_mb": st["peak_pool_bytes"] / 1e6,
+            "submit_lag_p99_ms": float(np.percentile(lags, 99) * 1e3), "host_buffer_waits": blocked[0],
+            "workload": "4 resident paper-scale scenes (seeds 1000-1003), Poisson arrivals, random scene and "
+                        "orbit (radius U(1.2,3), elevation U(-30,30) deg), resolution uniform over "
+                        "256x256/640x360/1280x720/1920x1080; latency = submit to image in host memory"}
+
+
 def run_reference(args):
     dist, rank, world, _ = _dist()
     if rank != 0:
@@ -276,6 +356,9 @@ def run_ours(args):
     precision = None
     if rank == 0 and world == 1 and not args.no_precision:
         precision = _precision_form(gs, scene)
+    serving = None
+    if rank == 0 and world == 1 and args.serve_requests > 0:
+        serving = _serving(gs, args.serve_requests)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -301,6 +384,8 @@ def run_ours(args):
             line["cpu_baseline"] = cpu
         if precision is not None:
             line["precision_form"] = precision
+        if serving is not None:
+            line["serving"] = serving
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -317,6 +402,7 @@ def main():
     ap.add_argument("--cams", type=int, default=N_CAMS, help="cameras per step (profiling cases)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-output measurement (profiling)")
     ap.add_argument("--no-precision", action="store_true", help="skip the FP16/BF16 comparison (profiling)")
+    ap.add_argument("--serve-requests", type=int, default=10000, help="requests of the serving run (0 = skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
