@@ -94,6 +94,9 @@ def lib():
                                 ct.c_void_p, ct.c_int, ct.c_double, ct.c_int, ct.c_double,
                                 ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int]
         L.orc_trace.restype = ct.c_int
+        L.orc_render_grad.argtypes = [ct.POINTER(_Scene), ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.c_void_p,
+                                      ct.c_int, ct.POINTER(_Opts), ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]
+        L.orc_render_grad.restype = ct.c_int
         L.orc32_ray.argtypes = [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p]
         L.orc32_segments.argtypes = [ct.c_void_p, ct.c_void_p, ct.POINTER(_Segs32)]
         L.orc32_lattice_count.argtypes = [ct.POINTER(_Segs32), ct.c_float]
@@ -292,3 +295,24 @@ def trace(oscene: OracleScene, cams: np.ndarray, W: int, H: int, step: float, wo
                     0 if pix is None else n, float(step), int(decide_f32), float(eps),
                     _ptr(mask), _ptr(flags), words, _ptr(nlat), threads or default_threads())
     return mask, flags, nlat
+
+
+def render_grad(oscene: OracleScene, cams: np.ndarray, W: int, H: int, step: float, pix: np.ndarray,
+                dl_drgb: np.ndarray, t_term: float = 2e-4, early_term: bool = False, decide_f32: bool = True):
+    """Gradient of sum_pixels dl_drgb . C (dense float scenes): (g_grid, g_planes, g_mlp) in FP64."""
+    sc = oscene.scene
+    if sc.cfg.storage != "f32":
+        raise ValueError("the adjoint is defined for dense float storage")
+    cams = np.ascontiguousarray(cams, dtype=np.float32).reshape(-1, 16)
+    pix = np.ascontiguousarray(pix, dtype=np.int32).reshape(-1, 3)
+    dl = np.ascontiguousarray(dl_drgb, dtype=np.float64).reshape(-1, 3)
+    L, R = sc.cfg.L, sc.cfg.R
+    g_grid = np.zeros((L, L, L, 8), np.float64)
+    g_planes = np.zeros((3, R, R, 8), np.float64)
+    g_mlp = np.zeros(883, np.float64)
+    op = _Opts(step=step, t_term=t_term, early_term=int(early_term), decide_f32=int(decide_f32), no_mlp=0)
+    rc = lib().orc_render_grad(ct.byref(oscene.s), _ptr(cams), cams.shape[0], W, H, _ptr(pix), pix.shape[0],
+                               ct.byref(op), _ptr(dl), _ptr(g_grid), _ptr(g_planes), _ptr(g_mlp))
+    if rc != 0:
+        raise ValueError(f"orc_render_grad failed ({rc})")
+    return g_grid, g_planes, g_mlp

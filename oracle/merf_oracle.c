@@ -577,6 +577,197 @@ static void render_ray(const orc_scene *sc, const orc_opts *op, const float *cam
 }
 
 /* ------------------------------------------------------------------------------------ */
+/* adjoint (dense float storage): the gradient of Eq. 1 / Eq. 2 compositing, the activations,  */
+/* the interpolation of Eq. 3 and the deferred MLP, by the chain rule, sample by sample.       */
+
+/* add g (8 channels) times the interpolation weights of p into the grid and plane gradients */
+static void scatter_field(const orc_scene *sc, const double p[3], const double g[8], double *g_grid,
+                          double *g_planes)
+{
+    int C = sc->C, L = sc->L, R = sc->R;
+    int ix[2], iy[2], iz[2];
+    double wx, wy, wz;
+    lin(p[0], L, &ix[0], &ix[1], &wx);
+    lin(p[1], L, &iy[0], &iy[1], &wy);
+    lin(p[2], L, &iz[0], &iz[1], &wz);
+    for (int cz = 0; cz < 2; ++cz)
+        for (int cy = 0; cy < 2; ++cy)
+            for (int cx = 0; cx < 2; ++cx) {
+                double w = (cx ? wx : 1.0 - wx) * (cy ? wy : 1.0 - wy) * (cz ? wz : 1.0 - wz);
+                double *q = g_grid + (((size_t)iz[cz] * L + iy[cy]) * L + ix[cx]) * C;
+                for (int c = 0; c < C; ++c) q[c] += w * g[c];
+            }
+    static const int col_axis[3] = {1, 0, 0}, row_axis[3] = {2, 2, 1};
+    for (int q = 0; q < 3; ++q) {
+        int u[2], v[2];
+        double wu, wv;
+        lin(p[col_axis[q]], R, &u[0], &u[1], &wu);
+        lin(p[row_axis[q]], R, &v[0], &v[1], &wv);
+        for (int cv = 0; cv < 2; ++cv)
+            for (int cu = 0; cu < 2; ++cu) {
+                double w = (cu ? wu : 1.0 - wu) * (cv ? wv : 1.0 - wv);
+                double *t = g_planes + (((size_t)q * R + v[cv]) * R + u[cu]) * C;
+                for (int c = 0; c < C; ++c) t[c] += w * g[c];
+            }
+    }
+}
+
+/* MLP forward with intermediates and backward: returns dL/dx[0..6] (C_d, F) for dL/dh = gh */
+static void mlp_backward(const float *w, const double cd[3], const double f[4], const double d[3],
+                         const double gh[3], double gx7[7], double *g_mlp)
+{
+    double x[34];
+    int n = 0;
+    for (int k = 0; k < 3; ++k) x[n++] = cd[k];
+    for (int k = 0; k < 4; ++k) x[n++] = f[k];
+    for (int k = 0; k < 3; ++k) x[n++] = d[k];
+    for (int l = 0; l < 4; ++l) {
+        double fr = (double)(1 << l);
+        for (int k = 0; k < 3; ++k) x[n++] = sin(fr * d[k]);
+        for (int k = 0; k < 3; ++k) x[n++] = cos(fr * d[k]);
+    }
+    const float *W0 = w, *b0 = W0 + 34 * 16, *W1 = b0 + 16, *b1 = W1 + 16 * 16, *W2 = b1 + 16;
+    double z1[16], a1[16], z2[16], a2[16];
+    for (int o = 0; o < 16; ++o) {
+        double a = b0[o];
+        for (int i = 0; i < 34; ++i) a += x[i] * (double)W0[i * 16 + o];
+        z1[o] = a;
+        a1[o] = a > 0.0 ? a : 0.0;
+    }
+    for (int o = 0; o < 16; ++o) {
+        double a = b1[o];
+        for (int i = 0; i < 16; ++i) a += a1[i] * (double)W1[i * 16 + o];
+        z2[o] = a;
+        a2[o] = a > 0.0 ? a : 0.0;
+    }
+    double *gW0 = g_mlp, *gb0 = gW0 + 34 * 16, *gW1 = gb0 + 16, *gb1 = gW1 + 16 * 16, *gW2 = gb1 + 16,
+           *gb2 = gW2 + 16 * 3;
+    double da2[16], dz2[16], da1[16], dz1[16];
+    for (int o = 0; o < 3; ++o) gb2[o] += gh[o];
+    for (int i = 0; i < 16; ++i) {
+        double a = 0.0;
+        for (int o = 0; o < 3; ++o) {
+            gW2[i * 3 + o] += a2[i] * gh[o];
+            a += (double)W2[i * 3 + o] * gh[o];
+        }
+        da2[i] = a;
+        dz2[i] = z2[i] > 0.0 ? a : 0.0;
+    }
+    for (int o = 0; o < 16; ++o) gb1[o] += dz2[o];
+    for (int i = 0; i < 16; ++i) {
+        double a = 0.0;
+        for (int o = 0; o < 16; ++o) {
+            gW1[i * 16 + o] += a1[i] * dz2[o];
+            a += (double)W1[i * 16 + o] * dz2[o];
+        }
+        da1[i] = a;
+        dz1[i] = z1[i] > 0.0 ? a : 0.0;
+    }
+    for (int o = 0; o < 16; ++o) gb0[o] += dz1[o];
+    for (int i = 0; i < 34; ++i) {
+        double a = 0.0;
+        for (int o = 0; o < 16; ++o) {
+            gW0[i * 16 + o] += x[i] * dz1[o];
+            a += (double)W0[i * 16 + o] * dz1[o];
+        }
+        if (i < 7) gx7[i] = a;
+    }
+}
+
+typedef struct {
+    double p[3], tau, delta, alpha, T, c[3], f[4];
+} orc_sample;
+
+static void grad_ray(const orc_scene *sc, const orc_opts *op, const float *cam, int i, int j,
+                     const double gC[3], double *g_grid, double *g_planes, double *g_mlp)
+{
+    double o[3], d[3];
+    orc_seg segs[ORC_MAX_SEGS];
+    orc_ray(cam, i, j, o, d);
+    int ns = orc_segments(o, d, segs);
+    double step = op->step;
+    orc32_segs sg;
+    int nlat;
+    if (op->decide_f32) {
+        float o32[3], d32[3];
+        orc32_ray(cam, i, j, o32, d32);
+        orc32_segments(o32, d32, &sg);
+        nlat = orc32_lattice_count(&sg, (float)step);
+    } else {
+        double total = segs[ns - 1].s0 + segs[ns - 1].len;
+        nlat = 0;
+        while (((double)nlat + 1.0) * step < total) ++nlat;
+    }
+    /* forward, keeping every evaluated sample */
+    orc_sample *smp = (orc_sample *)malloc(sizeof(orc_sample) * (size_t)(nlat > 0 ? nlat : 1));
+    int n = 0, N = sc->occ_res[0];
+    double T = 1.0, cd[3] = {0, 0, 0}, F[4] = {0, 0, 0, 0};
+    for (int k = 0; k < nlat; ++k) {
+        double p[3];
+        orc_point_at(segs, ns, ((double)k + 0.5) * step, p);
+        int cell[3];
+        if (op->decide_f32) {
+            if (!orc32_sample_cell(&sg, (float)step, k, N, cell)) continue;
+        } else {
+            cell64(p, N, cell, NULL);
+        }
+        if (!occ_at(sc, cell)) continue;
+        double tt[8];
+        orc_field(sc, p, tt, NULL);
+        orc_sample *s = &smp[n++];
+        for (int a = 0; a < 3; ++a) s->p[a] = p[a];
+        s->tau = exp(tt[0]);
+        s->delta = orc_t_of_s(segs, ns, o, d, ((double)k + 1.0) * step) - orc_t_of_s(segs, ns, o, d, (double)k * step);
+        s->alpha = 1.0 - exp(-s->tau * s->delta);
+        s->T = T;
+        for (int c = 0; c < 3; ++c) s->c[c] = sigmoid(tt[1 + c]);
+        for (int c = 0; c < 4; ++c) s->f[c] = sigmoid(tt[4 + c]);
+        double w = s->alpha * T;
+        for (int c = 0; c < 3; ++c) cd[c] += w * s->c[c];
+        for (int c = 0; c < 4; ++c) F[c] += w * s->f[c];
+        T *= (1.0 - s->alpha);
+        if (op->early_term && T < op->t_term) break;
+    }
+    /* C = C_d + h(C_d, F, d): dL/dC_d = gC + dh/dC_d^T gC, dL/dF = dh/dF^T gC */
+    double gx7[7];
+    mlp_backward(sc->mlp, cd, F, d, gC, gx7, g_mlp);
+    double Gc[3] = {gC[0] + gx7[0], gC[1] + gx7[1], gC[2] + gx7[2]};
+    double Gf[4] = {gx7[3], gx7[4], gx7[5], gx7[6]};
+    /* back to front: U_i = sum_{j>i} prod_{i<k<j} (1 - alpha_k) alpha_j G.v_j, so that
+     * dL/dalpha_i = T_i (G.v_i - U_i) */
+    double U = 0.0;
+    for (int m = n - 1; m >= 0; --m) {
+        const orc_sample *s = &smp[m];
+        double Gv = 0.0;
+        for (int c = 0; c < 3; ++c) Gv += Gc[c] * s->c[c];
+        for (int c = 0; c < 4; ++c) Gv += Gf[c] * s->f[c];
+        double dalpha = s->T * (Gv - U);
+        U = s->alpha * Gv + (1.0 - s->alpha) * U;
+        double w = s->alpha * s->T;
+        double g[8];
+        /* alpha = 1 - exp(-tau delta): dalpha/dtau = delta (1 - alpha); tau = exp(t0) */
+        g[0] = dalpha * s->delta * (1.0 - s->alpha) * s->tau;
+        for (int c = 0; c < 3; ++c) g[1 + c] = w * Gc[c] * s->c[c] * (1.0 - s->c[c]);
+        for (int c = 0; c < 4; ++c) g[4 + c] = w * Gf[c] * s->f[c] * (1.0 - s->f[c]);
+        scatter_field(sc, s->p, g, g_grid, g_planes);
+    }
+    free(smp);
+}
+
+int orc_render_grad(const orc_scene *sc, const float *cams, int n_cams, int W, int H,
+                    const int32_t *pix, int n_pix, const orc_opts *opts, const double *dl_drgb,
+                    double *g_grid, double *g_planes, double *g_mlp)
+{
+    if (sc->storage != 1) return -1;
+    for (int r = 0; r < n_pix; ++r) {
+        int c = pix[3 * r + 0], i = pix[3 * r + 1], j = pix[3 * r + 2];
+        if (c < 0 || c >= n_cams || i < 0 || i >= W || j < 0 || j >= H) return -2;
+        grad_ray(sc, opts, cams + 16 * c, i, j, dl_drgb + 3 * r, g_grid, g_planes, g_mlp);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
 /* threaded drivers                                                                      */
 
 typedef struct {

@@ -82,6 +82,14 @@ void orc_mlp(const float *w, const double cd[3], const double f[4], const double
 int orc_render(const orc_scene *sc, const float *cams, int n_cams, int W, int H,
                const int32_t *pix, int n_pix, const orc_opts *opts, double *out, int n_threads);
 
+/* Gradient of L = sum over the listed pixels of dl_drgb . C with respect to the dense float
+ * grid, the planes and the MLP weights (dense float storage only; lattice, occupancy and
+ * termination decisions frozen at their forward values).  g_grid [L^3][8], g_planes [3][R][R][8]
+ * and g_mlp [883] are accumulated (caller zeroes them).  Single-threaded. */
+int orc_render_grad(const orc_scene *sc, const float *cams, int n_cams, int W, int H,
+                    const int32_t *pix, int n_pix, const orc_opts *opts, const double *dl_drgb,
+                    double *g_grid, double *g_planes, double *g_mlp);
+
 /* evaluated-lattice-sample sets (early termination off): bit k of row r is set iff
  * lattice sample k of ray r lies in an occupied finest cell; flag bit k is set where the
  * FP64 position lies within `eps` of a cell face. */
