@@ -174,6 +174,23 @@ merf_status merf_trace(const merf_scene *scene, const merf_camera *cams, int n_c
                        int H, uint32_t *mask, int words, int32_t *n_lattice,
                        const merf_render_opts *opts, void *stream);
 
+/* Replace the parameters of a dense float scene (storage MERF_STORAGE_F32_DENSE) with new values
+ * from device memory: grid float32 [L][L][L][8], planes float32 [3][R][R][8], mlp float32 [883]
+ * (device-to-device copies on `stream`; no allocation).  Used between optimisation steps. */
+merf_status merf_scene_set_dense(merf_scene *scene, const float *d_grid, const float *d_planes,
+                                 const float *d_mlp, void *stream);
+
+/* Adjoint of merf_render for dense float scenes in FP32 (Eq. 1, Eq. 2, Sec. 3.1, App. B): given
+ * d_out = dL/dC (device float32 [n_cams][H][W][3]), accumulate dL/dgrid, dL/dplanes and dL/dmlp
+ * into g_grid, g_planes, g_mlp (device, shapes of merf_scene_set_dense's arguments; the caller
+ * zeroes them).  Lattice, occupancy and early-termination decisions are those of the forward
+ * pass with the same cameras and options (they do not depend on the parameters except through
+ * termination).  Transmittance is recomputed by a second front-to-back march, not stored.
+ * Gradient sums use atomics, so results vary in the last bits between runs. */
+merf_status merf_render_backward(const merf_scene *scene, const merf_camera *cams, int n_cams, int W, int H,
+                                 const float *d_out, float *g_grid, float *g_planes, float *g_mlp,
+                                 const merf_render_opts *opts, void *stream);
+
 /* ----------------------------------------------------------------------------------------
  * Serving: a render server holding several resident scenes and batching requests of mixed
  * scenes and resolutions continuously.  The paper renders one view at a time in a browser; this

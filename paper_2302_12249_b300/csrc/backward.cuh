@@ -1,0 +1,233 @@
+// backward.cuh -- hand-written adjoint of the renderer for dense float scenes (sm_103a).
+//
+// For L with dL/dC given per pixel, one thread per ray:
+//   1. recompute the forward march (same arithmetic, hence the same samples, opacities and
+//      termination) to get C_d, F;
+//   2. run the deferred MLP forward and backward in FP32: dL/dC_d = dL/dC + (dh/dC_d)^T dL/dC,
+//      dL/dF = (dh/dF)^T dL/dC, and the weight gradients, accumulated per CTA in shared memory;
+//   3. march again front to back, recomputing transmittance instead of storing per-sample
+//      state.  With G = (dL/dC_d, dL/dF), v_i = (c_i, f_i) and A_i = sum_{j<=i} w_j G.v_j, the
+//      gradient of Eq. 1 / Eq. 2 with respect to a sample's opacity is
+//          dL/dalpha_i = T_i G.v_i - (G.C - A_i) / (1 - alpha_i),
+//      because the contribution of the samples behind i is G.C - A_i and each of them carries a
+//      factor (1 - alpha_i).  Through alpha = 1 - exp(-tau delta), tau = exp(t~_0) and the two
+//      sigmoids this gives dL/dt~ (8 channels), which is scattered into the grid and plane
+//      gradients with the interpolation weights (float4 atomics).
+#pragma once
+
+#include "render.cuh"
+
+namespace merf {
+
+struct BackwardParams {
+    FieldView fv;
+    OccView occ;
+    const float *mlp;
+    const float *d_out;     // [n][H][W][3] dL/dC
+    float *g_grid;          // [L][L][L][8]
+    float *g_planes;        // [3][R][R][8]
+    float *g_mlp;           // [883]
+    int W, H, cam0;
+    float step, t_term;
+    int early_term;
+    CamBlock cams;
+};
+
+__device__ __forceinline__ void atomic_add8(float *dst, const float g[8], float w)
+{
+    atomicAdd(reinterpret_cast<float4 *>(dst), make_float4(w * g[0], w * g[1], w * g[2], w * g[3]));
+    atomicAdd(reinterpret_cast<float4 *>(dst + 4), make_float4(w * g[4], w * g[5], w * g[6], w * g[7]));
+}
+
+// Add g (per channel) times the interpolation weights of p to the dense grid and plane gradients.
+__device__ __forceinline__ void scatter_f32(const FieldView &fv, float *g_grid, float *g_planes, float p0, float p1,
+                                            float p2, const float g[8])
+{
+    const float sL = (float)fv.L * 0.25f;
+    const int hL = fv.L >> 1, L = fv.L;
+    int x0, y0, z0;
+    float fx, fy, fz;
+    texel_coord(p0, sL, hL, L, x0, fx);
+    texel_coord(p1, sL, hL, L, y0, fy);
+    texel_coord(p2, sL, hL, L, z0, fz);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+        const float w = (cx ? fx : 1.0f - fx) * (cy ? fy : 1.0f - fy) * (cz ? fz : 1.0f - fz);
+        if (w != 0.0f) atomic_add8(g_grid + (((size_t)(z0 + cz) * L + (y0 + cy)) * L + (x0 + cx)) * 8, g, w);
+    }
+    const float sR = (float)fv.R * 0.25f;
+    const int hR = fv.R >> 1, R = fv.R;
+    int u0[3];
+    float fu[3];
+    texel_coord(p0, sR, hR, R, u0[0], fu[0]);
+    texel_coord(p1, sR, hR, R, u0[1], fu[1]);
+    texel_coord(p2, sR, hR, R, u0[2], fu[2]);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int ca = q == 0 ? 1 : 0, ra = q == 2 ? 1 : 2;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int cu = c & 1, cv = c >> 1;
+            const float w = (cu ? fu[ca] : 1.0f - fu[ca]) * (cv ? fu[ra] : 1.0f - fu[ra]);
+            if (w != 0.0f) atomic_add8(g_planes + (((size_t)q * R + u0[ra] + cv) * R + u0[ca] + cu) * 8, g, w);
+        }
+    }
+}
+
+__device__ __forceinline__ void smem_add(float *p, float v)
+{
+    if (v != 0.0f) atomicAdd(p, v);
+}
+
+// Deferred MLP forward + backward for one pixel (FP32).  w: weights in shared memory, gw: the
+// CTA's weight-gradient accumulator.  Returns dL/dx for x[0..6] = (C_d, F).
+__device__ __forceinline__ void mlp_backward_f32(const float *w, float *gw, const float cd[3], const float f[4],
+                                                 const float d[3], const float gh[3], float gx7[7])
+{
+    float x[34];
+    x[0] = cd[0]; x[1] = cd[1]; x[2] = cd[2];
+    x[3] = f[0]; x[4] = f[1]; x[5] = f[2]; x[6] = f[3];
+    x[7] = d[0]; x[8] = d[1]; x[9] = d[2];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        const float fr = (float)(1 << l);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float sn, cs;
+            sincosf(fr * d[k], &sn, &cs);
+            x[10 + 6 * l + k] = sn;
+            x[13 + 6 * l + k] = cs;
+        }
+    }
+    const float *W0 = w, *b0 = w + 544, *W1 = w + 560, *b1 = w + 816, *W2 = w + 832;
+    float z1[16], z2[16];
+#pragma unroll
+    for (int o = 0; o < 16; ++o) z1[o] = b0[o];
+#pragma unroll
+    for (int i = 0; i < 34; ++i)
+#pragma unroll
+        for (int o = 0; o < 16; ++o) z1[o] = fmaf(x[i], W0[i * 16 + o], z1[o]);
+#pragma unroll
+    for (int o = 0; o < 16; ++o) z2[o] = b1[o];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const float a = fmaxf(z1[i], 0.0f);
+#pragma unroll
+        for (int o = 0; o < 16; ++o) z2[o] = fmaf(a, W1[i * 16 + o], z2[o]);
+    }
+    float *gW0 = gw, *gb0 = gw + 544, *gW1 = gw + 560, *gb1 = gw + 816, *gW2 = gw + 832, *gb2 = gw + 880;
+#pragma unroll
+    for (int o = 0; o < 3; ++o) smem_add(gb2 + o, gh[o]);
+    float dz2[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const float a2 = fmaxf(z2[i], 0.0f);
+        float acc = 0.0f;
+#pragma unroll
+        for (int o = 0; o < 3; ++o) {
+            smem_add(gW2 + i * 3 + o, a2 * gh[o]);
+            acc = fmaf(W2[i * 3 + o], gh[o], acc);
+        }
+        dz2[i] = z2[i] > 0.0f ? acc : 0.0f;
+    }
+    float dz1[16];
+#pragma unroll
+    for (int o = 0; o < 16; ++o) smem_add(gb1 + o, dz2[o]);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const float a1 = fmaxf(z1[i], 0.0f);
+        float acc = 0.0f;
+#pragma unroll
+        for (int o = 0; o < 16; ++o) {
+            if (a1 != 0.0f) smem_add(gW1 + i * 16 + o, a1 * dz2[o]);
+            acc = fmaf(W1[i * 16 + o], dz2[o], acc);
+        }
+        dz1[i] = z1[i] > 0.0f ? acc : 0.0f;
+    }
+#pragma unroll
+    for (int o = 0; o < 16; ++o) smem_add(gb0 + o, dz1[o]);
+#pragma unroll
+    for (int i = 0; i < 34; ++i) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int o = 0; o < 16; ++o) {
+            smem_add(gW0 + i * 16 + o, x[i] * dz1[o]);
+            acc = fmaf(W0[i * 16 + o], dz1[o], acc);
+        }
+        if (i < 7) gx7[i] = acc;
+    }
+}
+
+static __global__ void __launch_bounds__(kThreads) backward_kernel(const __grid_constant__ BackwardParams P)
+{
+    __shared__ float wsm[kMlpParams];
+    __shared__ float gsm[kMlpParams];
+    for (int t = threadIdx.x; t < kMlpParams; t += kThreads) {
+        wsm[t] = __ldg(P.mlp + t);
+        gsm[t] = 0.0f;
+    }
+    __syncthreads();
+    int i, j;
+    pixel_of_thread(i, j);
+    const int cl = blockIdx.z;
+    if (i < P.W && j < P.H) {
+        const size_t pix = ((size_t)(P.cam0 + cl) * P.H + j) * P.W + i;
+        const float gC[3] = {P.d_out[pix * 3 + 0], P.d_out[pix * 3 + 1], P.d_out[pix * 3 + 2]};
+        const float *cam = P.cams.m[cl];
+        RayState r;
+        ray_state_init(r);
+        march_ray<1, 0>(P.fv, P.occ, cam, i, j, P.step, P.t_term, P.early_term, r);
+        float gx7[7];
+        mlp_backward_f32(wsm, gsm, r.cd, r.F, r.d, gC, gx7);
+        const float Gc[3] = {gC[0] + gx7[0], gC[1] + gx7[1], gC[2] + gx7[2]};
+        const float Gf[4] = {gx7[3], gx7[4], gx7[5], gx7[6]};
+        const float Gtot = Gc[0] * r.cd[0] + Gc[1] * r.cd[1] + Gc[2] * r.cd[2] + Gf[0] * r.F[0] + Gf[1] * r.F[1] +
+                           Gf[2] * r.F[2] + Gf[3] * r.F[3];
+        // second march, front to back, recomputing T
+        float o[3], d[3];
+        ray_f32(cam, i, j, o, d);
+        Walker wk;
+        wk.init(o, d, P.step);
+        float T = 1.0f, A = 0.0f;
+        int run_end = 0;
+        for (;;) {
+            if (wk.k >= run_end && !wk.next_run(P.occ, run_end)) break;
+            float p0, p1, p2;
+            wk.position(wk.k, p0, p1, p2);
+            float t8[8];
+            field_f32(P.fv, p0, p1, p2, t8);
+            const float tau = __expf(t8[0]);
+            const float dw = wk.delta_world(wk.k);
+            const float alpha = 1.0f - __expf(-tau * dw);
+            if (alpha > 0.0f) {
+                float c[3], f[4];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) c[k] = sigmoid_f(t8[1 + k]);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) f[k] = sigmoid_f(t8[4 + k]);
+                const float w = alpha * T;
+                const float Gv = Gc[0] * c[0] + Gc[1] * c[1] + Gc[2] * c[2] + Gf[0] * f[0] + Gf[1] * f[1] +
+                                 Gf[2] * f[2] + Gf[3] * f[3];
+                A = fmaf(w, Gv, A);
+                const float om = 1.0f - alpha;
+                const float dalpha = T * Gv - (om > 0.0f ? (Gtot - A) / om : 0.0f);
+                float g[8];
+                g[0] = dalpha * dw * om * tau;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) g[1 + k] = w * Gc[k] * c[k] * (1.0f - c[k]);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) g[4 + k] = w * Gf[k] * f[k] * (1.0f - f[k]);
+                scatter_f32(P.fv, P.g_grid, P.g_planes, p0, p1, p2, g);
+                T = T * om;
+                if (P.early_term && T < P.t_term) break;
+            }
+            ++wk.k;
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kMlpParams; t += kThreads)
+        if (gsm[t] != 0.0f) atomicAdd(P.g_mlp + t, gsm[t]);
+}
+
+}  // namespace merf

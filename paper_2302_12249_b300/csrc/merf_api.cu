@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "merf.h"
+#include "backward.cuh"
 #include "render.cuh"
 #include "scene.h"
 
@@ -438,6 +439,62 @@ merf_status merf_render_host_noalloc(const merf_scene *scene, const merf_camera 
     e = cudaMemcpyAsync(h_out, staging, bytes, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(MERF_ERR_CUDA, "render_host_noalloc copy: %s", cudaGetErrorString(e));
+    return ok();
+}
+
+merf_status merf_scene_set_dense(merf_scene *scene, const float *d_grid, const float *d_planes, const float *d_mlp,
+                                 void *stream)
+{
+    if (!scene || !d_grid || !d_planes || !d_mlp) return fail(MERF_ERR_INVALID_ARG, "NULL argument");
+    if (scene->desc.storage != MERF_STORAGE_F32_DENSE)
+        return fail(MERF_ERR_UNSUPPORTED, "merf_scene_set_dense needs a dense float scene");
+    const size_t L = scene->desc.grid_res, R = scene->desc.plane_res;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(scene->atlas, d_grid, L * L * L * 8 * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(scene->planes, d_planes, 3 * R * R * 8 * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(scene->mlp, d_mlp, MERF_MLP_PARAMS * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return fail(MERF_ERR_CUDA, "set_dense: %s", cudaGetErrorString(e));
+    return ok();
+}
+
+merf_status merf_render_backward(const merf_scene *scene, const merf_camera *cams, int n_cams, int W, int H,
+                                 const float *d_out, float *g_grid, float *g_planes, float *g_mlp,
+                                 const merf_render_opts *opts, void *stream)
+{
+    merf_status st = check_frame(scene, cams, n_cams, W, H);
+    if (st) return st;
+    if ((st = check_opts(opts))) return st;
+    if (!d_out || !g_grid || !g_planes || !g_mlp) return fail(MERF_ERR_INVALID_ARG, "NULL gradient buffer");
+    if (scene->desc.storage != MERF_STORAGE_F32_DENSE)
+        return fail(MERF_ERR_UNSUPPORTED, "the adjoint is defined for dense float scenes");
+    if (opts->precision != MERF_PREC_FP32) return fail(MERF_ERR_UNSUPPORTED, "the adjoint runs in FP32");
+    merf::RenderParams R = make_params(scene, opts, W, H);
+    merf::BackwardParams P;
+    memset(&P, 0, sizeof P);
+    P.fv = R.fv;
+    P.occ = R.occ;
+    P.mlp = R.mlp;
+    P.d_out = d_out;
+    P.g_grid = g_grid;
+    P.g_planes = g_planes;
+    P.g_mlp = g_mlp;
+    P.W = W;
+    P.H = H;
+    P.step = opts->step;
+    P.t_term = opts->t_term;
+    P.early_term = opts->early_term;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int c0 = 0; c0 < n_cams; c0 += merf::kMaxCams) {
+        const int nc = std::min(merf::kMaxCams, n_cams - c0);
+        P.cam0 = c0;
+        for (int c = 0; c < nc; ++c) memcpy(P.cams.m[c], &cams[c0 + c], sizeof(merf_camera));
+        const dim3 grid((W + merf::kTileW - 1) / merf::kTileW, (H + merf::kTileH - 1) / merf::kTileH, nc);
+        merf::backward_kernel<<<grid, merf::kThreads, 0, s>>>(P);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(MERF_ERR_CUDA, "backward launch: %s", cudaGetErrorString(e));
+    }
     return ok();
 }
 

@@ -26,7 +26,7 @@ CNT_RAYS, CNT_LATTICE, CNT_EVAL, CNT_APPEAR = 0, 1, 2, 3
 
 EXPORTS = ("merf_scene_upload", "merf_scene_upload_dense", "merf_scene_free", "merf_scene_device_bytes",
            "merf_render", "merf_render_aux", "merf_render_host", "merf_render_host_noalloc", "merf_trace",
-           "merf_set_device_budget", "merf_server_create", "merf_server_submit", "merf_server_wait",
+           "merf_set_device_budget", "merf_scene_set_dense", "merf_render_backward", "merf_server_create", "merf_server_submit", "merf_server_wait",
            "merf_server_get_stats", "merf_server_destroy",
            "merf_last_error", "merf_version")
 
@@ -83,6 +83,10 @@ def lib():
         L.merf_trace.argtypes = [vp, vp, i32, i32, i32, vp, i32, vp, ct.POINTER(Opts), vp]
         L.merf_set_device_budget.argtypes = [ct.c_size_t]
         L.merf_set_device_budget.restype = None
+        L.merf_scene_set_dense.argtypes = [vp, vp, vp, vp, vp]
+        L.merf_render_backward.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp, ct.POINTER(Opts), vp]
+        L.merf_scene_set_dense.restype = ct.c_int
+        L.merf_render_backward.restype = ct.c_int
         L.merf_server_create.argtypes = [vp, i32, ct.POINTER(ServerOpts), ct.POINTER(vp)]
         L.merf_server_submit.argtypes = [vp, i32, vp, i32, i32, vp, ct.POINTER(ct.c_uint64)]
         L.merf_server_wait.argtypes = [vp, ct.c_uint64, ct.c_double, ct.POINTER(ct.c_double)]
@@ -246,6 +250,59 @@ def trace(scene: Scene, cams: np.ndarray, W: int, H: int, step: float, words: in
     _check(lib().merf_trace(scene.handle, _np_ptr(cams), n, W, H, ct.c_void_p(mask.data_ptr()), words,
                             ct.c_void_p(nlat.data_ptr()), ct.byref(o), _stream(stream)))
     return mask, nlat
+
+
+def set_dense(scene: Scene, grid: torch.Tensor, planes: torch.Tensor, mlp: torch.Tensor, stream=None):
+    """Copy new parameter values (CUDA float32 tensors) into a dense float scene."""
+    L, R = scene.desc.grid_res, scene.desc.plane_res
+    _check(lib().merf_scene_set_dense(scene.handle, _dev_ptr(grid, torch.float32, L ** 3 * 8, "grid"),
+                                      _dev_ptr(planes, torch.float32, 3 * R * R * 8, "planes"),
+                                      _dev_ptr(mlp, torch.float32, 883, "mlp"), _stream(stream)))
+
+
+def render_backward(scene: Scene, cams: np.ndarray, W: int, H: int, step: float, d_out: torch.Tensor,
+                    g_grid: torch.Tensor, g_planes: torch.Tensor, g_mlp: torch.Tensor, t_term: float = 2e-4,
+                    early_term: bool = True, stream=None):
+    """Accumulate dL/dgrid, dL/dplanes, dL/dmlp (zeroed by the caller) for dL/dC = d_out."""
+    cams = cameras(cams)
+    n = cams.shape[0]
+    L, R = scene.desc.grid_res, scene.desc.plane_res
+    o = opts(step, t_term, early_term, PREC_FP32)
+    _check(lib().merf_render_backward(scene.handle, _np_ptr(cams), n, W, H,
+                                      _dev_ptr(d_out, torch.float32, n * H * W * 3, "d_out"),
+                                      _dev_ptr(g_grid, torch.float32, L ** 3 * 8, "g_grid"),
+                                      _dev_ptr(g_planes, torch.float32, 3 * R * R * 8, "g_planes"),
+                                      _dev_ptr(g_mlp, torch.float32, 883, "g_mlp"), ct.byref(o), _stream(stream)))
+
+
+class _RenderFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, grid, planes, mlp, scene, cams, W, H, step, t_term, early_term):
+        set_dense(scene, grid.detach(), planes.detach(), mlp.detach())
+        out = render(scene, cams, W, H, step, t_term=t_term, early_term=early_term)
+        ctx.scene, ctx.cams, ctx.args = scene, cams, (W, H, step, t_term, early_term)
+        ctx.shapes = (grid.shape, planes.shape, mlp.shape)
+        return out
+
+    @staticmethod
+    def backward(ctx, g_out):
+        W, H, step, t_term, early_term = ctx.args
+        gs, ps, ms = ctx.shapes
+        g_grid = torch.zeros(gs, dtype=torch.float32, device="cuda")
+        g_planes = torch.zeros(ps, dtype=torch.float32, device="cuda")
+        g_mlp = torch.zeros(ms, dtype=torch.float32, device="cuda")
+        render_backward(ctx.scene, ctx.cams, W, H, step, g_out.contiguous(), g_grid, g_planes, g_mlp, t_term,
+                        early_term)
+        return g_grid, g_planes, g_mlp, None, None, None, None, None, None, None
+
+
+def render_differentiable(scene: Scene, grid: torch.Tensor, planes: torch.Tensor, mlp: torch.Tensor,
+                          cams: np.ndarray, W: int, H: int, step: float, t_term: float = 2e-4,
+                          early_term: bool = True) -> torch.Tensor:
+    """Render a dense float scene whose grid, planes and MLP weights are the given CUDA tensors;
+    the result is differentiable with respect to them through the library's adjoint kernel.
+    The scene's device copy of the parameters is replaced by these values."""
+    return _RenderFn.apply(grid, planes, mlp, scene, cameras(cams), W, H, step, t_term, early_term)
 
 
 def set_device_budget(nbytes: int):
