@@ -8,11 +8,13 @@
 //   3. march again front to back, recomputing transmittance instead of storing per-sample
 //      state.  With G = (dL/dC_d, dL/dF), v_i = (c_i, f_i) and A_i = sum_{j<=i} w_j G.v_j, the
 //      gradient of Eq. 1 / Eq. 2 with respect to a sample's opacity is
-//          dL/dalpha_i = T_i G.v_i - (G.C - A_i) / (1 - alpha_i),
-//      because the contribution of the samples behind i is G.C - A_i and each of them carries a
-//      factor (1 - alpha_i).  Through alpha = 1 - exp(-tau delta), tau = exp(t~_0) and the two
-//      sigmoids this gives dL/dt~ (8 channels), which is scattered into the grid and plane
-//      gradients with the interpolation weights (float4 atomics).
+//          dL/dalpha_i = T_i G.v_i - S_i / (1 - alpha_i),   S_i = G.C - A_i,
+//      because S_i, the contribution of the samples behind i, carries a factor (1 - alpha_i).
+//      Through alpha = 1 - exp(-tau delta) and tau = exp(t~_0) the factor cancels:
+//          dL/dt~_0 = (T_i G.v_i (1 - alpha_i) - S_i) tau delta,
+//      so nothing is divided by a vanishing 1 - alpha.  With the two sigmoids this gives dL/dt~
+//      (8 channels), scattered into the grid and plane gradients with the interpolation weights
+//      (float4 atomics).
 #pragma once
 
 #include "render.cuh"
@@ -184,6 +186,8 @@ static __global__ void __launch_bounds__(kThreads) backward_kernel(const __grid_
         const float Gf[4] = {gx7[3], gx7[4], gx7[5], gx7[6]};
         const float Gtot = Gc[0] * r.cd[0] + Gc[1] * r.cd[1] + Gc[2] * r.cd[2] + Gf[0] * r.F[0] + Gf[1] * r.F[1] +
                            Gf[2] * r.F[2] + Gf[3] * r.F[3];
+        const float Gabs = fabsf(Gc[0]) + fabsf(Gc[1]) + fabsf(Gc[2]) + fabsf(Gf[0]) + fabsf(Gf[1]) + fabsf(Gf[2]) +
+                           fabsf(Gf[3]);
         // second march, front to back, recomputing T
         float o[3], d[3];
         ray_f32(cam, i, j, o, d);
@@ -211,9 +215,14 @@ static __global__ void __launch_bounds__(kThreads) backward_kernel(const __grid_
                                  Gf[2] * f[2] + Gf[3] * f[3];
                 A = fmaf(w, Gv, A);
                 const float om = 1.0f - alpha;
-                const float dalpha = T * Gv - (om > 0.0f ? (Gtot - A) / om : 0.0f);
+                // dL/dt~_0 = dL/dalpha (1 - alpha) tau delta = (T G.v (1 - alpha) - S) tau delta with
+                // S = G.C - A the contribution behind the sample: no division by 1 - alpha.  S is
+                // clamped to its bound |S| <= T (1 - alpha) sum |G|, which removes the rounding noise
+                // of the subtraction where almost nothing lies behind.
+                const float sbound = T * om * Gabs;
+                const float S = fminf(fmaxf(Gtot - A, -sbound), sbound);
                 float g[8];
-                g[0] = dalpha * dw * om * tau;
+                g[0] = (T * Gv * om - S) * (tau * dw);
 #pragma unroll
                 for (int k = 0; k < 3; ++k) g[1 + k] = w * Gc[k] * c[k] * (1.0f - c[k]);
 #pragma unroll
