@@ -61,28 +61,35 @@ __device__ __forceinline__ void ray_f32(const float *cam, int i, int j, float o[
     for (int r = 0; r < 3; ++r) d[r] = F_DIV(w[r], n);
 }
 
+// Component j (0, 1 or 2, not a compile-time constant) of a 3-vector, by selection: small arrays
+// are never indexed dynamically, so they stay in registers.
+__device__ __forceinline__ float comp3(const float v[3], int j)
+{
+    return j == 0 ? v[0] : (j == 1 ? v[1] : v[2]);
+}
+
 // Region of a point: 0 inside |x|_inf <= 1, else 1 + 2 j + (x_j < 0), j the first axis of
 // largest magnitude.
 __device__ __forceinline__ int region_f32(const float x[3])
 {
     int j = 0;
-    float ax = fabsf(x[0]);
-    if (fabsf(x[1]) > ax) { ax = fabsf(x[1]); j = 1; }
-    if (fabsf(x[2]) > ax) { ax = fabsf(x[2]); j = 2; }
+    float ax = fabsf(x[0]), xj = x[0];
+    if (fabsf(x[1]) > ax) { ax = fabsf(x[1]); xj = x[1]; j = 1; }
+    if (fabsf(x[2]) > ax) { ax = fabsf(x[2]); xj = x[2]; j = 2; }
     if (ax <= 1.0f) return 0;
-    return 1 + 2 * j + (x[j] < 0.0f ? 1 : 0);
+    return 1 + 2 * j + (xj < 0.0f ? 1 : 0);
 }
 
 // One region's projective map (Sec. 3.2): x_k / |x_j| and (2 - 1/|x_j|) sign(x_j).
 __device__ __forceinline__ void contract_f32(int region, const float x[3], float p[3])
 {
     if (region == 0) { p[0] = x[0]; p[1] = x[1]; p[2] = x[2]; return; }
-    int j = (region - 1) >> 1;
-    float ax = fabsf(x[j]);
+    const int j = (region - 1) >> 1;
+    const float ax = fabsf(comp3(x, j));
+    const float q = F_SUB(2.0f, F_DIV(1.0f, ax));
+    const float qs = ((region - 1) & 1) ? -q : q;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) p[k] = F_DIV(x[k], ax);
-    float q = F_SUB(2.0f, F_DIV(1.0f, ax));
-    p[j] = ((region - 1) & 1) ? -q : q;
+    for (int k = 0; k < 3; ++k) p[k] = (k == j) ? qs : F_DIV(x[k], ax);
 }
 
 __device__ __forceinline__ float lattice_s(int k, float step)
@@ -198,10 +205,10 @@ __device__ __forceinline__ void build_segments(const float o[3], const float d[3
             pb[0] = pa[0]; pb[1] = pa[1]; pb[2] = pa[2];
         } else {
             // image of t -> infinity in region (j, s): p_j = 2 s, p_k = d_k / |d_j|
-            float adj = fabsf(d[j]);
+            const float adj = fabsf(comp3(d, j));
+            const float lim = ((r - 1) & 1) ? -2.0f : 2.0f;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) pb[k] = F_DIV(d[k], adj);
-            pb[j] = ((r - 1) & 1) ? -2.0f : 2.0f;
+            for (int k = 0; k < 3; ++k) pb[k] = (k == j) ? lim : F_DIV(d[k], adj);
         }
         float ev[3];
 #pragma unroll
@@ -221,17 +228,19 @@ __device__ __forceinline__ void build_segments(const float o[3], const float d[3
             sg.g[i] = 0.0f;
         } else {
             const float sgn = ((r - 1) & 1) ? -1.0f : 1.0f;
-            const float xj = o[j] + ta[i] * d[j];
+            const float dj = comp3(d, j);
+            const float xj = comp3(o, j) + ta[i] * dj;
             const float w = 1.0f / fabsf(xj);           // 1 / |x_j| at the segment start
             float v2 = 0.0f;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 // contracted velocity per unit t: w^2 d_j along j, w (d_k - s d_j p_k) otherwise
-                const float vk = (k == j) ? d[j] * w * w : w * (d[k] - sgn * d[j] * pa[k]);
+                const float vk = (k == j) ? dj * w * w : w * (d[k] - sgn * dj * pa[k]);
                 v2 += vk * vk;
             }
+            const float ej = len > 0.0f ? F_DIV(comp3(ev, j), len) : 0.0f;
             sg.c[i] = 1.0f / sqrtf(v2);
-            sg.g[i] = sgn * sg.e[i][j] / w;
+            sg.g[i] = sgn * ej / w;
         }
     }
 }

@@ -201,3 +201,20 @@ def test_paper_scale_traversal_bit_exact(paper):
     m_o, _, n_o = oracle.trace(osc, cams, 480, 270, 1 / 256, words=64, decide_f32=True)
     np.testing.assert_array_equal(nlat.cpu().numpy(), n_o)
     np.testing.assert_array_equal(mask.cpu().numpy().view(np.uint32), m_o)
+
+
+def test_traversal_bit_exact_dense_scene_and_random_orbits():
+    """Lattice counts and evaluated sets identical to the FP32 restatement for the dense scene's
+    cameras and for random orbit cameras (radius 1.2 .. 3.5, every region of contracted space)."""
+    sc = synth.make_scene("dense128")
+    gs, osc = merf.Scene(sc), oracle.OracleScene(sc)
+    sets = [synth.config_cameras("dense128", W=128, H=128, n=4)]
+    rng = np.random.default_rng(21)
+    sets.append(np.stack([synth.sphere_cameras(1, 96, 64, radius=float(r), seed=int(s))[0]
+                          for r, s in zip(rng.uniform(1.2, 3.5, 12), rng.integers(0, 10 ** 6, 12))]))
+    for cams in sets:
+        W, H = (128, 128) if cams.shape[0] == 4 else (96, 64)
+        mask, nlat = merf.trace(gs, cams, W, H, sc.cfg.step, words=40)
+        m_o, _, n_o = oracle.trace(osc, cams, W, H, sc.cfg.step, words=40, decide_f32=True)
+        np.testing.assert_array_equal(nlat.cpu().numpy(), n_o)
+        np.testing.assert_array_equal(mask.cpu().numpy().view(np.uint32), m_o)
