@@ -159,6 +159,39 @@ def _precision_form(gs, scene, n_cams=64, steps=2, n_pix=2000):
     return res
 
 
+def _differentiation(steps: int = 5):
+    """Differentiation form: dense float scene (128^3 grid, 512^2 planes), 4 cameras at 512x512,
+    L2 loss against a seeded target; forward, then the hand-written adjoint through autograd."""
+    import torch
+    from paper_2302_12249_b300 import merf, synth
+    sc = synth.make_scene("dense128")
+    gs = merf.Scene(sc)
+    cams = synth.config_cameras("dense128")
+    grid = torch.from_numpy(sc.grid_f32).cuda().requires_grad_(True)
+    planes = torch.from_numpy(sc.planes_f32).cuda().requires_grad_(True)
+    mlp = torch.from_numpy(sc.mlp).cuda().requires_grad_(True)
+    target = torch.rand((4, 512, 512, 3), generator=torch.Generator().manual_seed(5)).cuda()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fwd = bwd = 0.0
+    for it in range(steps + 2):
+        grid.grad = planes.grad = mlp.grad = None
+        ev[0].record()
+        out = merf.render_differentiable(gs, grid, planes, mlp, cams, 512, 512, sc.cfg.step)
+        loss = 0.5 * ((out - target) ** 2).sum()
+        ev[1].record()
+        loss.backward()
+        ev[2].record()
+        torch.cuda.synchronize()
+        if it >= 2:
+            fwd += ev[0].elapsed_time(ev[1])
+            bwd += ev[1].elapsed_time(ev[2])
+    rays = 4 * 512 * 512
+    gs.close()
+    return {"workload": "dense float 128^3 grid + 3 x 512^2 planes, 4 cameras x 512x512, L2 loss",
+            "forward_ms": fwd / steps, "backward_ms": bwd / steps,
+            "backward_mrays_per_s": rays / (bwd / steps / 1e3) / 1e6}
+
+
 SERVE_RES = [(256, 256), (640, 360), (1280, 720), (1920, 1080)]
 
 
@@ -356,6 +389,9 @@ def run_ours(args):
     precision = None
     if rank == 0 and world == 1 and not args.no_precision:
         precision = _precision_form(gs, scene)
+    differentiation = None
+    if rank == 0 and world == 1 and not args.no_precision:
+        differentiation = _differentiation()
     serving = None
     if rank == 0 and world == 1 and args.serve_requests > 0:
         serving = _serving(gs, args.serve_requests)
@@ -384,6 +420,8 @@ def run_ours(args):
             line["cpu_baseline"] = cpu
         if precision is not None:
             line["precision_form"] = precision
+        if differentiation is not None:
+            line["differentiation"] = differentiation
         if serving is not None:
             line["serving"] = serving
         print(json.dumps(line), flush=True)
