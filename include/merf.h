@@ -141,7 +141,9 @@ merf_status merf_render_aux(const merf_scene *scene, const merf_camera *cams, in
 
 /* Render into host memory: renders like merf_render into the caller's device buffer
  * `d_staging` (float32 [n_cams][H][W][3]) and copies it to `h_out` (host, same shape;
- * page-locked for the copy to be asynchronous).  Returns after the copy has completed. */
+ * page-locked for the copy to be asynchronous).  Cameras are rendered one launch each on
+ * `stream` while the previous camera's image is copied on a library-owned copy stream (created on
+ * the first call on each device).  Returns after every copy has completed. */
 merf_status merf_render_host(const merf_scene *scene, const merf_camera *cams, int n_cams,
                              int W, int H, float *d_staging, float *h_out,
                              const merf_render_opts *opts, void *stream);

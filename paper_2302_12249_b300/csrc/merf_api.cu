@@ -354,16 +354,50 @@ merf_status merf_render(const merf_scene *scene, const merf_camera *cams, int n_
     return merf_render_aux(scene, cams, n_cams, W, H, out, nullptr, nullptr, opts, stream);
 }
 
+namespace {
+// Per-device copy stream and events of merf_render_host (created on first use, kept until exit).
+struct HostCopy {
+    cudaStream_t stream = nullptr;
+    std::vector<cudaEvent_t> events;
+};
+std::mutex g_host_copy_mu;
+HostCopy g_host_copy[64];
+}  // namespace
+
 merf_status merf_render_host(const merf_scene *scene, const merf_camera *cams, int n_cams, int W, int H,
                              float *d_staging, float *h_out, const merf_render_opts *opts, void *stream)
 {
     if (!h_out || !d_staging) return fail(MERF_ERR_INVALID_ARG, "h_out / d_staging is NULL");
-    merf_status st = merf_render(scene, cams, n_cams, W, H, d_staging, opts, stream);
+    merf_status st = check_frame(scene, cams, n_cams, W, H);
     if (st) return st;
+    if ((st = check_opts(opts))) return st;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return fail(MERF_ERR_UNSUPPORTED, "device ordinal %d", dev);
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t bytes = (size_t)n_cams * W * H * 3 * sizeof(float);
-    cudaError_t e = cudaMemcpyAsync(h_out, d_staging, bytes, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    const size_t per = (size_t)W * H * 3;
+    // Camera c renders on the caller's stream while camera c-1's image streams to the host on a
+    // second stream, so the device-to-host copies hide behind the rendering.
+    std::lock_guard<std::mutex> lk(g_host_copy_mu);
+    HostCopy &hc = g_host_copy[dev];
+    cudaError_t e = cudaSuccess;
+    if (!hc.stream) e = cudaStreamCreateWithFlags(&hc.stream, cudaStreamNonBlocking);
+    while (e == cudaSuccess && (int)hc.events.size() < n_cams) {
+        cudaEvent_t ev;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) hc.events.push_back(ev);
+    }
+    if (e != cudaSuccess) return fail(MERF_ERR_CUDA, "render_host resources: %s", cudaGetErrorString(e));
+    for (int c = 0; c < n_cams; ++c) {
+        if ((st = launch_render(scene, cams + c, 1, W, H, d_staging + c * per, nullptr, nullptr, opts, s))) return st;
+        e = cudaEventRecord(hc.events[c], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(hc.stream, hc.events[c], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_out + c * per, d_staging + c * per, per * sizeof(float), cudaMemcpyDeviceToHost,
+                                hc.stream);
+        if (e != cudaSuccess) return fail(MERF_ERR_CUDA, "render_host: %s", cudaGetErrorString(e));
+    }
+    e = cudaStreamSynchronize(hc.stream);
     if (e != cudaSuccess) return fail(MERF_ERR_CUDA, "render_host copy: %s", cudaGetErrorString(e));
     return ok();
 }
