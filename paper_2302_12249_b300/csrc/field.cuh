@@ -181,6 +181,38 @@ __device__ __forceinline__ float channel_u8(const Taps &t)
 
 __device__ __forceinline__ float density_u8(const Taps &t) { return channel_u8<0>(t); }
 
+// All eight pre-activations in one pass over the taps (tap-major): each tap's weight is formed
+// once and its eight bytes are accumulated into eight running sums.
+template <int i>
+__device__ __forceinline__ void accumulate_tap(const Taps &t, float acc[8])
+{
+    const float w = i < 8 ? grid_w(t, i) : plane_w(t, (i - 8) >> 2, (i - 8) & 3);
+    acc[0] = fmaf(w, byte_of<0>(t.v[i]), acc[0]);
+    acc[1] = fmaf(w, byte_of<1>(t.v[i]), acc[1]);
+    acc[2] = fmaf(w, byte_of<2>(t.v[i]), acc[2]);
+    acc[3] = fmaf(w, byte_of<3>(t.v[i]), acc[3]);
+    acc[4] = fmaf(w, byte_of<4>(t.v[i]), acc[4]);
+    acc[5] = fmaf(w, byte_of<5>(t.v[i]), acc[5]);
+    acc[6] = fmaf(w, byte_of<6>(t.v[i]), acc[6]);
+    acc[7] = fmaf(w, byte_of<7>(t.v[i]), acc[7]);
+}
+
+__device__ __forceinline__ void field_u8(const Taps &t, float out[8])
+{
+    float acc[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    accumulate_tap<0>(t, acc);  accumulate_tap<1>(t, acc);  accumulate_tap<2>(t, acc);
+    accumulate_tap<3>(t, acc);  accumulate_tap<4>(t, acc);  accumulate_tap<5>(t, acc);
+    accumulate_tap<6>(t, acc);  accumulate_tap<7>(t, acc);  accumulate_tap<8>(t, acc);
+    accumulate_tap<9>(t, acc);  accumulate_tap<10>(t, acc); accumulate_tap<11>(t, acc);
+    accumulate_tap<12>(t, acc); accumulate_tap<13>(t, acc); accumulate_tap<14>(t, acc);
+    accumulate_tap<15>(t, acc); accumulate_tap<16>(t, acc); accumulate_tap<17>(t, acc);
+    accumulate_tap<18>(t, acc); accumulate_tap<19>(t, acc);
+    out[0] = acc[0] * (28.0f / 255.0f) - 14.0f * (t.wv + 3.0f);
+    const float off = 7.0f * (t.wv + 3.0f);
+#pragma unroll
+    for (int c = 1; c < 8; ++c) out[c] = acc[c] * (14.0f / 255.0f) - off;
+}
+
 __device__ __forceinline__ void appearance_u8(const Taps &t, float out[7])
 {
     out[0] = channel_u8<1>(t);

@@ -329,7 +329,16 @@ __device__ __forceinline__ void march_ray(const FieldView &fv, const OccView &oc
         wk.position(wk.k, p0, p1, p2);
         float dens, app[7];
         Taps tp;
-        if constexpr (kStorage == 0) {
+        if constexpr (kStorage == 0 && kPrec == 0) {
+            // FP32: all channels in one tap-major pass; the appearance values are used only when
+            // the opacity is non-zero (Sec. 5), which changes nothing else (weight alpha T = 0)
+            gather_u8(fv, p0, p1, p2, tp);
+            float all[8];
+            field_u8(tp, all);
+            dens = all[0];
+#pragma unroll
+            for (int c = 0; c < 7; ++c) app[c] = all[1 + c];
+        } else if constexpr (kStorage == 0) {
             gather_u8(fv, p0, p1, p2, tp);
             dens = density_u8(tp);
         } else {
@@ -345,10 +354,7 @@ __device__ __forceinline__ void march_ray(const FieldView &fv, const OccView &oc
         ++r.neval;
         if (alpha > 0.0f) {
             ++r.napp;
-            if constexpr (kStorage == 0) {
-                if constexpr (kPrec == 0) appearance_u8(tp, app);
-                else appearance_lp<kPrec>(tp, app);
-            }
+            if constexpr (kStorage == 0 && kPrec != 0) appearance_lp<kPrec>(tp, app);
             const float wgt = alpha * r.T;
 #pragma unroll
             for (int c = 0; c < 3; ++c) r.cd[c] = fmaf(wgt, sigmoid_f(app[c]), r.cd[c]);
