@@ -72,13 +72,23 @@ struct Taps {
     float fx, fy, fz;       // grid fractions
     float fu[3];            // plane fractions along x, y, z
     float wv;               // weight of the stored grid corners
-    uint32_t gmask;         // bit c set: grid corner c is stored
 };
 
+// Trilinear weight of grid corner c.  A corner that is not stored holds zero bytes (the apron
+// of a missing neighbour is zero-filled and the slow path loads zeros), so it contributes
+// nothing to any weighted byte sum without masking; only W_V excludes it.
 __device__ __forceinline__ float grid_w(const Taps &t, int c)
 {
-    const float w = ((c & 1) ? t.fx : 1.0f - t.fx) * ((c & 2) ? t.fy : 1.0f - t.fy) * ((c & 4) ? t.fz : 1.0f - t.fz);
-    return ((t.gmask >> c) & 1u) ? w : 0.0f;
+    return ((c & 1) ? t.fx : 1.0f - t.fx) * ((c & 2) ? t.fy : 1.0f - t.fy) * ((c & 4) ? t.fz : 1.0f - t.fz);
+}
+
+// W_V: the sum of the weights of the stored corners (bit c of mask set: corner c stored).
+__device__ __forceinline__ float stored_weight(const Taps &t, uint32_t mask)
+{
+    float wv = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) wv += ((mask >> c) & 1u) ? grid_w(t, c) : 0.0f;
+    return wv;
 }
 
 __device__ __forceinline__ float plane_w(const Taps &t, int q, int c)
@@ -91,7 +101,7 @@ __device__ __forceinline__ float plane_w(const Taps &t, int q, int c)
 __device__ __forceinline__ void gather_grid_slow(const FieldView &fv, int x0, int y0, int z0, Taps &t)
 {
     const int sh = fv.log2B, msk = fv.B - 1, nb = fv.nb, B1 = fv.B + 1;
-    t.gmask = 0u;
+    uint32_t gmask = 0u;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         const int x = x0 + (c & 1), y = y0 + ((c >> 1) & 1), z = z0 + (c >> 2);
@@ -99,11 +109,12 @@ __device__ __forceinline__ void gather_grid_slow(const FieldView &fv, int x0, in
         if (ent >= 0) {
             const size_t slot = (size_t)(ent & 0xffffff);
             t.v[c] = __ldg(fv.atlas + ((slot * B1 + (z & msk)) * B1 + (y & msk)) * B1 + (x & msk));
-            t.gmask |= 1u << c;
+            gmask |= 1u << c;
         } else {
             t.v[c] = make_uint2(0u, 0u);
         }
     }
+    t.wv = stored_weight(t, gmask);
 }
 
 __device__ __forceinline__ void gather_u8(const FieldView &fv, float p0, float p1, float p2, Taps &t)
@@ -128,16 +139,18 @@ __device__ __forceinline__ void gather_u8(const FieldView &fv, float p0, float p
         t.v[5] = __ldg(base + sz + 1);
         t.v[6] = __ldg(base + sz + sy);
         t.v[7] = __ldg(base + sz + sy + 1);
-        t.gmask = 0xffu;
+        t.wv = 1.0f;
         const uint32_t miss = ((uint32_t)ent >> 24) << 1;     // bit n: neighbour n not stored
         if (miss) {
+            uint32_t gmask = 0xffu;
             // corners that fall in the apron of a neighbour that is not stored
             const int ex = lx == msk, ey = ly == msk, ez = lz == msk;
 #pragma unroll
             for (int c = 1; c < 8; ++c) {
                 const int nbr = ((c & 1) & ex) | ((((c >> 1) & 1) & ey) << 1) | ((((c >> 2) & 1) & ez) << 2);
-                if ((miss >> nbr) & 1u) t.gmask &= ~(1u << c);
+                if ((miss >> nbr) & 1u) gmask &= ~(1u << c);
             }
+            t.wv = stored_weight(t, gmask);
         }
     } else {
         gather_grid_slow(fv, x0, y0, z0, t);
@@ -158,15 +171,18 @@ __device__ __forceinline__ void gather_u8(const FieldView &fv, float p0, float p
         t.v[8 + 4 * q + 2] = __ldg(base + R);
         t.v[8 + 4 * q + 3] = __ldg(base + R + 1);
     }
-    float wv = 0.0f;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) wv += grid_w(t, c);
-    t.wv = wv;
 }
 
-// Pre-activation of channel c from gathered taps.
+// Density pre-activation from its weighted byte sum k: (28 / 255) k - 14 (W_V + 3).  Every
+// path that evaluates density calls this one expression, so their opacities agree bit for bit.
+__device__ __forceinline__ float dequant_density(float k, float wv)
+{
+    return k * (28.0f / 255.0f) - 14.0f * (wv + 3.0f);
+}
+
+// Weighted byte sum of channel c over the 20 taps.
 template <int c>
-__device__ __forceinline__ float channel_u8(const Taps &t)
+__device__ __forceinline__ float byte_sum_u8(const Taps &t)
 {
     float k = 0.0f;
 #pragma unroll
@@ -175,31 +191,39 @@ __device__ __forceinline__ float channel_u8(const Taps &t)
     for (int q = 0; q < 3; ++q)
 #pragma unroll
         for (int i = 0; i < 4; ++i) k = fmaf(plane_w(t, q, i), byte_of<c>(t.v[8 + 4 * q + i]), k);
-    constexpr float m = c == 0 ? 14.0f : 7.0f;
-    return k * (2.0f * m / 255.0f) - m * (t.wv + 3.0f);
+    return k;
 }
 
-__device__ __forceinline__ float density_u8(const Taps &t) { return channel_u8<0>(t); }
+__device__ __forceinline__ float density_u8(const Taps &t) { return dequant_density(byte_sum_u8<0>(t), t.wv); }
+
+// Bytes b and b + 1 of a 32-bit word as two floats (byte_f on both, the subtraction packed).
+template <int b>
+__device__ __forceinline__ float2 byte_pair_f(uint32_t w)
+{
+    const float2 m = make_float2(__uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u | b)),
+                                 __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u | (b + 1))));
+    return __fadd2_rn(m, make_float2(-8388608.0f, -8388608.0f));
+}
 
 // All eight pre-activations in one pass over the taps (tap-major): each tap's weight is formed
-// once and its eight bytes are accumulated into eight running sums.
+// once and its eight bytes are accumulated into four running float2 sums with packed FP32
+// arithmetic (each lane rounds exactly as the scalar fmaf does).
 template <int i>
-__device__ __forceinline__ void accumulate_tap(const Taps &t, float acc[8])
+__device__ __forceinline__ void accumulate_tap(const Taps &t, float2 acc[4])
 {
     const float w = i < 8 ? grid_w(t, i) : plane_w(t, (i - 8) >> 2, (i - 8) & 3);
-    acc[0] = fmaf(w, byte_of<0>(t.v[i]), acc[0]);
-    acc[1] = fmaf(w, byte_of<1>(t.v[i]), acc[1]);
-    acc[2] = fmaf(w, byte_of<2>(t.v[i]), acc[2]);
-    acc[3] = fmaf(w, byte_of<3>(t.v[i]), acc[3]);
-    acc[4] = fmaf(w, byte_of<4>(t.v[i]), acc[4]);
-    acc[5] = fmaf(w, byte_of<5>(t.v[i]), acc[5]);
-    acc[6] = fmaf(w, byte_of<6>(t.v[i]), acc[6]);
-    acc[7] = fmaf(w, byte_of<7>(t.v[i]), acc[7]);
+    const float2 ww = make_float2(w, w);
+    acc[0] = __ffma2_rn(ww, byte_pair_f<0>(t.v[i].x), acc[0]);
+    acc[1] = __ffma2_rn(ww, byte_pair_f<2>(t.v[i].x), acc[1]);
+    acc[2] = __ffma2_rn(ww, byte_pair_f<0>(t.v[i].y), acc[2]);
+    acc[3] = __ffma2_rn(ww, byte_pair_f<2>(t.v[i].y), acc[3]);
 }
 
-__device__ __forceinline__ void field_u8(const Taps &t, float out[8])
+// Weighted byte sums of all eight channels, as the pairs (0, 1), (2, 3), (4, 5), (6, 7).
+__device__ __forceinline__ void byte_sums_u8(const Taps &t, float2 acc[4])
 {
-    float acc[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[j] = make_float2(0.0f, 0.0f);
     accumulate_tap<0>(t, acc);  accumulate_tap<1>(t, acc);  accumulate_tap<2>(t, acc);
     accumulate_tap<3>(t, acc);  accumulate_tap<4>(t, acc);  accumulate_tap<5>(t, acc);
     accumulate_tap<6>(t, acc);  accumulate_tap<7>(t, acc);  accumulate_tap<8>(t, acc);
@@ -207,21 +231,6 @@ __device__ __forceinline__ void field_u8(const Taps &t, float out[8])
     accumulate_tap<12>(t, acc); accumulate_tap<13>(t, acc); accumulate_tap<14>(t, acc);
     accumulate_tap<15>(t, acc); accumulate_tap<16>(t, acc); accumulate_tap<17>(t, acc);
     accumulate_tap<18>(t, acc); accumulate_tap<19>(t, acc);
-    out[0] = acc[0] * (28.0f / 255.0f) - 14.0f * (t.wv + 3.0f);
-    const float off = 7.0f * (t.wv + 3.0f);
-#pragma unroll
-    for (int c = 1; c < 8; ++c) out[c] = acc[c] * (14.0f / 255.0f) - off;
-}
-
-__device__ __forceinline__ void appearance_u8(const Taps &t, float out[7])
-{
-    out[0] = channel_u8<1>(t);
-    out[1] = channel_u8<2>(t);
-    out[2] = channel_u8<3>(t);
-    out[3] = channel_u8<4>(t);
-    out[4] = channel_u8<5>(t);
-    out[5] = channel_u8<6>(t);
-    out[6] = channel_u8<7>(t);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -231,8 +240,10 @@ __device__ __forceinline__ void appearance_u8(const Taps &t, float out[7])
 // tap: the difference of two such halves is an exact integer in [-255, 255], so the 16-bit
 // arithmetic only carries the interpolation corrections sum_i w_i (b_i - b_first), accumulated
 // in half2 (FP16) or bfloat162 (BF16, which also holds those integers exactly) with weights
-// rounded to that type.  The first taps' values and the dequantisation stay in FP32:
-//     K_c = W_V b_first,V + b_first,Px + b_first,Py + b_first,Pz + sum of corrections.
+// rounded to that type.  A grid corner that is not stored holds zero bytes, so with the
+// (unmasked) trilinear weights summing to one the first taps enter with weight one; their sum
+// (an integer <= 1020) is exact in half and the dequantisation stays in FP32:
+//     K_c = b_first,V + b_first,Px + b_first,Py + b_first,Pz + sum of corrections.
 
 template <int pair>   // appearance channel pairs (1,2), (3,3), (4,5), (6,7)
 __device__ __forceinline__ __half2 magic_h2(uint2 v)
@@ -269,8 +280,7 @@ __device__ __forceinline__ void lp_weights(const Taps &t, LpWeights<kPrec> &lw)
 }
 
 template <int kPrec, int pair>   // kPrec 1: FP16, 2: BF16
-__device__ __forceinline__ float2 lp_pair(const Taps &t, const LpWeights<kPrec> &lw, float2 &first_v,
-                                          float2 &first_p)
+__device__ __forceinline__ float2 lp_pair(const Taps &t, const LpWeights<kPrec> &lw, float2 &firsts)
 {
     const __half2 mag = __float2half2_rn(1024.0f);
     __half2 first[4];
@@ -307,9 +317,9 @@ __device__ __forceinline__ float2 lp_pair(const Taps &t, const LpWeights<kPrec> 
         }
         corr = __bfloat1622float2(acc);
     }
-    first_v = __half22float2(__hsub2(first[0], mag));
-    // the three plane first taps summed exactly in half (integers <= 765)
-    first_p = __half22float2(__hadd2(__hadd2(__hsub2(first[1], mag), __hsub2(first[2], mag)), __hsub2(first[3], mag)));
+    // the four first taps summed exactly in half (integers <= 1020)
+    firsts = __half22float2(__hadd2(__hadd2(__hsub2(first[0], mag), __hsub2(first[1], mag)),
+                                    __hadd2(__hsub2(first[2], mag), __hsub2(first[3], mag))));
     return corr;
 }
 
@@ -319,15 +329,15 @@ __device__ __forceinline__ void appearance_lp(const Taps &t, float out[7])
     LpWeights<kPrec> lw;
     lp_weights<kPrec>(t, lw);
     float K[8];
-    float2 fv, fp, cr;
-    cr = lp_pair<kPrec, 0>(t, lw, fv, fp);
-    K[0] = fmaf(t.wv, fv.x, fp.x) + cr.x; K[1] = fmaf(t.wv, fv.y, fp.y) + cr.y;
-    cr = lp_pair<kPrec, 1>(t, lw, fv, fp);
-    K[2] = fmaf(t.wv, fv.x, fp.x) + cr.x; K[3] = K[2];
-    cr = lp_pair<kPrec, 2>(t, lw, fv, fp);
-    K[4] = fmaf(t.wv, fv.x, fp.x) + cr.x; K[5] = fmaf(t.wv, fv.y, fp.y) + cr.y;
-    cr = lp_pair<kPrec, 3>(t, lw, fv, fp);
-    K[6] = fmaf(t.wv, fv.x, fp.x) + cr.x; K[7] = fmaf(t.wv, fv.y, fp.y) + cr.y;
+    float2 fs, cr;
+    cr = lp_pair<kPrec, 0>(t, lw, fs);
+    K[0] = fs.x + cr.x; K[1] = fs.y + cr.y;
+    cr = lp_pair<kPrec, 1>(t, lw, fs);
+    K[2] = fs.x + cr.x; K[3] = K[2];
+    cr = lp_pair<kPrec, 2>(t, lw, fs);
+    K[4] = fs.x + cr.x; K[5] = fs.y + cr.y;
+    cr = lp_pair<kPrec, 3>(t, lw, fs);
+    K[6] = fs.x + cr.x; K[7] = fs.y + cr.y;
     const float off = 7.0f * (t.wv + 3.0f), sc = 14.0f / 255.0f;
     out[0] = K[0] * sc - off;   // channel 1
     out[1] = K[1] * sc - off;   // channel 2

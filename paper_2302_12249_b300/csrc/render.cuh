@@ -42,6 +42,76 @@ struct RenderParams {
 
 __device__ __forceinline__ float sigmoid_f(float x) { return __fdividef(1.0f, 1.0f + __expf(-x)); }
 
+// 2^x and 1/x by the special-function unit (PTX ex2.approx / rcp.approx, relative error about
+// 2^-22): sigmoid(x) = 1 / (1 + 2^y) with y = -x log2(e).
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+constexpr float kLog2e = 1.44269504088896341f;
+
+// Appearance of one sample as exponents y = -x log2(e) of its seven sigmoids: channel 1 and
+// the pairs (2, 3), (4, 5), (6, 7), so that pairs go through packed FP32 arithmetic.
+struct AppArg {
+    float y1;
+    float2 y23, y45, y67;
+};
+
+__device__ __forceinline__ AppArg app_arg(const float app[7])
+{
+    const float2 nl = make_float2(-kLog2e, -kLog2e);
+    AppArg a;
+    a.y1 = app[0] * -kLog2e;
+    a.y23 = __fmul2_rn(make_float2(app[1], app[2]), nl);
+    a.y45 = __fmul2_rn(make_float2(app[3], app[4]), nl);
+    a.y67 = __fmul2_rn(make_float2(app[5], app[6]), nl);
+    return a;
+}
+
+// From the weighted byte sums of the uint8 path: x = (14 / 255) k - 7 (W_V + 3), so
+// y = k (-14 log2(e) / 255) + 7 log2(e) (W_V + 3), one fused multiply-add per channel.
+__device__ __forceinline__ AppArg app_arg_u8(const float2 k[4], float wv)
+{
+    const float A = -kLog2e * 14.0f / 255.0f, b = (7.0f * kLog2e) * (wv + 3.0f);
+    const float2 A2 = make_float2(A, A), b2 = make_float2(b, b);
+    AppArg a;
+    a.y1 = fmaf(k[0].y, A, b);
+    a.y23 = __ffma2_rn(k[1], A2, b2);
+    a.y45 = __ffma2_rn(k[2], A2, b2);
+    a.y67 = __ffma2_rn(k[3], A2, b2);
+    return a;
+}
+
+// Front-to-back accumulators of C_d (channels 1..3) and F (channels 4..7), paired as AppArg.
+struct Accum {
+    float c0;
+    float2 c12, f01, f23;
+};
+
+__device__ __forceinline__ float2 sigmoid2(float2 y)
+{
+    const float2 e = __fadd2_rn(make_float2(ex2_approx(y.x), ex2_approx(y.y)), make_float2(1.0f, 1.0f));
+    return make_float2(rcp_approx(e.x), rcp_approx(e.y));
+}
+
+// acc += w sigmoid(x) for the seven appearance channels (Eq. 4 with weight w = alpha T).
+__device__ __forceinline__ void composite(Accum &acc, float w, const AppArg &a)
+{
+    const float2 w2 = make_float2(w, w);
+    acc.c0 = fmaf(w, rcp_approx(1.0f + ex2_approx(a.y1)), acc.c0);
+    acc.c12 = __ffma2_rn(w2, sigmoid2(a.y23), acc.c12);
+    acc.f01 = __ffma2_rn(w2, sigmoid2(a.y45), acc.f01);
+    acc.f23 = __ffma2_rn(w2, sigmoid2(a.y67), acc.f23);
+}
+
 // h(C_d, F, d): [C_d, F, d, sin d, cos d, sin 2d, cos 2d, sin 4d, cos 4d, sin 8d, cos 8d]
 // -> 16 ReLU -> 16 ReLU -> 3 (App. B: three layers, 16 hidden units, 4 frequencies).
 __device__ __forceinline__ void mlp_f32(const float *w, const float cd[3], const float f[4],
@@ -323,21 +393,24 @@ __device__ __forceinline__ void march_ray(const FieldView &fv, const OccView &oc
     wk.init(o, r.d, step);
     r.nlat = wk.nlat;
     int run_end = 0;
+    Accum acc;
+    acc.c0 = 0.0f;
+    acc.c12 = acc.f01 = acc.f23 = make_float2(0.0f, 0.0f);
     for (;;) {
         if (wk.k >= run_end && !wk.next_run(occ, run_end)) break;
         float p0, p1, p2;
         wk.position(wk.k, p0, p1, p2);
-        float dens, app[7];
+        float dens;
+        AppArg ya;
         Taps tp;
         if constexpr (kStorage == 0 && kPrec == 0) {
             // FP32: all channels in one tap-major pass; the appearance values are used only when
             // the opacity is non-zero (Sec. 5), which changes nothing else (weight alpha T = 0)
             gather_u8(fv, p0, p1, p2, tp);
-            float all[8];
-            field_u8(tp, all);
-            dens = all[0];
-#pragma unroll
-            for (int c = 0; c < 7; ++c) app[c] = all[1 + c];
+            float2 k[4];
+            byte_sums_u8(tp, k);
+            dens = dequant_density(k[0].x, tp.wv);
+            ya = app_arg_u8(k, tp.wv);
         } else if constexpr (kStorage == 0) {
             gather_u8(fv, p0, p1, p2, tp);
             dens = density_u8(tp);
@@ -345,8 +418,7 @@ __device__ __forceinline__ void march_ray(const FieldView &fv, const OccView &oc
             float all[8];
             field_f32(fv, p0, p1, p2, all);
             dens = all[0];
-#pragma unroll
-            for (int c = 0; c < 7; ++c) app[c] = all[1 + c];
+            ya = app_arg(all + 1);
         }
         const float tau = __expf(dens);
         const float dw = wk.delta_world(wk.k);
@@ -354,17 +426,19 @@ __device__ __forceinline__ void march_ray(const FieldView &fv, const OccView &oc
         ++r.neval;
         if (alpha > 0.0f) {
             ++r.napp;
-            if constexpr (kStorage == 0 && kPrec != 0) appearance_lp<kPrec>(tp, app);
-            const float wgt = alpha * r.T;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) r.cd[c] = fmaf(wgt, sigmoid_f(app[c]), r.cd[c]);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) r.F[c] = fmaf(wgt, sigmoid_f(app[3 + c]), r.F[c]);
+            if constexpr (kStorage == 0 && kPrec != 0) {
+                float app[7];
+                appearance_lp<kPrec>(tp, app);
+                ya = app_arg(app);
+            }
+            composite(acc, alpha * r.T, ya);
             r.T = r.T * (1.0f - alpha);
             if (early_term && r.T < t_term) { r.term = 1; break; }
         }
         ++wk.k;
     }
+    r.cd[0] = acc.c0; r.cd[1] = acc.c12.x; r.cd[2] = acc.c12.y;
+    r.F[0] = acc.f01.x; r.F[1] = acc.f01.y; r.F[2] = acc.f23.x; r.F[3] = acc.f23.y;
 }
 
 __device__ __forceinline__ void ray_state_init(RayState &r)
