@@ -38,16 +38,18 @@ struct FieldView {
 };
 
 // Lowest corner i0 and weight f of the upper corner for the continuous texel index
-// u = (p + 2) N / 4 - 1/2 with clamp-to-edge: p * N/4 is exact when N/4 is a power of two,
-// floor and remainder are exact, and the shift by 1/2 is exact or below one float ulp of 1/2.
+// u = (p + 2) N / 4 - 1/2 with clamp-to-edge.  a = p N/4 is exact when N/4 is a power of two;
+// adding 1.5 * 2^23 rounds it to the nearest integer n (held in the low mantissa bits, |a| <
+// 2^22), which is read back exactly; d = a - n in [-1/2, 1/2] is exact, so
+// u = (n - 1 + N/2) + (d + 1/2) with d + 1/2 in [0, 1] rounded at most once, below 2^-25.
 // Outside [0, N-1] the clamped value is expressed as i0 in {0, N-2} with f in {0, 1}.
 __device__ __forceinline__ void texel_coord(float p, float scale, int half, int N, int &i0, float &f)
 {
     const float a = __fmul_rn(p, scale);
-    const float fl = floorf(a);
-    const float r = a - fl;
-    const int ib = (int)fl + half;
-    if (r >= 0.5f) { i0 = ib; f = r - 0.5f; } else { i0 = ib - 1; f = r + 0.5f; }
+    const float t = __fadd_rn(a, 12582912.0f);
+    const float n = __fsub_rn(t, 12582912.0f);
+    i0 = (int)(__float_as_uint(t) - 0x4B400000u) - 1 + half;
+    f = __fadd_rn(__fsub_rn(a, n), 0.5f);
     if (i0 < 0) { i0 = 0; f = 0.0f; }
     if (i0 > N - 2) { i0 = N - 2; f = 1.0f; }
 }
@@ -180,21 +182,6 @@ __device__ __forceinline__ float dequant_density(float k, float wv)
     return k * (28.0f / 255.0f) - 14.0f * (wv + 3.0f);
 }
 
-// Weighted byte sum of channel c over the 20 taps.
-template <int c>
-__device__ __forceinline__ float byte_sum_u8(const Taps &t)
-{
-    float k = 0.0f;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) k = fmaf(grid_w(t, i), byte_of<c>(t.v[i]), k);
-#pragma unroll
-    for (int q = 0; q < 3; ++q)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) k = fmaf(plane_w(t, q, i), byte_of<c>(t.v[8 + 4 * q + i]), k);
-    return k;
-}
-
-__device__ __forceinline__ float density_u8(const Taps &t) { return dequant_density(byte_sum_u8<0>(t), t.wv); }
 
 // Bytes b and b + 1 of a 32-bit word as two floats (byte_f on both, the subtraction packed).
 template <int b>
@@ -234,118 +221,115 @@ __device__ __forceinline__ void byte_sums_u8(const Taps &t, float2 acc[4])
 }
 
 // ---------------------------------------------------------------------------------------------
-// Reduced-precision appearance (the precision form).  Each tap's seven appearance bytes become
-// four half2 values 1024 + byte, one byte permute each (exact: the half 0x64XX is 1024 + XX).
-// Within each source (grid, P_x, P_y, P_z) every tap is taken relative to the source's first
-// tap: the difference of two such halves is an exact integer in [-255, 255], so the 16-bit
-// arithmetic only carries the interpolation corrections sum_i w_i (b_i - b_first), accumulated
-// in half2 (FP16) or bfloat162 (BF16, which also holds those integers exactly) with weights
+// Reduced-precision byte sums (the precision form).  Density and channel 1 keep the FP32 packed
+// pair of the FP32 path (so density, opacity and transmittance are those of the FP32 path bit
+// for bit); channels (2, 3), (4, 5), (6, 7) go through 16-bit pairs.  Within each source (grid,
+// P_x, P_y, P_z) every tap is taken relative to the source's first tap: the difference of two
+// bytes is an exact integer in [-255, 255] (exact in half and in bfloat16), so the 16-bit
+// arithmetic only carries the interpolation corrections sum_i w_i (b_i - b_first), with weights
 // rounded to that type.  A grid corner that is not stored holds zero bytes, so with the
-// (unmasked) trilinear weights summing to one the first taps enter with weight one; their sum
-// (an integer <= 1020) is exact in half and the dequantisation stays in FP32:
+// unmasked trilinear weights summing to one the first taps enter with weight one; their sum is
+// an integer <= 1020, exact in either form:
 //     K_c = b_first,V + b_first,Px + b_first,Py + b_first,Pz + sum of corrections.
+// FP16: one byte permute gives a half2 of 1024 + byte for two channels (the half 0x64XX is
+// 1024 + XX), and the difference of two such halves is the exact byte difference.  BF16 (7
+// stored mantissa bits cannot hold 1024 + byte) takes the differences in FP32 from the packed
+// 2^23 + byte floats and converts them to bfloat16 exactly.
 
-template <int pair>   // appearance channel pairs (1,2), (3,3), (4,5), (6,7)
-__device__ __forceinline__ __half2 magic_h2(uint2 v)
+__device__ __forceinline__ __half2 magic_h2(uint32_t w, uint32_t sel)
 {
-    const uint32_t u = pair == 0 ? __byte_perm(v.x, 0x64646464u, 0x4241u)
-                     : pair == 1 ? __byte_perm(v.x, 0x64646464u, 0x4343u)
-                     : pair == 2 ? __byte_perm(v.y, 0x64646464u, 0x4140u)
-                                 : __byte_perm(v.y, 0x64646464u, 0x4342u);
+    const uint32_t u = __byte_perm(w, 0x64646464u, sel);
     __half2 h;
     memcpy(&h, &u, 4);
     return h;
 }
 
-// 16-bit weights of the 20 taps, both halves of each pair equal (converted once per sample)
+// 2^23 + byte for bytes b and b + 1 of a word (no subtraction).
+template <int b>
+__device__ __forceinline__ float2 byte_pair_magic(uint32_t w)
+{
+    return make_float2(__uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u | b)),
+                       __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u | (b + 1))));
+}
+
 template <int kPrec>
-struct LpWeights {
-    uint32_t w[20];
+struct LpAcc;
+template <>
+struct LpAcc<1> {                        // FP16
+    __half2 first[3], fsum[3], corr[3];
+};
+template <>
+struct LpAcc<2> {                        // BF16
+    float2 nfirst[3], fsum[3];           // nfirst: -(2^23 + first byte)
+    __nv_bfloat162 corr[3];
 };
 
-template <int kPrec>
-__device__ __forceinline__ void lp_weights(const Taps &t, LpWeights<kPrec> &lw)
+template <int kPrec, int i>
+__device__ __forceinline__ void lp_tap(const Taps &t, float2 &k01, LpAcc<kPrec> &a)
 {
-#pragma unroll
-    for (int i = 0; i < 20; ++i) {
-        const float v = i < 8 ? grid_w(t, i) : plane_w(t, (i - 8) >> 2, (i - 8) & 3);
-        if constexpr (kPrec == 1) {
-            const __half2 h = __float2half2_rn(v);
-            memcpy(&lw.w[i], &h, 4);
-        } else {
-            const __nv_bfloat162 h = __float2bfloat162_rn(v);
-            memcpy(&lw.w[i], &h, 4);
-        }
-    }
-}
-
-template <int kPrec, int pair>   // kPrec 1: FP16, 2: BF16
-__device__ __forceinline__ float2 lp_pair(const Taps &t, const LpWeights<kPrec> &lw, float2 &firsts)
-{
-    const __half2 mag = __float2half2_rn(1024.0f);
-    __half2 first[4];
-    float2 corr;
+    constexpr bool first = i == 0 || i == 8 || i == 12 || i == 16;
+    const float w = i < 8 ? grid_w(t, i) : plane_w(t, (i - 8) >> 2, (i - 8) & 3);
+    k01 = __ffma2_rn(make_float2(w, w), byte_pair_f<0>(t.v[i].x), k01);
     if constexpr (kPrec == 1) {
-        __half2 acc = __float2half2_rn(0.0f);
+        const __half2 m[3] = {magic_h2(t.v[i].x, 0x4342u), magic_h2(t.v[i].y, 0x4140u),
+                              magic_h2(t.v[i].y, 0x4342u)};
+        if constexpr (first) {
+            const __half2 mag = __float2half2_rn(1024.0f);
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            const int b = s == 0 ? 0 : 4 + 4 * s, n = s == 0 ? 8 : 4;
-            first[s] = magic_h2<pair>(t.v[b]);
-#pragma unroll
-            for (int i = 1; i < n; ++i) {
-                __half2 w;
-                memcpy(&w, &lw.w[b + i], 4);
-                acc = __hfma2(w, __hsub2(magic_h2<pair>(t.v[b + i]), first[s]), acc);
+            for (int p = 0; p < 3; ++p) {
+                a.first[p] = m[p];
+                a.fsum[p] = i == 0 ? __hsub2(m[p], mag) : __hadd2(a.fsum[p], __hsub2(m[p], mag));
             }
+        } else {
+            const __half2 w2 = __float2half2_rn(w);
+#pragma unroll
+            for (int p = 0; p < 3; ++p) a.corr[p] = __hfma2(w2, __hsub2(m[p], a.first[p]), a.corr[p]);
         }
-        corr = __half22float2(acc);
     } else {
-        __nv_bfloat162 acc = __float2bfloat162_rn(0.0f);
+        const float2 m[3] = {byte_pair_magic<2>(t.v[i].x), byte_pair_magic<0>(t.v[i].y),
+                             byte_pair_magic<2>(t.v[i].y)};
+        if constexpr (first) {
+            const float2 nmag = make_float2(-8388608.0f, -8388608.0f);
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            const int b = s == 0 ? 0 : 4 + 4 * s, n = s == 0 ? 8 : 4;
-            first[s] = magic_h2<pair>(t.v[b]);
+            for (int p = 0; p < 3; ++p) {
+                a.nfirst[p] = make_float2(-m[p].x, -m[p].y);
+                a.fsum[p] = i == 0 ? __fadd2_rn(m[p], nmag) : __fadd2_rn(a.fsum[p], __fadd2_rn(m[p], nmag));
+            }
+        } else {
+            const __nv_bfloat162 w2 = __float2bfloat162_rn(w);
 #pragma unroll
-            for (int i = 1; i < n; ++i) {
-                __nv_bfloat162 w;
-                memcpy(&w, &lw.w[b + i], 4);
-                // the difference is an exact integer in [-255, 255], exact in bfloat16 too
-                const __nv_bfloat162 dd =
-                    __float22bfloat162_rn(__half22float2(__hsub2(magic_h2<pair>(t.v[b + i]), first[s])));
-                acc = __hfma2(w, dd, acc);
+            for (int p = 0; p < 3; ++p) {
+                const float2 d = __fadd2_rn(m[p], a.nfirst[p]);
+                a.corr[p] = __hfma2(w2, __float22bfloat162_rn(d), a.corr[p]);
             }
         }
-        corr = __bfloat1622float2(acc);
     }
-    // the four first taps summed exactly in half (integers <= 1020)
-    firsts = __half22float2(__hadd2(__hadd2(__hsub2(first[0], mag), __hsub2(first[1], mag)),
-                                    __hadd2(__hsub2(first[2], mag), __hsub2(first[3], mag))));
-    return corr;
 }
 
+// Weighted byte sums in the layout of byte_sums_u8: k[0] = channels (0, 1) in FP32, k[1..3] =
+// channels (2, 3), (4, 5), (6, 7) from their 16-bit corrections.
 template <int kPrec>
-__device__ __forceinline__ void appearance_lp(const Taps &t, float out[7])
+__device__ __forceinline__ void byte_sums_lp(const Taps &t, float2 k[4])
 {
-    LpWeights<kPrec> lw;
-    lp_weights<kPrec>(t, lw);
-    float K[8];
-    float2 fs, cr;
-    cr = lp_pair<kPrec, 0>(t, lw, fs);
-    K[0] = fs.x + cr.x; K[1] = fs.y + cr.y;
-    cr = lp_pair<kPrec, 1>(t, lw, fs);
-    K[2] = fs.x + cr.x; K[3] = K[2];
-    cr = lp_pair<kPrec, 2>(t, lw, fs);
-    K[4] = fs.x + cr.x; K[5] = fs.y + cr.y;
-    cr = lp_pair<kPrec, 3>(t, lw, fs);
-    K[6] = fs.x + cr.x; K[7] = fs.y + cr.y;
-    const float off = 7.0f * (t.wv + 3.0f), sc = 14.0f / 255.0f;
-    out[0] = K[0] * sc - off;   // channel 1
-    out[1] = K[1] * sc - off;   // channel 2
-    out[2] = K[2] * sc - off;   // channel 3
-    out[3] = K[4] * sc - off;   // channel 4
-    out[4] = K[5] * sc - off;   // channel 5
-    out[5] = K[6] * sc - off;   // channel 6
-    out[6] = K[7] * sc - off;   // channel 7
+    LpAcc<kPrec> a;
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        if constexpr (kPrec == 1) a.corr[p] = __float2half2_rn(0.0f);
+        else a.corr[p] = __float2bfloat162_rn(0.0f);
+    }
+    k[0] = make_float2(0.0f, 0.0f);
+    lp_tap<kPrec, 0>(t, k[0], a);  lp_tap<kPrec, 1>(t, k[0], a);  lp_tap<kPrec, 2>(t, k[0], a);
+    lp_tap<kPrec, 3>(t, k[0], a);  lp_tap<kPrec, 4>(t, k[0], a);  lp_tap<kPrec, 5>(t, k[0], a);
+    lp_tap<kPrec, 6>(t, k[0], a);  lp_tap<kPrec, 7>(t, k[0], a);  lp_tap<kPrec, 8>(t, k[0], a);
+    lp_tap<kPrec, 9>(t, k[0], a);  lp_tap<kPrec, 10>(t, k[0], a); lp_tap<kPrec, 11>(t, k[0], a);
+    lp_tap<kPrec, 12>(t, k[0], a); lp_tap<kPrec, 13>(t, k[0], a); lp_tap<kPrec, 14>(t, k[0], a);
+    lp_tap<kPrec, 15>(t, k[0], a); lp_tap<kPrec, 16>(t, k[0], a); lp_tap<kPrec, 17>(t, k[0], a);
+    lp_tap<kPrec, 18>(t, k[0], a); lp_tap<kPrec, 19>(t, k[0], a);
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        if constexpr (kPrec == 1) k[1 + p] = __fadd2_rn(__half22float2(a.fsum[p]), __half22float2(a.corr[p]));
+        else k[1 + p] = __fadd2_rn(a.fsum[p], __bfloat1622float2(a.corr[p]));
+    }
 }
 
 // Dense float storage: all eight channels of all 20 taps, summed.

@@ -67,7 +67,7 @@ struct ServeParams {
 };
 
 template <int kPrec>
-__global__ void __launch_bounds__(kThreads, 4) serve_kernel(const __grid_constant__ ServeParams P)
+__global__ void __launch_bounds__(kThreads, (kMinBlocks<0, kPrec>)) serve_kernel(const __grid_constant__ ServeParams P)
 {
     __shared__ MlpSmem<kPrec> ms;
     __shared__ int s_tile;

@@ -403,17 +403,21 @@ __device__ __forceinline__ void march_ray(const FieldView &fv, const OccView &oc
         float dens;
         AppArg ya;
         Taps tp;
+        // all channels in one tap-major pass; the appearance values are used only when the
+        // opacity is non-zero (Sec. 5), which changes nothing else (weight alpha T = 0)
         if constexpr (kStorage == 0 && kPrec == 0) {
-            // FP32: all channels in one tap-major pass; the appearance values are used only when
-            // the opacity is non-zero (Sec. 5), which changes nothing else (weight alpha T = 0)
             gather_u8(fv, p0, p1, p2, tp);
             float2 k[4];
             byte_sums_u8(tp, k);
             dens = dequant_density(k[0].x, tp.wv);
             ya = app_arg_u8(k, tp.wv);
         } else if constexpr (kStorage == 0) {
+            // FP16 / BF16 appearance arithmetic; density in FP32 exactly as above
             gather_u8(fv, p0, p1, p2, tp);
-            dens = density_u8(tp);
+            float2 k[4];
+            byte_sums_lp<kPrec>(tp, k);
+            dens = dequant_density(k[0].x, tp.wv);
+            ya = app_arg_u8(k, tp.wv);
         } else {
             float all[8];
             field_f32(fv, p0, p1, p2, all);
@@ -426,11 +430,6 @@ __device__ __forceinline__ void march_ray(const FieldView &fv, const OccView &oc
         ++r.neval;
         if (alpha > 0.0f) {
             ++r.napp;
-            if constexpr (kStorage == 0 && kPrec != 0) {
-                float app[7];
-                appearance_lp<kPrec>(tp, app);
-                ya = app_arg(app);
-            }
             composite(acc, alpha * r.T, ya);
             r.T = r.T * (1.0f - alpha);
             if (early_term && r.T < t_term) { r.term = 1; break; }
@@ -478,9 +477,14 @@ __device__ __forceinline__ void deferred_mlp(MlpSmem<kPrec> &ms, const RayState 
     }
 }
 
+// Resident CTAs per SM the register allocation is bounded for (measured on the 8 x 1080p
+// paper-scale workload: the uint8 FP32 kernel is fastest at 6 (80 registers), FP16 and BF16 at 5).
+template <int kStorage, int kPrec>
+constexpr int kMinBlocks = kStorage != 0 ? 4 : kPrec == 0 ? 6 : 5;
+
 template <int kStorage, int kPrec>   // storage 0: uint8 block-sparse, 1: float32 dense;
                                      // precision 0: FP32, 1: FP16, 2: BF16 (uint8 storage only)
-__global__ void __launch_bounds__(kThreads, 4) render_kernel(const __grid_constant__ RenderParams P)
+__global__ void __launch_bounds__(kThreads, (kMinBlocks<kStorage, kPrec>)) render_kernel(const __grid_constant__ RenderParams P)
 {
     __shared__ MlpSmem<kPrec> ms;
     ms.load(P.mlp);
