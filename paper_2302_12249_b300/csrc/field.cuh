@@ -31,7 +31,7 @@ namespace merf {
 struct FieldView {
     const int32_t *index_grid;   // [(L/B)^3] slot | missing-neighbour mask << 24, or -1
     const uint2 *atlas;          // [n_blocks][B+1][B+1][B+1]
-    const uint2 *planes;         // [3][R][R]
+    const uint2 *planes;         // [3][R+2][R+2]: one-texel clamp-to-edge border
     const float4 *grid_f32;      // dense storage: [L][L][L][2]
     const float4 *planes_f32;    // dense storage: [3][R][R][2]
     int L, B, log2B, nb, R;
@@ -52,6 +52,19 @@ __device__ __forceinline__ void texel_coord(float p, float scale, int half, int 
     f = __fadd_rn(__fsub_rn(a, n), 0.5f);
     if (i0 < 0) { i0 = 0; f = 0.0f; }
     if (i0 > N - 2) { i0 = N - 2; f = 1.0f; }
+}
+
+// The same for a plane stored with a one-texel border that repeats its edge texels: the lowest
+// tap in bordered coordinates is i0 + 1 = n + N/2 in [0, N], with f unchanged.  Clamp-to-edge
+// then needs no clamp (a tap on the border reads the edge value), because every contracted
+// point lies in [-2, 2]; the index is still bounded to [0, N] so that no tap leaves the array.
+__device__ __forceinline__ void plane_coord(float p, float scale, int half, int N, int &i0, float &f)
+{
+    const float a = __fmul_rn(p, scale);
+    const float t = __fadd_rn(a, 12582912.0f);
+    const float n = __fsub_rn(t, 12582912.0f);
+    i0 = min(max((int)(__float_as_uint(t) - 0x4B400000u) + half, 0), N);
+    f = __fadd_rn(__fsub_rn(a, n), 0.5f);
 }
 
 // Byte b of a 32-bit word as a float: the byte is placed in the low mantissa bits of 2^23
@@ -119,15 +132,25 @@ __device__ __forceinline__ void gather_grid_slow(const FieldView &fv, int x0, in
     t.wv = stored_weight(t, gmask);
 }
 
+// Scene geometry a gather is compiled for.  kGeoRuntime reads L, B and R from the FieldView;
+// kGeoPaper is the paper's configuration (L = 512 stored in 16^3 blocks, planes R = 2048;
+// Sec. 4), for which every stride, shift and scale below is a compile-time constant.
+constexpr int kGeoRuntime = 0, kGeoPaper = 1;
+
+template <int kGeo>
 __device__ __forceinline__ void gather_u8(const FieldView &fv, float p0, float p1, float p2, Taps &t)
 {
-    const float sL = (float)fv.L * 0.25f;
-    const int hL = fv.L >> 1;
+    const int L = kGeo == kGeoPaper ? 512 : fv.L;
+    const int sh = kGeo == kGeoPaper ? 4 : fv.log2B;
+    const int nb = kGeo == kGeoPaper ? 32 : fv.nb;
+    const int Rg = kGeo == kGeoPaper ? 2048 : fv.R;
+    const float sL = (float)L * 0.25f;
+    const int hL = L >> 1;
     int x0, y0, z0;
-    texel_coord(p0, sL, hL, fv.L, x0, t.fx);
-    texel_coord(p1, sL, hL, fv.L, y0, t.fy);
-    texel_coord(p2, sL, hL, fv.L, z0, t.fz);
-    const int sh = fv.log2B, msk = fv.B - 1, nb = fv.nb, B1 = fv.B + 1;
+    texel_coord(p0, sL, hL, L, x0, t.fx);
+    texel_coord(p1, sL, hL, L, y0, t.fy);
+    texel_coord(p2, sL, hL, L, z0, t.fz);
+    const int msk = (1 << sh) - 1, B1 = (1 << sh) + 1;
     const int ent = __ldg(fv.index_grid + ((z0 >> sh) * nb + (y0 >> sh)) * nb + (x0 >> sh));
     if (ent >= 0) {
         const int lx = x0 & msk, ly = y0 & msk, lz = z0 & msk;
@@ -157,21 +180,21 @@ __device__ __forceinline__ void gather_u8(const FieldView &fv, float p0, float p
     } else {
         gather_grid_slow(fv, x0, y0, z0, t);
     }
-    const float sR = (float)fv.R * 0.25f;
-    const int hR = fv.R >> 1, R = fv.R;
+    const float sR = (float)Rg * 0.25f;
+    const int hR = Rg >> 1, R = Rg, Rp = Rg + 2;
     int u0[3];
-    texel_coord(p0, sR, hR, R, u0[0], t.fu[0]);
-    texel_coord(p1, sR, hR, R, u0[1], t.fu[1]);
-    texel_coord(p2, sR, hR, R, u0[2], t.fu[2]);
+    plane_coord(p0, sR, hR, R, u0[0], t.fu[0]);
+    plane_coord(p1, sR, hR, R, u0[1], t.fu[1]);
+    plane_coord(p2, sR, hR, R, u0[2], t.fu[2]);
     // plane q: columns along axis (1, 0, 0)[q], rows along axis (2, 2, 1)[q]
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         const int ca = q == 0 ? 1 : 0, ra = q == 2 ? 1 : 2;
-        const uint2 *base = fv.planes + ((size_t)q * R + u0[ra]) * R + u0[ca];
+        const uint2 *base = fv.planes + ((size_t)q * Rp + u0[ra]) * Rp + u0[ca];
         t.v[8 + 4 * q + 0] = __ldg(base);
         t.v[8 + 4 * q + 1] = __ldg(base + 1);
-        t.v[8 + 4 * q + 2] = __ldg(base + R);
-        t.v[8 + 4 * q + 3] = __ldg(base + R + 1);
+        t.v[8 + 4 * q + 2] = __ldg(base + Rp);
+        t.v[8 + 4 * q + 3] = __ldg(base + Rp + 1);
     }
 }
 

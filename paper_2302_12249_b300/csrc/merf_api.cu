@@ -220,14 +220,18 @@ merf_status launch_render(const merf_scene *s, const merf_camera *cams, int n, i
         P.cam0 = c0;
         for (int c = 0; c < nc; ++c) memcpy(P.cams.m[c], &cams[c0 + c], sizeof(merf_camera));
         const dim3 grid((W + merf::kTileW - 1) / merf::kTileW, (H + merf::kTileH - 1) / merf::kTileH, nc);
+        const bool paper = merf::paper_geometry(s->desc);
         if (s->desc.storage == MERF_STORAGE_F32_DENSE)
-            merf::render_kernel<1, 0><<<grid, block, 0, st>>>(P);
+            merf::render_kernel<1, 0, merf::kGeoRuntime><<<grid, block, 0, st>>>(P);
         else if (o->precision == MERF_PREC_FP16)
-            merf::render_kernel<0, 1><<<grid, block, 0, st>>>(P);
+            paper ? merf::render_kernel<0, 1, merf::kGeoPaper><<<grid, block, 0, st>>>(P)
+                  : merf::render_kernel<0, 1, merf::kGeoRuntime><<<grid, block, 0, st>>>(P);
         else if (o->precision == MERF_PREC_BF16)
-            merf::render_kernel<0, 2><<<grid, block, 0, st>>>(P);
+            paper ? merf::render_kernel<0, 2, merf::kGeoPaper><<<grid, block, 0, st>>>(P)
+                  : merf::render_kernel<0, 2, merf::kGeoRuntime><<<grid, block, 0, st>>>(P);
         else
-            merf::render_kernel<0, 0><<<grid, block, 0, st>>>(P);
+            paper ? merf::render_kernel<0, 0, merf::kGeoPaper><<<grid, block, 0, st>>>(P)
+                  : merf::render_kernel<0, 0, merf::kGeoRuntime><<<grid, block, 0, st>>>(P);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return fail(MERF_ERR_CUDA, "render launch: %s", cudaGetErrorString(e));
     }
@@ -309,7 +313,22 @@ merf_status merf_scene_upload(const merf_scene_desc *desc, const int32_t *index_
                             memcpy(dst + (((size_t)lz * B1 + ly) * B1 + lx) * 8, sv, 8);
                         }
             }
-    return upload_common(desc, apron.data(), apron.size(), planes, 3 * R * R * 8, ig.data(),
+    // Each plane gets a one-texel border that repeats its edge texels, so that bilinear taps of
+    // clamp-to-edge interpolation never need their coordinates clamped: [3][R+2][R+2].
+    const size_t Rp = R + 2;
+    std::vector<uint8_t> padded;
+    try {
+        padded.resize(3 * Rp * Rp * 8);
+    } catch (...) {
+        return fail(MERF_ERR_OOM, "host memory for the bordered planes");
+    }
+    for (size_t q = 0; q < 3; ++q)
+        for (size_t v = 0; v < Rp; ++v)
+            for (size_t u = 0; u < Rp; ++u) {
+                const size_t sv = v == 0 ? 0 : v > R ? R - 1 : v - 1, su = u == 0 ? 0 : u > R ? R - 1 : u - 1;
+                memcpy(padded.data() + ((q * Rp + v) * Rp + u) * 8, planes + ((q * R + sv) * R + su) * 8, 8);
+            }
+    return upload_common(desc, apron.data(), apron.size(), padded.data(), padded.size(), ig.data(),
                          nb * nb * nb * sizeof(int32_t), occ_levels, mlp_weights, stream, out);
 }
 

@@ -66,7 +66,7 @@ struct ServeParams {
     int early_term;
 };
 
-template <int kPrec>
+template <int kPrec, int kGeo>
 __global__ void __launch_bounds__(kThreads, (kMinBlocks<0, kPrec>)) serve_kernel(const __grid_constant__ ServeParams P)
 {
     __shared__ MlpSmem<kPrec> ms;
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kThreads, (kMinBlocks<0, kPrec>)) serve_kernel
         RayState r;
         ray_state_init(r);
         if (inside)
-            march_ray<0, kPrec>(P.scenes[sc].fv, P.scenes[sc].occ, R.cam, i, j, P.step, P.t_term, P.early_term, r);
+            march_ray<0, kPrec, kGeo>(P.scenes[sc].fv, P.scenes[sc].occ, R.cam, i, j, P.step, P.t_term, P.early_term, r);
         float h[3];
         deferred_mlp<kPrec>(ms, r, inside, h);
         if (inside) {
@@ -321,7 +321,7 @@ struct merf_server {
 
 namespace {
 
-template <int kPrec>
+template <int kPrec, int kGeo>
 merf_status capture(merf_server *s, int b)
 {
     cudaStream_t cs;
@@ -331,7 +331,7 @@ merf_status capture(merf_server *s, int b)
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_work[b], s->h_work[b], sizeof(merf::ServeWork), cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_counter + b, 0, sizeof(int), cs);
     if (e == cudaSuccess) {
-        merf::serve_kernel<kPrec><<<s->grid, merf::kThreads, 0, cs>>>(s->params[b]);
+        merf::serve_kernel<kPrec, kGeo><<<s->grid, merf::kThreads, 0, cs>>>(s->params[b]);
         e = cudaGetLastError();
     }
     cudaGraph_t g = nullptr;
@@ -344,13 +344,13 @@ merf_status capture(merf_server *s, int b)
     return MERF_OK;
 }
 
-template <int kPrec>
+template <int kPrec, int kGeo>
 int resident_grid()
 {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, merf::serve_kernel<kPrec>, merf::kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, merf::serve_kernel<kPrec, kGeo>, merf::kThreads, 0);
     return std::max(1, sms) * std::max(1, per);
 }
 
@@ -407,7 +407,15 @@ merf_status merf_server_create(const merf_scene *const *scenes, int n_scenes, co
     s->n_scenes = n_scenes;
     cudaGetDevice(&s->device);
     const int prec = opts->precision;
-    s->grid = prec == MERF_PREC_FP16 ? resident_grid<1>() : prec == MERF_PREC_BF16 ? resident_grid<2>() : resident_grid<0>();
+    // one persistent kernel serves every scene: the paper-geometry gather only if all have it
+    bool paper = true;
+    for (int k = 0; k < n_scenes; ++k) paper = paper && merf::paper_geometry(scenes[k]->desc);
+    s->grid = paper ? (prec == MERF_PREC_FP16   ? resident_grid<1, merf::kGeoPaper>()
+                       : prec == MERF_PREC_BF16 ? resident_grid<2, merf::kGeoPaper>()
+                                                : resident_grid<0, merf::kGeoPaper>())
+                    : (prec == MERF_PREC_FP16   ? resident_grid<1, merf::kGeoRuntime>()
+                       : prec == MERF_PREC_BF16 ? resident_grid<2, merf::kGeoRuntime>()
+                                                : resident_grid<0, merf::kGeoRuntime>());
     cudaError_t e = cudaMalloc(&s->d_pool, opts->pool_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_counter, 2 * sizeof(int));
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
@@ -439,8 +447,13 @@ merf_status merf_server_create(const merf_scene *const *scenes, int n_scenes, co
         P.t_term = opts->t_term;
         P.early_term = opts->early_term;
         memset(s->h_work[b], 0, sizeof(int) * 4);
-        const merf_status st = prec == MERF_PREC_FP16 ? capture<1>(s, b) : prec == MERF_PREC_BF16 ? capture<2>(s, b)
-                                                                                                : capture<0>(s, b);
+        const merf_status st =
+            paper ? (prec == MERF_PREC_FP16   ? capture<1, merf::kGeoPaper>(s, b)
+                     : prec == MERF_PREC_BF16 ? capture<2, merf::kGeoPaper>(s, b)
+                                              : capture<0, merf::kGeoPaper>(s, b))
+                  : (prec == MERF_PREC_FP16   ? capture<1, merf::kGeoRuntime>(s, b)
+                     : prec == MERF_PREC_BF16 ? capture<2, merf::kGeoRuntime>(s, b)
+                                              : capture<0, merf::kGeoRuntime>(s, b));
         if (st != MERF_OK) {
             release(s);
             return st;

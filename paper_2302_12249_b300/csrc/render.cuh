@@ -383,7 +383,7 @@ struct RayState {
 };
 
 // March one pixel ray: traversal, gather, activations and front-to-back compositing.
-template <int kStorage, int kPrec>
+template <int kStorage, int kPrec, int kGeo = kGeoRuntime>
 __device__ __forceinline__ void march_ray(const FieldView &fv, const OccView &occ, const float *cam, int i, int j,
                                           float step, float t_term, int early_term, RayState &r)
 {
@@ -406,14 +406,14 @@ __device__ __forceinline__ void march_ray(const FieldView &fv, const OccView &oc
         // all channels in one tap-major pass; the appearance values are used only when the
         // opacity is non-zero (Sec. 5), which changes nothing else (weight alpha T = 0)
         if constexpr (kStorage == 0 && kPrec == 0) {
-            gather_u8(fv, p0, p1, p2, tp);
+            gather_u8<kGeo>(fv, p0, p1, p2, tp);
             float2 k[4];
             byte_sums_u8(tp, k);
             dens = dequant_density(k[0].x, tp.wv);
             ya = app_arg_u8(k, tp.wv);
         } else if constexpr (kStorage == 0) {
             // FP16 / BF16 appearance arithmetic; density in FP32 exactly as above
-            gather_u8(fv, p0, p1, p2, tp);
+            gather_u8<kGeo>(fv, p0, p1, p2, tp);
             float2 k[4];
             byte_sums_lp<kPrec>(tp, k);
             dens = dequant_density(k[0].x, tp.wv);
@@ -482,8 +482,9 @@ __device__ __forceinline__ void deferred_mlp(MlpSmem<kPrec> &ms, const RayState 
 template <int kStorage, int kPrec>
 constexpr int kMinBlocks = kStorage != 0 ? 4 : kPrec == 0 ? 6 : 5;
 
-template <int kStorage, int kPrec>   // storage 0: uint8 block-sparse, 1: float32 dense;
-                                     // precision 0: FP32, 1: FP16, 2: BF16 (uint8 storage only)
+template <int kStorage, int kPrec, int kGeo>   // storage 0: uint8 block-sparse, 1: float32 dense;
+                                               // precision 0: FP32, 1: FP16, 2: BF16 (uint8 only);
+                                               // kGeo: gather geometry (kGeoRuntime / kGeoPaper)
 __global__ void __launch_bounds__(kThreads, (kMinBlocks<kStorage, kPrec>)) render_kernel(const __grid_constant__ RenderParams P)
 {
     __shared__ MlpSmem<kPrec> ms;
@@ -496,7 +497,7 @@ __global__ void __launch_bounds__(kThreads, (kMinBlocks<kStorage, kPrec>)) rende
     const bool inside = (i < P.W) && (j < P.H);
     RayState r;
     ray_state_init(r);
-    if (inside) march_ray<kStorage, kPrec>(P.fv, P.occ, P.cams.m[cl], i, j, P.step, P.t_term, P.early_term, r);
+    if (inside) march_ray<kStorage, kPrec, kGeo>(P.fv, P.occ, P.cams.m[cl], i, j, P.step, P.t_term, P.early_term, r);
     float h[3];
     deferred_mlp<kPrec>(ms, r, inside, h);
     if (inside) {

@@ -51,6 +51,12 @@ inline void scene_views(const merf_scene *s, FieldView &fv, OccView &occ)
     }
 }
 
+// True when the gather may use the kernels compiled for the paper's geometry (kGeoPaper).
+inline bool paper_geometry(const merf_scene_desc &d)
+{
+    return d.storage == MERF_STORAGE_U8_SPARSE && d.grid_res == 512 && d.block_size == 16 && d.plane_res == 2048;
+}
+
 // Thread-local error message of the C ABI (defined in merf_api.cu).
 merf_status set_error(merf_status s, const char *fmt, ...);
 merf_status clear_error();
