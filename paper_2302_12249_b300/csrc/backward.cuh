@@ -194,11 +194,9 @@ static __global__ void __launch_bounds__(kThreads) backward_kernel(const __grid_
         Walker wk;
         wk.init(o, d, P.step);
         float T = 1.0f, A = 0.0f;
-        int run_end = 0;
         for (;;) {
-            if (wk.k >= run_end && !wk.next_run(P.occ, run_end)) break;
             float p0, p1, p2;
-            wk.position(wk.k, p0, p1, p2);
+            if (!wk.next_sample(P.occ, p0, p1, p2)) break;
             float t8[8];
             field_f32(P.fv, p0, p1, p2, t8);
             const float tau = __expf(t8[0]);

@@ -1,10 +1,11 @@
 // render.cuh -- fused per-ray render kernel and traversal-only kernel for sm_103a.
 //
 // One thread renders one pixel ray end to end: ray generation, segment table, lattice walk
-// with coarse-to-fine empty-space skipping (occupied samples come in runs that share a finest
-// occupancy cell), gather of the 20 texels of each evaluated sample, density-first activation
-// (Sec. 5: appearance is unpacked only when the sample's opacity is non-zero), front-to-back compositing of C_d and F with early termination
-// (Eq. 1, Eq. 2, Sec. 5), and finally the deferred MLP h(C_d, F, d) (Sec. 2, App. B), whose
+// with a per-sample finest-cell test and coarse-to-fine empty-space skipping, gather of the 20
+// texels of each evaluated sample, all eight channels interpolated in one tap-major pass (the
+// appearance values enter the result only when the sample's opacity is non-zero, Sec. 5),
+// front-to-back compositing of C_d and F with early termination (Eq. 1, Eq. 2, Sec. 5), and
+// finally the deferred MLP h(C_d, F, d) (Sec. 2, App. B), whose
 // 883 weights are staged once per CTA in shared memory and read as warp-wide broadcasts.
 // A warp covers an 8 x 4 pixel tile and a CTA a 16 x 8 tile, so neighbouring rays walk
 // neighbouring texels together and share L1 lines.
@@ -392,14 +393,12 @@ __device__ __forceinline__ void march_ray(const FieldView &fv, const OccView &oc
     Walker wk;
     wk.init(o, r.d, step);
     r.nlat = wk.nlat;
-    int run_end = 0;
     Accum acc;
     acc.c0 = 0.0f;
     acc.c12 = acc.f01 = acc.f23 = make_float2(0.0f, 0.0f);
     for (;;) {
-        if (wk.k >= run_end && !wk.next_run(occ, run_end)) break;
         float p0, p1, p2;
-        wk.position(wk.k, p0, p1, p2);
+        if (!wk.next_sample(occ, p0, p1, p2)) break;
         float dens;
         AppArg ya;
         Taps tp;
@@ -546,10 +545,10 @@ static __global__ void __launch_bounds__(kThreads) trace_kernel(const __grid_con
     Walker wk;
     wk.init(o, d, P.step);
     P.nlat[pix] = wk.nlat;
-    int run_end = 0;
-    while (wk.next_run(P.occ, run_end)) {
-        for (; wk.k < run_end; ++wk.k)
-            if (wk.k < 32 * P.words) row[wk.k >> 5] |= 1u << (wk.k & 31);
+    float p0, p1, p2;
+    while (wk.next_sample(P.occ, p0, p1, p2)) {
+        if (wk.k < 32 * P.words) row[wk.k >> 5] |= 1u << (wk.k & 31);
+        ++wk.k;
     }
 }
 

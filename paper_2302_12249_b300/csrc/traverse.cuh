@@ -4,12 +4,12 @@
 // (Sec. 3.2) into [-2, 2]^3, where it becomes at most seven straight segments, one per region
 // it crosses.  Samples sit on a uniform lattice s_k = (k + 1/2) delta_s of cumulative contracted
 // arc length (the renderer's "small uniform step size", Sec. 4.3); sample k is evaluated iff
-// its finest occupancy cell is set.  Empty space is skipped coarse-to-fine against the
-// max-pooled occupancy hierarchy (Sec. 5): when a level reports the sample's cell empty, a
-// slab test against that cell's box on the current straight segment gives the exit, and the
-// walk jumps past the last lattice sample before it.  When every level reports the cell
-// occupied, the same exit test on the finest cell yields the run of consecutive samples
-// that share it, and the run is evaluated without querying the hierarchy again.
+// its finest occupancy cell is set.  Each candidate sample reads its own finest cell (one
+// cached byte: the test is the definition itself, and every lane of a warp does the same
+// work).  A sample in an empty finest cell starts a skip through the max-pooled occupancy
+// hierarchy (Sec. 5): the coarsest level that reports its cell empty gives the largest empty
+// box around it, a slab test against that box on the current straight segment gives the exit,
+// and the walk jumps past the last lattice sample before it.
 //
 // Exactness.  Every float operation that decides an integer (which lattice samples exist,
 // which segment and which occupancy cell a sample falls in) is an IEEE round-to-nearest
@@ -330,30 +330,30 @@ struct Walker {
         return k + 1;
     }
 
-    // Advance k to the next occupied lattice sample and return the end (exclusive) of the run
-    // of samples that share its finest occupancy cell: they are all evaluated without querying
-    // the hierarchy again.  False when the ray has no further occupied sample.
-    __device__ __forceinline__ bool next_run(const OccView &occ, int &run_end)
+    // Advance k to the next lattice sample whose own finest occupancy cell is set and return
+    // its position.  A sample in an empty finest cell starts a skip out of the largest empty
+    // cell that contains it (coarse-to-fine: the first empty level from the coarsest), through
+    // cell_exit's verified jump.  False when the ray has no further occupied sample.
+    __device__ __forceinline__ bool next_sample(const OccView &occ, float &p0, float &p1, float &p2)
     {
         const int N0 = occ.res[0];
         const float sc0 = (float)N0 * 0.25f;
         const int h0 = N0 >> 1;
         while (k < nlat) {
             while (k >= kend) load_seg(seg + 1);
-            float p0, p1, p2;
             position(k, p0, p1, p2);
             const int c0 = cell_of(p0, sc0, h0, N0), c1 = cell_of(p1, sc0, h0, N0),
                       c2 = cell_of(p2, sc0, h0, N0);
-            int lvl = -1;
-            for (int l = occ.n - 1; l >= 0; --l) {
-                const int sh = occ.shift[l], Nl = occ.res[l];
-                const int x = c0 >> sh, y = c1 >> sh, z = c2 >> sh;
-                if (__ldg(occ.level[l] + ((size_t)z * Nl + y) * Nl + x) == 0) { lvl = l; break; }
+            if (__ldg(occ.level[0] + ((size_t)c2 * N0 + c1) * N0 + c0) != 0) return true;
+            int sh = 0;
+            for (int l = occ.n - 1; l > 0; --l) {
+                const int s = occ.shift[l], Nl = occ.res[l];
+                if (__ldg(occ.level[l] + ((size_t)(c2 >> s) * Nl + (c1 >> s)) * Nl + (c0 >> s)) == 0) {
+                    sh = s;
+                    break;
+                }
             }
-            const int sh = lvl < 0 ? 0 : occ.shift[lvl];
-            const int nk = cell_exit(p0, p1, p2, c0 >> sh, c1 >> sh, c2 >> sh, sh, N0, sc0, h0);
-            if (lvl < 0) { run_end = nk; return true; }
-            k = nk;
+            k = cell_exit(p0, p1, p2, c0 >> sh, c1 >> sh, c2 >> sh, sh, N0, sc0, h0);
         }
         return false;
     }
