@@ -170,12 +170,17 @@ constexpr int kW0Stride = 28, kW1Stride = 12, kXStride = 28;   // 32-bit words p
 // BF16 keeps only 8 significant bits, so in that mode every operand is carried as an unevaluated
 // sum hi + lo of two bfloat16 values and each product takes three tensor-core passes
 // (hi*hi + lo*hi + hi*lo, all accumulated in FP32); FP16 uses one pass.
+// Shared memory is kept small (it is carved out of the same on-chip storage as the L1 cache
+// that serves the texel gathers): only BF16 stores low parts, and each warp stages the input
+// rows of one 16-pixel tile at a time.
+template <int kPrec>
 struct MlpTC {
-    uint32_t w0[2][16 * kW0Stride];   // W0^T [n][k], k < 48, 16-bit pairs; [1]: BF16 low parts
-    uint32_t w1[2][16 * kW1Stride];   // W1^T [n][k], k < 16
-    uint32_t w2[2][8 * kW1Stride];    // W2^T [n][k], n < 3 used
+    static constexpr int kParts = kPrec == 2 ? 2 : 1;
+    uint32_t w0[kParts][16 * kW0Stride];   // W0^T [n][k], k < 48, 16-bit pairs; [1]: BF16 low parts
+    uint32_t w1[kParts][16 * kW1Stride];   // W1^T [n][k], k < 16
+    uint32_t w2[kParts][8 * kW1Stride];    // W2^T [n][k], n < 3 used
     float b0[16], b1[16], b2[8];
-    uint32_t x[2][kThreads / 32][32 * kXStride];   // per-warp input rows; [1]: BF16 low parts
+    uint32_t x[kParts][kThreads / 32][16 * kXStride];   // per-warp rows of one tile; [1]: BF16 low parts
 };
 
 template <int kPrec>
@@ -221,7 +226,7 @@ __device__ __forceinline__ void mma16816(float d[4], const uint32_t a[4], uint32
 
 // Stage the scene's FP32 weights as transposed 16-bit tiles (whole CTA, before a barrier).
 template <int kPrec>
-__device__ __forceinline__ void mlp_tc_load(MlpTC &ms, const float *w)
+__device__ __forceinline__ void mlp_tc_load(MlpTC<kPrec> &ms, const float *w)
 {
     const float *W0 = w, *B0 = w + 544, *W1 = w + 560, *B1 = w + 816, *W2 = w + 832, *B2 = w + 880;
     for (int e = threadIdx.x; e < 16 * 24; e += kThreads) {
@@ -229,19 +234,19 @@ __device__ __forceinline__ void mlp_tc_load(MlpTC &ms, const float *w)
         const float a = kk < 34 ? __ldg(W0 + kk * 16 + n) : 0.0f;
         const float b = kk + 1 < 34 ? __ldg(W0 + (kk + 1) * 16 + n) : 0.0f;
         ms.w0[0][n * kW0Stride + e % 24] = pack16<kPrec>(a, b);
-        if (kPrec == 2) ms.w0[1][n * kW0Stride + e % 24] = pack16_lo<kPrec>(a, b);
+        if constexpr (kPrec == 2) ms.w0[1][n * kW0Stride + e % 24] = pack16_lo<kPrec>(a, b);
     }
     for (int e = threadIdx.x; e < 16 * 8; e += kThreads) {
         const int n = e / 8, kk = 2 * (e % 8);
         const float a = __ldg(W1 + kk * 16 + n), b = __ldg(W1 + (kk + 1) * 16 + n);
         ms.w1[0][n * kW1Stride + e % 8] = pack16<kPrec>(a, b);
-        if (kPrec == 2) ms.w1[1][n * kW1Stride + e % 8] = pack16_lo<kPrec>(a, b);
+        if constexpr (kPrec == 2) ms.w1[1][n * kW1Stride + e % 8] = pack16_lo<kPrec>(a, b);
     }
     for (int e = threadIdx.x; e < 8 * 8; e += kThreads) {
         const int n = e / 8, kk = 2 * (e % 8);
         const float a = n < 3 ? __ldg(W2 + kk * 3 + n) : 0.0f, b = n < 3 ? __ldg(W2 + (kk + 1) * 3 + n) : 0.0f;
         ms.w2[0][n * kW1Stride + e % 8] = pack16<kPrec>(a, b);
-        if (kPrec == 2) ms.w2[1][n * kW1Stride + e % 8] = pack16_lo<kPrec>(a, b);
+        if constexpr (kPrec == 2) ms.w2[1][n * kW1Stride + e % 8] = pack16_lo<kPrec>(a, b);
     }
     for (int e = threadIdx.x; e < 16; e += kThreads) {
         ms.b0[e] = __ldg(B0 + e);
@@ -274,14 +279,16 @@ __device__ __forceinline__ void mma_acc(float d[4], const uint32_t a[4], const u
     }
 }
 
-// All 32 lanes of the warp call this together (lanes without a pixel pass zeros).
+// All 32 lanes of the warp call this together (lanes without a pixel pass zeros).  The warp's
+// pixels form two 16-row tiles (lanes 0-15, 16-31), evaluated one after the other.
 template <int kPrec>
-__device__ __forceinline__ void mlp_tc(MlpTC &ms, const float cd[3], const float f[4], const float d[3],
+__device__ __forceinline__ void mlp_tc(MlpTC<kPrec> &ms, const float cd[3], const float f[4], const float d[3],
                                        float out[3])
 {
-    const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
-    uint32_t *xs = ms.x[0][threadIdx.x >> 5];
-    uint32_t *xl = ms.x[1][threadIdx.x >> 5];
+    constexpr int hi = 0, lo = MlpTC<kPrec>::kParts - 1;
+    const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3, row = lane & 15;
+    uint32_t *xs = ms.x[hi][threadIdx.x >> 5];
+    uint32_t *xl = ms.x[lo][threadIdx.x >> 5];
     float x[48];
     x[0] = cd[0]; x[1] = cd[1]; x[2] = cd[2];
     x[3] = f[0]; x[4] = f[1]; x[5] = f[2]; x[6] = f[3];
@@ -299,74 +306,75 @@ __device__ __forceinline__ void mlp_tc(MlpTC &ms, const float cd[3], const float
     }
 #pragma unroll
     for (int k = 34; k < 48; ++k) x[k] = 0.0f;
-    __syncwarp();
 #pragma unroll
-    for (int j = 0; j < 24; ++j) {
-        xs[lane * kXStride + j] = pack16<kPrec>(x[2 * j], x[2 * j + 1]);
-        if (kPrec == 2) xl[lane * kXStride + j] = pack16_lo<kPrec>(x[2 * j], x[2 * j + 1]);
-    }
-    __syncwarp();
-
-    float acc[2][2][4];
+    for (int t = 0; t < 2; ++t) {
+        __syncwarp();
+        if ((lane >> 4) == t) {
 #pragma unroll
-    for (int t = 0; t < 2; ++t)
+            for (int j = 0; j < 24; ++j) {
+                xs[row * kXStride + j] = pack16<kPrec>(x[2 * j], x[2 * j + 1]);
+                if constexpr (kPrec == 2) xl[row * kXStride + j] = pack16_lo<kPrec>(x[2 * j], x[2 * j + 1]);
+            }
+        }
+        __syncwarp();
+        // layer 1: [16 x 48] x [48 x 16]
+        float acc[2][4];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-            acc[t][u][0] = acc[t][u][2] = ms.b0[8 * u + 2 * c];
-            acc[t][u][1] = acc[t][u][3] = ms.b0[8 * u + 2 * c + 1];
+            acc[u][0] = acc[u][2] = ms.b0[8 * u + 2 * c];
+            acc[u][1] = acc[u][3] = ms.b0[8 * u + 2 * c + 1];
         }
 #pragma unroll
-    for (int sl = 0; sl < 3; ++sl)
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            const int r0 = (16 * t + g) * kXStride + 8 * sl + c, r1 = r0 + 8 * kXStride;
+        for (int sl = 0; sl < 3; ++sl) {
+            const int r0 = g * kXStride + 8 * sl + c, r1 = r0 + 8 * kXStride;
             const uint32_t a[4] = {xs[r0], xs[r1], xs[r0 + 4], xs[r1 + 4]};
             uint32_t al[4] = {0u, 0u, 0u, 0u};
-            if (kPrec == 2) { al[0] = xl[r0]; al[1] = xl[r1]; al[2] = xl[r0 + 4]; al[3] = xl[r1 + 4]; }
+            if constexpr (kPrec == 2) { al[0] = xl[r0]; al[1] = xl[r1]; al[2] = xl[r0 + 4]; al[3] = xl[r1 + 4]; }
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 const int wi = (8 * u + g) * kW0Stride + 8 * sl + c;
-                mma_acc<kPrec>(acc[t][u], a, al, ms.w0[0][wi], ms.w0[0][wi + 4], ms.w0[1][wi], ms.w0[1][wi + 4]);
+                mma_acc<kPrec>(acc[u], a, al, ms.w0[hi][wi], ms.w0[hi][wi + 4], ms.w0[lo][wi], ms.w0[lo][wi + 4]);
             }
         }
-    float acc2[2][2][4];
+        // layer 2: [16 x 16] x [16 x 16]
+        float acc2[2][4];
+        {
+            uint32_t a[4], al[4];
+            relu_pack<kPrec>(acc[0], acc[1], a, al);
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
-        uint32_t a[4], al[4];
-        relu_pack<kPrec>(acc[t][0], acc[t][1], a, al);
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            acc2[t][u][0] = acc2[t][u][2] = ms.b1[8 * u + 2 * c];
-            acc2[t][u][1] = acc2[t][u][3] = ms.b1[8 * u + 2 * c + 1];
-            const int wi = (8 * u + g) * kW1Stride + c;
-            mma_acc<kPrec>(acc2[t][u], a, al, ms.w1[0][wi], ms.w1[0][wi + 4], ms.w1[1][wi], ms.w1[1][wi + 4]);
+            for (int u = 0; u < 2; ++u) {
+                acc2[u][0] = acc2[u][2] = ms.b1[8 * u + 2 * c];
+                acc2[u][1] = acc2[u][3] = ms.b1[8 * u + 2 * c + 1];
+                const int wi = (8 * u + g) * kW1Stride + c;
+                mma_acc<kPrec>(acc2[u], a, al, ms.w1[hi][wi], ms.w1[hi][wi + 4], ms.w1[lo][wi], ms.w1[lo][wi + 4]);
+            }
         }
-    }
-    float acc3[2][4];
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-        uint32_t a[4], al[4];
-        relu_pack<kPrec>(acc2[t][0], acc2[t][1], a, al);
-        acc3[t][0] = acc3[t][2] = ms.b2[2 * c];
-        acc3[t][1] = acc3[t][3] = ms.b2[2 * c + 1];
-        const int wi = g * kW1Stride + c;
-        mma_acc<kPrec>(acc3[t], a, al, ms.w2[0][wi], ms.w2[0][wi + 4], ms.w2[1][wi], ms.w2[1][wi + 4]);
-    }
-    // the 32 x 3 outputs go back to their pixels through shared memory
-    __syncwarp();
-    float *os = reinterpret_cast<float *>(xs);
-#pragma unroll
-    for (int t = 0; t < 2; ++t)
+        // layer 3: [16 x 16] x [16 x 8]
+        float acc3[4];
+        {
+            uint32_t a[4], al[4];
+            relu_pack<kPrec>(acc2[0], acc2[1], a, al);
+            acc3[0] = acc3[2] = ms.b2[2 * c];
+            acc3[1] = acc3[3] = ms.b2[2 * c + 1];
+            const int wi = g * kW1Stride + c;
+            mma_acc<kPrec>(acc3, a, al, ms.w2[hi][wi], ms.w2[hi][wi + 4], ms.w2[lo][wi], ms.w2[lo][wi + 4]);
+        }
+        // the tile's 16 x 3 outputs go back to their pixels through shared memory
+        __syncwarp();
+        float *os = reinterpret_cast<float *>(xs);
         if (c < 2) {
-            os[(16 * t + g) * 4 + 2 * c] = acc3[t][0];
-            os[(16 * t + g) * 4 + 2 * c + 1] = acc3[t][1];
-            os[(16 * t + g + 8) * 4 + 2 * c] = acc3[t][2];
-            os[(16 * t + g + 8) * 4 + 2 * c + 1] = acc3[t][3];
+            os[g * 4 + 2 * c] = acc3[0];
+            os[g * 4 + 2 * c + 1] = acc3[1];
+            os[(g + 8) * 4 + 2 * c] = acc3[2];
+            os[(g + 8) * 4 + 2 * c + 1] = acc3[3];
         }
-    __syncwarp();
-    out[0] = os[lane * 4 + 0];
-    out[1] = os[lane * 4 + 1];
-    out[2] = os[lane * 4 + 2];
+        __syncwarp();
+        if ((lane >> 4) == t) {
+            out[0] = os[row * 4 + 0];
+            out[1] = os[row * 4 + 1];
+            out[2] = os[row * 4 + 2];
+        }
+    }
     __syncwarp();
 }
 
@@ -461,7 +469,7 @@ struct MlpSmem<0> {
 };
 template <int kPrec>
 struct MlpSmem {
-    MlpTC tc;
+    MlpTC<kPrec> tc;
     __device__ __forceinline__ void load(const float *mlp) { mlp_tc_load<kPrec>(tc, mlp); }
 };
 
@@ -477,9 +485,9 @@ __device__ __forceinline__ void deferred_mlp(MlpSmem<kPrec> &ms, const RayState 
 }
 
 // Resident CTAs per SM the register allocation is bounded for (measured on the 8 x 1080p
-// paper-scale workload: the uint8 FP32 kernel is fastest at 6 (80 registers), FP16 and BF16 at 5).
+// paper-scale workload: the uint8 kernels are fastest at 6, i.e. 80 registers per thread).
 template <int kStorage, int kPrec>
-constexpr int kMinBlocks = kStorage != 0 ? 4 : kPrec == 0 ? 6 : 5;
+constexpr int kMinBlocks = kStorage != 0 ? 4 : 6;
 
 template <int kStorage, int kPrec, int kGeo>   // storage 0: uint8 block-sparse, 1: float32 dense;
                                                // precision 0: FP32, 1: FP16, 2: BF16 (uint8 only);
