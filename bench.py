@@ -5,7 +5,8 @@ feature-gather bandwidth roofline).
 One step renders 8 cameras at 1920 x 1080 (16.6 M pixel rays) of the paper-scale synthetic
 scene: 512^3 grid in 16^3 blocks, three 2048^2 planes, occupancy 128^3..16^3, step 1/256,
 cameras on a ring of radius 1.5.  Inputs are resident in HBM before timing; the scene
-(~620 MB) and each step's output (199 MB) exceed the 126 MB L2, so no flush is needed.
+(722 MB on the device) and each step's output (199 MB) exceed the 126 MB L2, so no flush is
+needed.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -37,6 +38,24 @@ WORKLOAD = ("paper-scale synthetic MERF scene (L=512 in 16^3 blocks, R=2048, uin
 # the density byte (20 B) and one 4-byte index-grid entry; per sample with non-zero opacity the
 # 7 appearance bytes of the same 20 texels (140 B); per ray the 12-byte RGB output.
 B_DENSITY, B_INDEX, B_APPEAR, B_OUT = 20, 4, 140, 12
+
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one timed 8-camera render
+# launch from an ncu capture of this workload; reported as roofline.traffic only while the
+# kernel sources hash to the value they were measured with (otherwise null).
+TRAFFIC_BYTES_PER_LAUNCH = (399.45 + 617.07) * 1e6
+TRAFFIC_SOURCES_SHA256 = "ff014fdba233fcf9ef86c4bf410a9d406700d7a73cc0ed6edc5343023220a1b3"
+
+
+def _sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2302_12249_b300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
 
 
 def _peaks():
@@ -411,7 +430,10 @@ def run_ours(args):
                          "appearance_per_ray": c[merf.CNT_APPEAR] / c[merf.CNT_RAYS],
                          "algorithmic_bytes_per_ray": alg_bytes / c[merf.CNT_RAYS]},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "traffic": None,
+                             "frac": achieved / peak,
+                             "traffic": (TRAFFIC_BYTES_PER_LAUNCH
+                                         if _sources_sha256() == TRAFFIC_SOURCES_SHA256 and n_cams == N_CAMS
+                                         else None),
                              "kernel": "render_kernel<0,0> (FP32)", "kernel_ms": mean_kern_ms,
                              "peak_source": peak_src},
                 "gpu_launches": args.steps,
