@@ -134,8 +134,40 @@ def _cpu_baseline(scene, cams, seconds: float = 12.0):
         oracle.render(osc, cams, W_IMG, H_IMG, STEP, pix=pix.astype(np.int32), threads=threads)
         rays += n
     dt = time.perf_counter() - t0
+    # the same oracle on one host thread, for ~3 s
+    rays1, t1 = 0, time.perf_counter()
+    while time.perf_counter() - t1 < 3.0:
+        n = 256
+        pix = np.stack([rng.integers(0, N_CAMS, n), rng.integers(0, W_IMG, n), rng.integers(0, H_IMG, n)], 1)
+        oracle.render(osc, cams, W_IMG, H_IMG, STEP, pix=pix.astype(np.int32), threads=1)
+        rays1 += n
+    dt1 = time.perf_counter() - t1
     return {"value": rays / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{rays} random pixel rays of the 8 x 1920x1080 frames ({dt:.1f} s, FP64, {threads} threads)"}
+            "sample": f"{rays} random pixel rays of the 8 x 1920x1080 frames ({dt:.1f} s, FP64, {threads} threads)",
+            "one_thread": {"value": rays1 / dt1 / 1e6, "unit": UNIT,
+                           "sample": f"{rays1} random pixel rays ({dt1:.1f} s, FP64, 1 thread)"}}
+
+
+def _frames_720p(gs, steps=10, warmup=3):
+    """Frames/s at 1280x720 (the paper's other viewer resolution): the same 8 ring cameras and
+    scene, FP32, CUDA-event time of `steps` launches after `warmup`."""
+    import torch
+    from paper_2302_12249_b300 import merf, synth
+    W, H = 1280, 720
+    cams = synth.config_cameras("paper", W=W, H=H)
+    out = torch.empty((cams.shape[0], H, W, 3), dtype=torch.float32, device="cuda")
+    for _ in range(warmup):
+        merf.render(gs, cams, W, H, STEP, out=out)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        merf.render(gs, cams, W, H, STEP, out=out)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    return {"frames_per_s": cams.shape[0] / (ms / 1e3), "mrays_per_s": cams.shape[0] * W * H / (ms / 1e3) / 1e6,
+            "ms_per_step": ms, "workload": f"{cams.shape[0]} ring cameras x {W}x{H}, FP32"}
 
 
 def _precision_form(gs, scene, n_cams=64, steps=2, n_pix=2000):
@@ -402,6 +434,9 @@ def run_ours(args):
         e2e = {"value": rays_per_step * world * args.steps / e2e_s / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": n_cams * 64, "d2h_bytes_per_step": int(out.numel() * 4)}
 
+    p720 = None
+    if rank == 0 and world == 1 and not args.no_precision:
+        p720 = _frames_720p(gs)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = _cpu_baseline(scene, cams)
@@ -425,6 +460,8 @@ def run_ours(args):
                            "l2": "inputs larger than L2 (scene and per-step output each exceed 126 MB); no flush",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "frames_per_s_1080p": value * 1e6 / (W_IMG * H_IMG),
+                "step_ms": {"mean": mean_kern_ms, "median": statistics.median(kern_ms), "min": min(kern_ms),
+                            "max": max(kern_ms), "frames": n_cams * args.steps},
                 "work": {"lattice_per_ray": c[merf.CNT_LATTICE] / c[merf.CNT_RAYS],
                          "evaluated_per_ray": c[merf.CNT_EVAL] / c[merf.CNT_RAYS],
                          "appearance_per_ray": c[merf.CNT_APPEAR] / c[merf.CNT_RAYS],
@@ -440,6 +477,8 @@ def run_ours(args):
                 "e2e": e2e, "clocks": ck}
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        if p720 is not None:
+            line["frames_720p"] = p720
         if precision is not None:
             line["precision_form"] = precision
         if differentiation is not None:

@@ -22,3 +22,10 @@ def tiny_scene():
 def tiny_oscene(tiny_scene):
     import oracle
     return oracle.OracleScene(tiny_scene)
+
+
+@pytest.fixture(scope="session")
+def paper_scene():
+    """The paper-scale synthetic scene (host arrays), built once per session."""
+    from paper_2302_12249_b300 import synth
+    return synth.make_scene("paper")

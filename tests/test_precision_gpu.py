@@ -44,9 +44,8 @@ def tiny(tiny_scene):
 
 
 @pytest.fixture(scope="module")
-def paper():
-    sc = synth.make_scene("paper")
-    return merf.Scene(sc), oracle.OracleScene(sc)
+def paper(paper_scene):
+    return merf.Scene(paper_scene), oracle.OracleScene(paper_scene)
 
 
 @pytest.mark.parametrize("prec", PRECS)

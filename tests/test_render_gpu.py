@@ -1,4 +1,5 @@
 """GPU parity of the FP32 render path against the FP64 oracle, through the C ABI."""
+import dataclasses
 import math
 
 import numpy as np
@@ -15,11 +16,6 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module")
 def tiny(tiny_scene):
     return merf.Scene(tiny_scene), oracle.OracleScene(tiny_scene)
-
-
-@pytest.fixture(scope="module")
-def paper_scene():
-    return synth.make_scene("paper")
 
 
 @pytest.fixture(scope="module")
@@ -199,6 +195,33 @@ def test_paper_scale_traversal_bit_exact(paper):
     cams = synth.config_cameras("paper", W=480, H=270, n=2)
     mask, nlat = merf.trace(gs, cams, 480, 270, 1 / 256, words=64)
     m_o, _, n_o = oracle.trace(osc, cams, 480, 270, 1 / 256, words=64, decide_f32=True)
+    np.testing.assert_array_equal(nlat.cpu().numpy(), n_o)
+    np.testing.assert_array_equal(mask.cpu().numpy().view(np.uint32), m_o)
+
+
+def test_paper_geometry_full_occupancy_reaches_the_edges(paper_scene):
+    """Every occupancy cell set on the paper-scale scene: nothing is skipped, so rays that do not
+    terminate are evaluated out to the limit point of contracted space, where the grid's
+    clamp-to-edge and the planes' border texels are read (the kernel compiled for the paper's
+    geometry).  Sampled pixels against the oracle, and the traversal bit for bit."""
+    sc = dataclasses.replace(paper_scene, occ=[np.ones_like(o) for o in paper_scene.occ])
+    gs, osc = merf.Scene(sc), oracle.OracleScene(sc)
+    # cameras in the shell looking outward, one along an axis: rays cross the outer shell to
+    # the limit point instead of ending in the central blobs
+    eyes = [(1.2, 0.3, 0.2), (-0.4, 1.3, -0.3), (0.0, 0.0, 1.4)]
+    cams = np.stack([synth.camera_record(synth.look_at(e, 3.0 * np.asarray(e), up=(0.3, 0.2, 1.0)), 240, 135)
+                     for e in eyes])
+    W, H, step = 240, 135, 1 / 256
+    rgb, aux = parity.gpu_render(gs, cams, W, H, step)
+    pix, lin = parity.pick_pixels(cams.shape[0], W, H, 1200, seed=5)
+    lo, hi = parity.oracle_rgb(osc, cams, W, H, step, pix=pix)
+    err = parity.max_err(rgb[lin], lo, hi)
+    assert err.max() <= parity.RGB_TOL, (err.max(), np.argmax(err))
+    a = aux[lin]
+    reached = a[:, merf.AUX_NEVAL] == a[:, merf.AUX_NLAT]
+    assert reached.sum() > 40                        # rays evaluated through to the far edge
+    mask, nlat = merf.trace(gs, cams[:1], W, H, step, words=_words(aux[:, merf.AUX_NLAT]))
+    m_o, _, n_o = oracle.trace(osc, cams[:1], W, H, step, words=mask.shape[-1], decide_f32=True)
     np.testing.assert_array_equal(nlat.cpu().numpy(), n_o)
     np.testing.assert_array_equal(mask.cpu().numpy().view(np.uint32), m_o)
 

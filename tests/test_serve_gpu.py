@@ -35,6 +35,23 @@ def test_single_request_equals_render(scenes, prec):
     assert (out - _reference(scenes[0], cam, 50, 37, prec)).abs().max().item() <= parity.RGB_TOL
 
 
+@pytest.mark.parametrize("prec", [merf.PREC_FP16, merf.PREC_FP32])
+def test_paper_geometry_request_equals_render(paper_scene, prec):
+    """With every resident scene in the paper's geometry the server runs the persistent kernel
+    compiled for it; a request's image is the one merf_render gives."""
+    g = merf.Scene(paper_scene)
+    cams = synth.config_cameras("paper", W=320, H=180, n=2)
+    srv = merf.Server([g], pool_bytes=1 << 26, step=1 / 256, precision=prec)
+    outs = [_host(320, 180) for _ in range(2)]
+    ids = [srv.submit(0, cams[k], 320, 180, outs[k]) for k in range(2)]
+    for rid in ids:
+        srv.wait(rid)
+    srv.close()
+    for k in range(2):
+        ref = merf.render(g, cams[k][None], 320, 180, 1 / 256, precision=prec)[0].cpu()
+        assert (outs[k] - ref).abs().max().item() <= parity.RGB_TOL
+
+
 def test_same_alone_and_in_the_mix(scenes):
     """A request's image does not depend on what shares its iterations."""
     cam = synth.sphere_cameras(1, 61, 45, radius=2.6, seed=51)[0]
