@@ -42,19 +42,20 @@ B_DENSITY, B_INDEX, B_APPEAR, B_OUT = 20, 4, 140, 12
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one timed 8-camera render
 # launch from an ncu capture of this workload; reported as roofline.traffic only while the
-# kernel sources hash to the value they were measured with (otherwise null).
+# render kernel's sources (device code, launch and scene layout) hash to the value they were
+# measured with (otherwise null).
 TRAFFIC_BYTES_PER_LAUNCH = (399.45 + 617.07) * 1e6
-TRAFFIC_SOURCES_SHA256 = "ff014fdba233fcf9ef86c4bf410a9d406700d7a73cc0ed6edc5343023220a1b3"
+TRAFFIC_SOURCES = ("field.cuh", "merf_api.cu", "render.cuh", "scene.h", "traverse.cuh")
+TRAFFIC_SOURCES_SHA256 = "b73b920e43fe00183a8d01f505d930f7620b7bf6154ef9bf45c22ff0ed1df61c"
 
 
 def _sources_sha256() -> str:
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2302_12249_b300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + b"\0" + f.read())
+    for name in TRAFFIC_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()
 
 

@@ -4,7 +4,8 @@
 //   1. recompute the forward march (same arithmetic, hence the same samples, opacities and
 //      termination) to get C_d, F;
 //   2. run the deferred MLP forward and backward in FP32: dL/dC_d = dL/dC + (dh/dC_d)^T dL/dC,
-//      dL/dF = (dh/dF)^T dL/dC, and the weight gradients, accumulated per CTA in shared memory;
+//      dL/dF = (dh/dF)^T dL/dC, and the weight gradients, summed over the warp's pixels as small
+//      matrix products in shared memory and accumulated per CTA;
 //   3. march again front to back, recomputing transmittance instead of storing per-sample
 //      state.  With G = (dL/dC_d, dL/dF), v_i = (c_i, f_i) and A_i = sum_{j<=i} w_j G.v_j, the
 //      gradient of Eq. 1 / Eq. 2 with respect to a sample's opacity is
@@ -77,17 +78,13 @@ __device__ __forceinline__ void scatter_f32(const FieldView &fv, float *g_grid, 
     }
 }
 
-__device__ __forceinline__ void smem_add(float *p, float v)
+// Deferred MLP forward + backward for one pixel (FP32), without the weight gradients: from
+// dL/dh = gh it returns x (the 34 inputs), a1, a2 (the ReLU activations), dz1, dz2 (gradients of
+// the two pre-activations) and dL/dx for x[0..6] = (C_d, F).
+__device__ __forceinline__ void mlp_backward_f32(const float *w, const float cd[3], const float f[4], const float d[3],
+                                                 const float gh[3], float x[34], float a1[16], float a2[16],
+                                                 float dz1[16], float dz2[16], float gx7[7])
 {
-    if (v != 0.0f) atomicAdd(p, v);
-}
-
-// Deferred MLP forward + backward for one pixel (FP32).  w: weights in shared memory, gw: the
-// CTA's weight-gradient accumulator.  Returns dL/dx for x[0..6] = (C_d, F).
-__device__ __forceinline__ void mlp_backward_f32(const float *w, float *gw, const float cd[3], const float f[4],
-                                                 const float d[3], const float gh[3], float gx7[7])
-{
-    float x[34];
     x[0] = cd[0]; x[1] = cd[1]; x[2] = cd[2];
     x[3] = f[0]; x[4] = f[1]; x[5] = f[2]; x[6] = f[3];
     x[7] = d[0]; x[8] = d[1]; x[9] = d[2];
@@ -103,68 +100,135 @@ __device__ __forceinline__ void mlp_backward_f32(const float *w, float *gw, cons
         }
     }
     const float *W0 = w, *b0 = w + 544, *W1 = w + 560, *b1 = w + 816, *W2 = w + 832;
-    float z1[16], z2[16];
 #pragma unroll
-    for (int o = 0; o < 16; ++o) z1[o] = b0[o];
+    for (int o = 0; o < 16; ++o) a1[o] = b0[o];
 #pragma unroll
     for (int i = 0; i < 34; ++i)
 #pragma unroll
-        for (int o = 0; o < 16; ++o) z1[o] = fmaf(x[i], W0[i * 16 + o], z1[o]);
+        for (int o = 0; o < 16; ++o) a1[o] = fmaf(x[i], W0[i * 16 + o], a1[o]);
 #pragma unroll
-    for (int o = 0; o < 16; ++o) z2[o] = b1[o];
+    for (int o = 0; o < 16; ++o) a1[o] = fmaxf(a1[o], 0.0f);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        const float a = fmaxf(z1[i], 0.0f);
+    for (int o = 0; o < 16; ++o) a2[o] = b1[o];
 #pragma unroll
-        for (int o = 0; o < 16; ++o) z2[o] = fmaf(a, W1[i * 16 + o], z2[o]);
-    }
-    float *gW0 = gw, *gb0 = gw + 544, *gW1 = gw + 560, *gb1 = gw + 816, *gW2 = gw + 832, *gb2 = gw + 880;
+    for (int i = 0; i < 16; ++i)
 #pragma unroll
-    for (int o = 0; o < 3; ++o) smem_add(gb2 + o, gh[o]);
-    float dz2[16];
+        for (int o = 0; o < 16; ++o) a2[o] = fmaf(a1[i], W1[i * 16 + o], a2[o]);
+    // ReLU derivative from the activations: a > 0 exactly where the pre-activation is
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-        const float a2 = fmaxf(z2[i], 0.0f);
+        a2[i] = fmaxf(a2[i], 0.0f);
         float acc = 0.0f;
 #pragma unroll
-        for (int o = 0; o < 3; ++o) {
-            smem_add(gW2 + i * 3 + o, a2 * gh[o]);
-            acc = fmaf(W2[i * 3 + o], gh[o], acc);
-        }
-        dz2[i] = z2[i] > 0.0f ? acc : 0.0f;
+        for (int o = 0; o < 3; ++o) acc = fmaf(W2[i * 3 + o], gh[o], acc);
+        dz2[i] = a2[i] > 0.0f ? acc : 0.0f;
     }
-    float dz1[16];
-#pragma unroll
-    for (int o = 0; o < 16; ++o) smem_add(gb1 + o, dz2[o]);
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-        const float a1 = fmaxf(z1[i], 0.0f);
         float acc = 0.0f;
 #pragma unroll
-        for (int o = 0; o < 16; ++o) {
-            if (a1 != 0.0f) smem_add(gW1 + i * 16 + o, a1 * dz2[o]);
-            acc = fmaf(W1[i * 16 + o], dz2[o], acc);
-        }
-        dz1[i] = z1[i] > 0.0f ? acc : 0.0f;
+        for (int o = 0; o < 16; ++o) acc = fmaf(W1[i * 16 + o], dz2[o], acc);
+        dz1[i] = a1[i] > 0.0f ? acc : 0.0f;
     }
 #pragma unroll
-    for (int o = 0; o < 16; ++o) smem_add(gb0 + o, dz1[o]);
-#pragma unroll
-    for (int i = 0; i < 34; ++i) {
+    for (int i = 0; i < 7; ++i) {
         float acc = 0.0f;
 #pragma unroll
-        for (int o = 0; o < 16; ++o) {
-            smem_add(gW0 + i * 16 + o, x[i] * dz1[o]);
-            acc = fmaf(W0[i * 16 + o], dz1[o], acc);
-        }
-        if (i < 7) gx7[i] = acc;
+        for (int o = 0; o < 16; ++o) acc = fmaf(W0[i * 16 + o], dz1[o], acc);
+        gx7[i] = acc;
     }
 }
 
-static __global__ void __launch_bounds__(kThreads) backward_kernel(const __grid_constant__ BackwardParams P)
+// Per-warp staging of the 32 pixels' MLP vectors for the weight gradients (rows padded to odd
+// strides, so that the 32 lanes writing their own rows hit 32 different banks).
+constexpr int kXs = 35, kVs = 17;
+constexpr int kStageFloats = 32 * kXs + 32 * kVs;      // phase 1: x and dz1; later phases reuse it
+
+// Weight gradients of the warp's 32 pixels, added into the CTA's accumulator gw (all 32 lanes
+// call; lanes without a pixel pass gh = 0, hence zero dz1, dz2).  Each parameter's gradient is a
+// sum over the pixels of an outer-product term, e.g. dL/dW0[i][o] = sum_p x_p[i] dz1_p[o]: the
+// vectors go through shared memory and lane l sums the column o = l mod 16 for the rows of its
+// parity, so each lane adds 17 + 8 + 2 distinct entries (plus biases) with no lane conflicts.
+__device__ __forceinline__ void mlp_weight_grads_warp(float *gw, float *st, const float x[34], const float a1[16],
+                                                      const float a2[16], const float dz1[16], const float dz2[16],
+                                                      const float gh[3])
+{
+    const int lane = threadIdx.x & 31, o = lane & 15, r0 = lane >> 4;
+    float *xs = st, *vs = st + 32 * kXs;
+    // W0 [34][16] and b0
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 34; ++i) xs[lane * kXs + i] = x[i];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) vs[lane * kVs + i] = dz1[i];
+    __syncwarp();
+    {
+        float acc[17], bsum = 0.0f;
+#pragma unroll
+        for (int m = 0; m < 17; ++m) acc[m] = 0.0f;
+#pragma unroll 2
+        for (int p = 0; p < 32; ++p) {
+            const float d = vs[p * kVs + o];
+            bsum += d;
+#pragma unroll
+            for (int m = 0; m < 17; ++m) acc[m] = fmaf(xs[p * kXs + r0 + 2 * m], d, acc[m]);
+        }
+#pragma unroll
+        for (int m = 0; m < 17; ++m)
+            if (acc[m] != 0.0f) atomicAdd(gw + (r0 + 2 * m) * 16 + o, acc[m]);
+        if (r0 == 0 && bsum != 0.0f) atomicAdd(gw + 544 + o, bsum);
+    }
+    // W1 [16][16] and b1
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) xs[lane * kVs + i] = a1[i];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) vs[lane * kVs + i] = dz2[i];
+    __syncwarp();
+    {
+        float acc[8], bsum = 0.0f;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) acc[m] = 0.0f;
+#pragma unroll 2
+        for (int p = 0; p < 32; ++p) {
+            const float d = vs[p * kVs + o];
+            bsum += d;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) acc[m] = fmaf(xs[p * kVs + r0 + 2 * m], d, acc[m]);
+        }
+#pragma unroll
+        for (int m = 0; m < 8; ++m)
+            if (acc[m] != 0.0f) atomicAdd(gw + 560 + (r0 + 2 * m) * 16 + o, acc[m]);
+        if (r0 == 0 && bsum != 0.0f) atomicAdd(gw + 816 + o, bsum);
+    }
+    // W2 [16][3] and b2
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) xs[lane * kVs + i] = a2[i];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) vs[lane * kVs + k] = gh[k];
+    __syncwarp();
+    {
+        float acc[2] = {0.0f, 0.0f}, bsum = 0.0f;
+        const int e1 = lane + 32;                  // entries lane and lane + 32 of the 48
+#pragma unroll 2
+        for (int p = 0; p < 32; ++p) {
+            acc[0] = fmaf(xs[p * kVs + lane / 3], vs[p * kVs + lane % 3], acc[0]);
+            if (e1 < 48) acc[1] = fmaf(xs[p * kVs + e1 / 3], vs[p * kVs + e1 % 3], acc[1]);
+            if (lane < 3) bsum += vs[p * kVs + lane];
+        }
+        if (acc[0] != 0.0f) atomicAdd(gw + 832 + lane, acc[0]);
+        if (e1 < 48 && acc[1] != 0.0f) atomicAdd(gw + 832 + e1, acc[1]);
+        if (lane < 3 && bsum != 0.0f) atomicAdd(gw + 880 + lane, bsum);
+    }
+    __syncwarp();
+}
+
+static __global__ void __launch_bounds__(kThreads, 4) backward_kernel(const __grid_constant__ BackwardParams P)
 {
     __shared__ float wsm[kMlpParams];
     __shared__ float gsm[kMlpParams];
+    __shared__ float stage[kThreads / 32][kStageFloats];
     for (int t = threadIdx.x; t < kMlpParams; t += kThreads) {
         wsm[t] = __ldg(P.mlp + t);
         gsm[t] = 0.0f;
@@ -173,15 +237,26 @@ static __global__ void __launch_bounds__(kThreads) backward_kernel(const __grid_
     int i, j;
     pixel_of_thread(i, j);
     const int cl = blockIdx.z;
-    if (i < P.W && j < P.H) {
-        const size_t pix = ((size_t)(P.cam0 + cl) * P.H + j) * P.W + i;
-        const float gC[3] = {P.d_out[pix * 3 + 0], P.d_out[pix * 3 + 1], P.d_out[pix * 3 + 2]};
-        const float *cam = P.cams.m[cl];
-        RayState r;
-        ray_state_init(r);
+    const bool live = i < P.W && j < P.H;
+    const size_t pix = live ? ((size_t)(P.cam0 + cl) * P.H + j) * P.W + i : 0;
+    const float *cam = P.cams.m[cl];
+    float gC[3] = {0.0f, 0.0f, 0.0f};
+    RayState r;
+    ray_state_init(r);
+    if (live) {
+        gC[0] = P.d_out[pix * 3 + 0];
+        gC[1] = P.d_out[pix * 3 + 1];
+        gC[2] = P.d_out[pix * 3 + 2];
         march_ray<1, 0>(P.fv, P.occ, cam, i, j, P.step, P.t_term, P.early_term, r);
-        float gx7[7];
-        mlp_backward_f32(wsm, gsm, r.cd, r.F, r.d, gC, gx7);
+    }
+    // the whole warp: MLP backward per lane, weight gradients reduced across the warp
+    float gx7[7];
+    {
+        float x[34], a1[16], a2[16], dz1[16], dz2[16];
+        mlp_backward_f32(wsm, r.cd, r.F, r.d, gC, x, a1, a2, dz1, dz2, gx7);
+        mlp_weight_grads_warp(gsm, stage[threadIdx.x >> 5], x, a1, a2, dz1, dz2, gC);
+    }
+    if (live) {
         const float Gc[3] = {gC[0] + gx7[0], gC[1] + gx7[1], gC[2] + gx7[2]};
         const float Gf[4] = {gx7[3], gx7[4], gx7[5], gx7[6]};
         const float Gtot = Gc[0] * r.cd[0] + Gc[1] * r.cd[1] + Gc[2] * r.cd[2] + Gf[0] * r.F[0] + Gf[1] * r.F[1] +
