@@ -76,7 +76,9 @@ typedef struct merf_camera {
 typedef struct merf_scene_desc {
     int32_t grid_res;        /* L: 3D grid resolution; even, a multiple of block_size */
     int32_t block_size;      /* B: block edge in voxels, a power of two (sparse storage) */
-    int32_t plane_res;       /* R: resolution of the three planes; even */
+    int32_t plane_res;       /* R: resolution of the three planes; even.  0 (uint8 storage only):
+                                a grid-only scene, t~ = V -- the SNeRG++-style baseline that
+                                Sec. 6 compares MERF with; `planes` is then ignored (may be NULL) */
     int32_t channels;        /* C: must be 8 */
     int32_t n_blocks;        /* stored blocks in the atlas (sparse storage) */
     int32_t n_occ_levels;    /* 1 .. MERF_MAX_OCC_LEVELS */
@@ -101,6 +103,7 @@ typedef struct merf_scene merf_scene;  /* opaque; owns device memory */
  *   index_grid  int32 [(L/B)^3]            block id in [0, n_blocks) or -1 (not stored)
  *   atlas       uint8 [n_blocks][B][B][B][8]
  *   planes      uint8 [3][R][R][8]         P_x(y,z) [z][y], P_y(x,z) [z][x], P_z(x,y) [y][x]
+ *                                          (NULL allowed when plane_res is 0: grid only)
  *   occ_levels  n_occ_levels pointers to uint8 [N][N][N], non-zero = occupied
  *   mlp_weights float32 [883]: W0[34][16], b0[16], W1[16][16], b1[16], W2[16][3], b2[3]
  * The layout is validated (ids in range, every coarse occupancy cell that is empty has

@@ -243,8 +243,10 @@ class OracleScene:
             s.storage = 0
             self._ig = np.ascontiguousarray(scene.index_grid, dtype=np.int32)
             self._atlas = np.ascontiguousarray(scene.atlas, dtype=np.uint8)
-            self._planes = np.ascontiguousarray(scene.planes, dtype=np.uint8)
-            s.index_grid, s.atlas, s.planes = self._ig.ctypes.data, self._atlas.ctypes.data, self._planes.ctypes.data
+            s.index_grid, s.atlas = self._ig.ctypes.data, self._atlas.ctypes.data
+            if scene.planes is not None:            # grid-only scenes (R = 0) have none
+                self._planes = np.ascontiguousarray(scene.planes, dtype=np.uint8)
+                s.planes = self._planes.ctypes.data
             s.n_blocks = scene.n_blocks
         else:
             s.storage = 1

@@ -10,6 +10,7 @@
  *   the contracted ray as straight segments, a uniform lattice of samples in contracted
  *   arc length, a sample evaluated iff its finest occupancy cell is set (Sec. 4.3, Sec. 5)
  *   field t~ = V + P_x + P_y + P_z, trilinear / bilinear            (Sec. 3.1, Eq. 3)
+ *   (grid-only scenes, R = 0: t~ = V, the SNeRG++-style baseline of Sec. 6)
  *   dequantisation 2 m k / 255 - m, m = 14 density, 7 otherwise     (Sec. 4.2)
  *   tau = exp(t~_0), c_d = sigmoid(t~_1..3), f = sigmoid(t~_4..7)   (Sec. 3.1, Eq. 4)
  *   front-to-back quadrature of C_d and F, T < 2e-4 termination      (Eq. 1, Eq. 2, Sec. 5)
@@ -280,9 +281,10 @@ void orc_field(const orc_scene *sc, const double p[3], double out[8], int *missi
                 for (int c = 0; c < C; ++c) out[c] += w * v[c];
             }
     if (missing) *missing = miss;
-    /* planes: (axis of columns, axis of rows) = P_x: (y, z), P_y: (x, z), P_z: (x, y) */
+    /* planes: (axis of columns, axis of rows) = P_x: (y, z), P_y: (x, z), P_z: (x, y).  A scene
+     * with R = 0 has none: the grid-only (SNeRG++-style) baseline of Sec. 6, t~ = V. */
     static const int col_axis[3] = {1, 0, 0}, row_axis[3] = {2, 2, 1};
-    for (int q = 0; q < 3; ++q) {
+    for (int q = 0; q < (sc->R > 0 ? 3 : 0); ++q) {
         int u[2], v[2];
         double wu, wv;
         lin(p[col_axis[q]], sc->R, &u[0], &u[1], &wu);

@@ -134,8 +134,14 @@ __device__ __forceinline__ void gather_grid_slow(const FieldView &fv, int x0, in
 
 // Scene geometry a gather is compiled for.  kGeoRuntime reads L, B and R from the FieldView;
 // kGeoPaper is the paper's configuration (L = 512 stored in 16^3 blocks, planes R = 2048;
-// Sec. 4), for which every stride, shift and scale below is a compile-time constant.
-constexpr int kGeoRuntime = 0, kGeoPaper = 1;
+// Sec. 4), for which every stride, shift and scale below is a compile-time constant;
+// kGeoGridOnly is a scene with no planes (R = 0, t~ = V: the SNeRG++-style baseline the paper
+// compares against in Sec. 6), L and B read at run time.
+constexpr int kGeoRuntime = 0, kGeoPaper = 1, kGeoGridOnly = 2;
+template <int kGeo>
+constexpr int kPlaneSources = kGeo == kGeoGridOnly ? 0 : 3;     // planes that add to the grid
+template <int kGeo>
+constexpr int kTaps = 8 + 4 * kPlaneSources<kGeo>;               // texels per sample
 
 template <int kGeo>
 __device__ __forceinline__ void gather_u8(const FieldView &fv, float p0, float p1, float p2, Taps &t)
@@ -180,6 +186,7 @@ __device__ __forceinline__ void gather_u8(const FieldView &fv, float p0, float p
     } else {
         gather_grid_slow(fv, x0, y0, z0, t);
     }
+    if constexpr (kGeo == kGeoGridOnly) return;
     const float sR = (float)Rg * 0.25f;
     const int hR = Rg >> 1, R = Rg, Rp = Rg + 2;
     int u0[3];
@@ -198,11 +205,13 @@ __device__ __forceinline__ void gather_u8(const FieldView &fv, float p0, float p
     }
 }
 
-// Density pre-activation from its weighted byte sum k: (28 / 255) k - 14 (W_V + 3).  Every
-// path that evaluates density calls this one expression, so their opacities agree bit for bit.
-__device__ __forceinline__ float dequant_density(float k, float wv)
+// Density pre-activation from its weighted byte sum k: (28 / 255) k - 14 W, where W = W_V + 3
+// is the total interpolation weight of the sources (the planes' weights sum to one each; W = W_V
+// for a grid-only scene).  Every path that evaluates density calls this one expression, so their
+// opacities agree bit for bit.
+__device__ __forceinline__ float dequant_density(float k, float wsum)
 {
-    return k * (28.0f / 255.0f) - 14.0f * (wv + 3.0f);
+    return k * (28.0f / 255.0f) - 14.0f * wsum;
 }
 
 
@@ -229,18 +238,22 @@ __device__ __forceinline__ void accumulate_tap(const Taps &t, float2 acc[4])
     acc[3] = __ffma2_rn(ww, byte_pair_f<2>(t.v[i].y), acc[3]);
 }
 
-// Weighted byte sums of all eight channels, as the pairs (0, 1), (2, 3), (4, 5), (6, 7).
+// Weighted byte sums of all eight channels, as the pairs (0, 1), (2, 3), (4, 5), (6, 7), over
+// the first nt taps (20: grid and planes; 8: grid only).
+template <int nt = 20>
 __device__ __forceinline__ void byte_sums_u8(const Taps &t, float2 acc[4])
 {
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[j] = make_float2(0.0f, 0.0f);
     accumulate_tap<0>(t, acc);  accumulate_tap<1>(t, acc);  accumulate_tap<2>(t, acc);
     accumulate_tap<3>(t, acc);  accumulate_tap<4>(t, acc);  accumulate_tap<5>(t, acc);
-    accumulate_tap<6>(t, acc);  accumulate_tap<7>(t, acc);  accumulate_tap<8>(t, acc);
-    accumulate_tap<9>(t, acc);  accumulate_tap<10>(t, acc); accumulate_tap<11>(t, acc);
-    accumulate_tap<12>(t, acc); accumulate_tap<13>(t, acc); accumulate_tap<14>(t, acc);
-    accumulate_tap<15>(t, acc); accumulate_tap<16>(t, acc); accumulate_tap<17>(t, acc);
-    accumulate_tap<18>(t, acc); accumulate_tap<19>(t, acc);
+    accumulate_tap<6>(t, acc);  accumulate_tap<7>(t, acc);
+    if constexpr (nt > 8) {
+        accumulate_tap<8>(t, acc);  accumulate_tap<9>(t, acc);  accumulate_tap<10>(t, acc);
+        accumulate_tap<11>(t, acc); accumulate_tap<12>(t, acc); accumulate_tap<13>(t, acc);
+        accumulate_tap<14>(t, acc); accumulate_tap<15>(t, acc); accumulate_tap<16>(t, acc);
+        accumulate_tap<17>(t, acc); accumulate_tap<18>(t, acc); accumulate_tap<19>(t, acc);
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -331,7 +344,7 @@ __device__ __forceinline__ void lp_tap(const Taps &t, float2 &k01, LpAcc<kPrec> 
 
 // Weighted byte sums in the layout of byte_sums_u8: k[0] = channels (0, 1) in FP32, k[1..3] =
 // channels (2, 3), (4, 5), (6, 7) from their 16-bit corrections.
-template <int kPrec>
+template <int kPrec, int nt = 20>
 __device__ __forceinline__ void byte_sums_lp(const Taps &t, float2 k[4])
 {
     LpAcc<kPrec> a;
@@ -343,11 +356,13 @@ __device__ __forceinline__ void byte_sums_lp(const Taps &t, float2 k[4])
     k[0] = make_float2(0.0f, 0.0f);
     lp_tap<kPrec, 0>(t, k[0], a);  lp_tap<kPrec, 1>(t, k[0], a);  lp_tap<kPrec, 2>(t, k[0], a);
     lp_tap<kPrec, 3>(t, k[0], a);  lp_tap<kPrec, 4>(t, k[0], a);  lp_tap<kPrec, 5>(t, k[0], a);
-    lp_tap<kPrec, 6>(t, k[0], a);  lp_tap<kPrec, 7>(t, k[0], a);  lp_tap<kPrec, 8>(t, k[0], a);
-    lp_tap<kPrec, 9>(t, k[0], a);  lp_tap<kPrec, 10>(t, k[0], a); lp_tap<kPrec, 11>(t, k[0], a);
-    lp_tap<kPrec, 12>(t, k[0], a); lp_tap<kPrec, 13>(t, k[0], a); lp_tap<kPrec, 14>(t, k[0], a);
-    lp_tap<kPrec, 15>(t, k[0], a); lp_tap<kPrec, 16>(t, k[0], a); lp_tap<kPrec, 17>(t, k[0], a);
-    lp_tap<kPrec, 18>(t, k[0], a); lp_tap<kPrec, 19>(t, k[0], a);
+    lp_tap<kPrec, 6>(t, k[0], a);  lp_tap<kPrec, 7>(t, k[0], a);
+    if constexpr (nt > 8) {
+        lp_tap<kPrec, 8>(t, k[0], a);  lp_tap<kPrec, 9>(t, k[0], a);  lp_tap<kPrec, 10>(t, k[0], a);
+        lp_tap<kPrec, 11>(t, k[0], a); lp_tap<kPrec, 12>(t, k[0], a); lp_tap<kPrec, 13>(t, k[0], a);
+        lp_tap<kPrec, 14>(t, k[0], a); lp_tap<kPrec, 15>(t, k[0], a); lp_tap<kPrec, 16>(t, k[0], a);
+        lp_tap<kPrec, 17>(t, k[0], a); lp_tap<kPrec, 18>(t, k[0], a); lp_tap<kPrec, 19>(t, k[0], a);
+    }
 #pragma unroll
     for (int p = 0; p < 3; ++p) {
         if constexpr (kPrec == 1) k[1 + p] = __fadd2_rn(__half22float2(a.fsum[p]), __half22float2(a.corr[p]));

@@ -51,8 +51,11 @@ merf_status check_desc(const merf_scene_desc *d, int storage)
                     d->mlp_hidden, d->mlp_out);
     if (d->grid_res < 2 || d->grid_res > 4096 || (d->grid_res & 1))
         return fail(MERF_ERR_INVALID_ARG, "grid_res %d must be even in [2, 4096]", d->grid_res);
-    if (d->plane_res < 2 || d->plane_res > 16384 || (d->plane_res & 1))
-        return fail(MERF_ERR_INVALID_ARG, "plane_res %d must be even in [2, 16384]", d->plane_res);
+    // plane_res 0: a grid-only scene (uint8 storage only), the SNeRG++-style baseline of Sec. 6
+    const bool grid_only = storage == MERF_STORAGE_U8_SPARSE && d->plane_res == 0;
+    if (!grid_only && (d->plane_res < 2 || d->plane_res > 16384 || (d->plane_res & 1)))
+        return fail(MERF_ERR_INVALID_ARG, "plane_res %d must be even in [2, 16384] (or 0 for a grid-only uint8 scene)",
+                    d->plane_res);
     if (storage == MERF_STORAGE_U8_SPARSE) {
         if (!pow2(d->block_size) || d->block_size > d->grid_res || d->grid_res % d->block_size)
             return fail(MERF_ERR_INVALID_ARG, "block_size %d must be a power of two dividing grid_res %d",
@@ -204,6 +207,17 @@ merf::RenderParams make_params(const merf_scene *s, const merf_render_opts *o, i
     return P;
 }
 
+template <int kPrec>
+void launch_u8(int geo, dim3 grid, dim3 block, cudaStream_t st, const merf::RenderParams &P)
+{
+    if (geo == merf::kGeoPaper)
+        merf::render_kernel<0, kPrec, merf::kGeoPaper><<<grid, block, 0, st>>>(P);
+    else if (geo == merf::kGeoGridOnly)
+        merf::render_kernel<0, kPrec, merf::kGeoGridOnly><<<grid, block, 0, st>>>(P);
+    else
+        merf::render_kernel<0, kPrec, merf::kGeoRuntime><<<grid, block, 0, st>>>(P);
+}
+
 merf_status launch_render(const merf_scene *s, const merf_camera *cams, int n, int W, int H, float *out,
                           float *aux, unsigned long long *counters, const merf_render_opts *o,
                           cudaStream_t st)
@@ -220,18 +234,15 @@ merf_status launch_render(const merf_scene *s, const merf_camera *cams, int n, i
         P.cam0 = c0;
         for (int c = 0; c < nc; ++c) memcpy(P.cams.m[c], &cams[c0 + c], sizeof(merf_camera));
         const dim3 grid((W + merf::kTileW - 1) / merf::kTileW, (H + merf::kTileH - 1) / merf::kTileH, nc);
-        const bool paper = merf::paper_geometry(s->desc);
+        const int geo = merf::gather_geometry(s->desc);
         if (s->desc.storage == MERF_STORAGE_F32_DENSE)
             merf::render_kernel<1, 0, merf::kGeoRuntime><<<grid, block, 0, st>>>(P);
         else if (o->precision == MERF_PREC_FP16)
-            paper ? merf::render_kernel<0, 1, merf::kGeoPaper><<<grid, block, 0, st>>>(P)
-                  : merf::render_kernel<0, 1, merf::kGeoRuntime><<<grid, block, 0, st>>>(P);
+            launch_u8<1>(geo, grid, block, st, P);
         else if (o->precision == MERF_PREC_BF16)
-            paper ? merf::render_kernel<0, 2, merf::kGeoPaper><<<grid, block, 0, st>>>(P)
-                  : merf::render_kernel<0, 2, merf::kGeoRuntime><<<grid, block, 0, st>>>(P);
+            launch_u8<2>(geo, grid, block, st, P);
         else
-            paper ? merf::render_kernel<0, 0, merf::kGeoPaper><<<grid, block, 0, st>>>(P)
-                  : merf::render_kernel<0, 0, merf::kGeoRuntime><<<grid, block, 0, st>>>(P);
+            launch_u8<0>(geo, grid, block, st, P);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return fail(MERF_ERR_CUDA, "render launch: %s", cudaGetErrorString(e));
     }
@@ -264,7 +275,7 @@ merf_status merf_scene_upload(const merf_scene_desc *desc, const int32_t *index_
     if (st) return st;
     if (!out) return fail(MERF_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
-    if (!index_grid || !planes || !mlp_weights || (desc->n_blocks > 0 && !atlas))
+    if (!index_grid || (desc->plane_res > 0 && !planes) || !mlp_weights || (desc->n_blocks > 0 && !atlas))
         return fail(MERF_ERR_INVALID_ARG, "a scene array is NULL");
     const size_t nb = (size_t)desc->grid_res / desc->block_size;
     for (size_t i = 0; i < nb * nb * nb; ++i)
@@ -315,14 +326,15 @@ merf_status merf_scene_upload(const merf_scene_desc *desc, const int32_t *index_
             }
     // Each plane gets a one-texel border that repeats its edge texels, so that bilinear taps of
     // clamp-to-edge interpolation never need their coordinates clamped: [3][R+2][R+2].
+    // (a grid-only scene, R = 0, has no planes at all)
     const size_t Rp = R + 2;
     std::vector<uint8_t> padded;
     try {
-        padded.resize(3 * Rp * Rp * 8);
+        padded.resize(R > 0 ? 3 * Rp * Rp * 8 : 0);
     } catch (...) {
         return fail(MERF_ERR_OOM, "host memory for the bordered planes");
     }
-    for (size_t q = 0; q < 3; ++q)
+    for (size_t q = 0; q < (R > 0 ? 3 : 0); ++q)
         for (size_t v = 0; v < Rp; ++v)
             for (size_t u = 0; u < Rp; ++u) {
                 const size_t sv = v == 0 ? 0 : v > R ? R - 1 : v - 1, su = u == 0 ? 0 : u > R ? R - 1 : u - 1;

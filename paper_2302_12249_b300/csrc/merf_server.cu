@@ -399,8 +399,9 @@ merf_status merf_server_create(const merf_scene *const *scenes, int n_scenes, co
         return merf::set_error(MERF_ERR_INVALID_ARG, "pool_bytes %zu too small", opts->pool_bytes);
     for (int k = 0; k < n_scenes; ++k) {
         if (!scenes[k]) return merf::set_error(MERF_ERR_INVALID_ARG, "scene %d is NULL", k);
-        if (scenes[k]->desc.storage != MERF_STORAGE_U8_SPARSE)
-            return merf::set_error(MERF_ERR_UNSUPPORTED, "scene %d: the server renders uint8 block-sparse scenes", k);
+        if (scenes[k]->desc.storage != MERF_STORAGE_U8_SPARSE || scenes[k]->desc.plane_res == 0)
+            return merf::set_error(MERF_ERR_UNSUPPORTED,
+                                   "scene %d: the server renders uint8 block-sparse scenes with planes", k);
     }
     merf_server *s = new merf_server();
     s->opts = *opts;

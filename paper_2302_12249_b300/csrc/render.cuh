@@ -77,11 +77,12 @@ __device__ __forceinline__ AppArg app_arg(const float app[7])
     return a;
 }
 
-// From the weighted byte sums of the uint8 path: x = (14 / 255) k - 7 (W_V + 3), so
-// y = k (-14 log2(e) / 255) + 7 log2(e) (W_V + 3), one fused multiply-add per channel.
-__device__ __forceinline__ AppArg app_arg_u8(const float2 k[4], float wv)
+// From the weighted byte sums of the uint8 path: x = (14 / 255) k - 7 W (W the sources' total
+// weight, as in dequant_density), so y = k (-14 log2(e) / 255) + 7 log2(e) W, one fused
+// multiply-add per channel.
+__device__ __forceinline__ AppArg app_arg_u8(const float2 k[4], float wsum)
 {
-    const float A = -kLog2e * 14.0f / 255.0f, b = (7.0f * kLog2e) * (wv + 3.0f);
+    const float A = -kLog2e * 14.0f / 255.0f, b = (7.0f * kLog2e) * wsum;
     const float2 A2 = make_float2(A, A), b2 = make_float2(b, b);
     AppArg a;
     a.y1 = fmaf(k[0].y, A, b);
@@ -415,16 +416,18 @@ __device__ __forceinline__ void march_ray(const FieldView &fv, const OccView &oc
         if constexpr (kStorage == 0 && kPrec == 0) {
             gather_u8<kGeo>(fv, p0, p1, p2, tp);
             float2 k[4];
-            byte_sums_u8(tp, k);
-            dens = dequant_density(k[0].x, tp.wv);
-            ya = app_arg_u8(k, tp.wv);
+            byte_sums_u8<kTaps<kGeo>>(tp, k);
+            const float wsum = tp.wv + (float)kPlaneSources<kGeo>;
+            dens = dequant_density(k[0].x, wsum);
+            ya = app_arg_u8(k, wsum);
         } else if constexpr (kStorage == 0) {
             // FP16 / BF16 appearance arithmetic; density in FP32 exactly as above
             gather_u8<kGeo>(fv, p0, p1, p2, tp);
             float2 k[4];
-            byte_sums_lp<kPrec>(tp, k);
-            dens = dequant_density(k[0].x, tp.wv);
-            ya = app_arg_u8(k, tp.wv);
+            byte_sums_lp<kPrec, kTaps<kGeo>>(tp, k);
+            const float wsum = tp.wv + (float)kPlaneSources<kGeo>;
+            dens = dequant_density(k[0].x, wsum);
+            ya = app_arg_u8(k, wsum);
         } else {
             float all[8];
             field_f32(fv, p0, p1, p2, all);

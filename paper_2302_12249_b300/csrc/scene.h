@@ -57,6 +57,15 @@ inline bool paper_geometry(const merf_scene_desc &d)
     return d.storage == MERF_STORAGE_U8_SPARSE && d.grid_res == 512 && d.block_size == 16 && d.plane_res == 2048;
 }
 
+// The gather variant of a uint8 scene: the paper's geometry, a grid-only scene (no planes), or
+// run-time strides.
+inline int gather_geometry(const merf_scene_desc &d)
+{
+    if (paper_geometry(d)) return kGeoPaper;
+    if (d.storage == MERF_STORAGE_U8_SPARSE && d.plane_res == 0) return kGeoGridOnly;
+    return kGeoRuntime;
+}
+
 // Thread-local error message of the C ABI (defined in merf_api.cu).
 merf_status set_error(merf_status s, const char *fmt, ...);
 merf_status clear_error();

@@ -157,8 +157,10 @@ class Scene:
             d.block_size, d.n_blocks = cfg.B, scene.n_blocks
             ig = np.ascontiguousarray(scene.index_grid, dtype=np.int32)
             atlas = np.ascontiguousarray(scene.atlas, dtype=np.uint8)
-            planes = np.ascontiguousarray(scene.planes, dtype=np.uint8)
-            _check(lib().merf_scene_upload(ct.byref(d), _np_ptr(ig), _np_ptr(atlas), _np_ptr(planes),
+            # a grid-only scene (R = 0) passes no planes
+            planes = None if scene.planes is None else np.ascontiguousarray(scene.planes, dtype=np.uint8)
+            _check(lib().merf_scene_upload(ct.byref(d), _np_ptr(ig), _np_ptr(atlas),
+                                           None if planes is None else _np_ptr(planes),
                                            ct.cast(occ_ptrs, ct.c_void_p), _np_ptr(mlp), s, ct.byref(handle)))
         else:
             d.storage = STORAGE_F32_DENSE

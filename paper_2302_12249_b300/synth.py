@@ -70,6 +70,10 @@ class SceneConfig:
     peak_opacity: float          # A * step: opacity scale of one step at a blob centre
     storage: str = "u8"          # "u8" (block-sparse bytes) or "f32" (dense float)
     radius_range: Tuple[float, float] = (0.05, 0.3)
+    # grid only (R = 0): the SNeRG++-style baseline of the paper's Sec. 6 -- the same fields
+    # (same seeded draws, planes included) sampled at the voxel centres of a finer 3D grid,
+    # with no planes stored
+    grid_only: bool = False
 
 
 CONFIGS: Dict[str, SceneConfig] = {
@@ -82,7 +86,22 @@ CONFIGS: Dict[str, SceneConfig] = {
     # Paper-scale: L = 512 in 16^3 blocks, R = 2048, occupancy at 1/16 .. 1/128 of R.
     "paper": SceneConfig("paper", L=512, B=16, R=2048, occ_res=(128, 64, 32, 16), n_blobs=256,
                          inner_blobs=128, step=1.0 / 256, peak_opacity=3.0),
+    # Grid-only (SNeRG++-style) versions of the same contents: "tiny" at 64^3 and 128^3, and
+    # the paper-scale scene at L = 512 / 1024 / 2048 with 16^3 blocks and no planes.
+    "tiny_grid": SceneConfig("tiny_grid", L=64, B=8, R=0, occ_res=(64,), n_blobs=32, inner_blobs=None,
+                             step=1.0 / 64, peak_opacity=3.0, grid_only=True),
+    "tiny_grid128": SceneConfig("tiny_grid128", L=128, B=8, R=0, occ_res=(64,), n_blobs=32, inner_blobs=None,
+                                step=1.0 / 64, peak_opacity=3.0, grid_only=True),
+    "snerg512": SceneConfig("snerg512", L=512, B=16, R=0, occ_res=(128, 64, 32, 16), n_blobs=256,
+                            inner_blobs=128, step=1.0 / 256, peak_opacity=3.0, grid_only=True),
+    "snerg1024": SceneConfig("snerg1024", L=1024, B=16, R=0, occ_res=(128, 64, 32, 16), n_blobs=256,
+                             inner_blobs=128, step=1.0 / 256, peak_opacity=3.0, grid_only=True),
+    "snerg2048": SceneConfig("snerg2048", L=2048, B=16, R=0, occ_res=(128, 64, 32, 16), n_blobs=256,
+                             inner_blobs=128, step=1.0 / 256, peak_opacity=3.0, grid_only=True),
 }
+
+# the MERF configuration whose seeded draws a grid-only configuration shares
+GRID_ONLY_BASE = {"tiny_grid": 256, "tiny_grid128": 256, "snerg512": 2048, "snerg1024": 2048, "snerg2048": 2048}
 
 
 @dataclasses.dataclass
@@ -185,6 +204,8 @@ def make_scene(name_or_cfg, seed: Optional[int] = None, mlp_seed: int = SEED_MLP
     plane_dens = [_waves(rng, 4, 2, (0.1, 0.5), 0.1) for _ in range(3)]
 
     L, R = cfg.L, cfg.R
+    if cfg.grid_only:
+        R = GRID_ONLY_BASE.get(cfg.name, 2048)     # only for evaluating the plane fields
     two_s2 = 2.0 * (radii / 3.0) ** 2
 
     def gauss(ax: torch.Tensor, d: int) -> torch.Tensor:          # [n_blobs, len(ax)]
@@ -218,18 +239,21 @@ def make_scene(name_or_cfg, seed: Optional[int] = None, mlp_seed: int = SEED_MLP
     # plane index -> (row axis, column axis) in world axes: P_x(y,z)[z][y], P_y(x,z)[z][x], P_z(x,y)[y][x]
     plane_axes = [(2, 1), (2, 0), (1, 0)]
 
-    def plane_field(waves_list, m) -> torch.Tensor:
+    def plane_field(waves_list, m, ax=None) -> torch.Tensor:
+        ax = pax if ax is None else ax
         out = []
         for (k, phi, a) in waves_list:
-            coef, (fc, fr) = _wave_factors(k, phi, a, [pax, pax])   # k[:,0] -> column, k[:,1] -> row
+            coef, (fc, fr) = _wave_factors(k, phi, a, [ax, ax])   # k[:,0] -> column, k[:,1] -> row
             out.append(torch.einsum("t,tv,tu->vu", coef, fr, fc).imag)
         return out
 
-    if cfg.storage == "u8":
+    if cfg.grid_only:
+        planes = None
+    elif cfg.storage == "u8":
         planes = torch.empty((3, R, R, C), dtype=torch.uint8)
     else:
         planes = torch.empty((3, R, R, C), dtype=torch.float32)
-    for pi in range(3):
+    for pi in range(3 if planes is not None else 0):
         dens = plane_field([plane_dens[pi]], M_DENSITY)[0]
         app = plane_field(plane_waves[pi], M_APPEAR)
         if cfg.storage == "u8":
@@ -245,6 +269,14 @@ def make_scene(name_or_cfg, seed: Optional[int] = None, mlp_seed: int = SEED_MLP
     gax = _centres(L, -2.0, 2.0)
     gx, gy, gz = gauss(gax, 0), gauss(gax, 1), gauss(gax, 2)
     vol_facs = [_wave_factors(k, phi, a, [gax, gax, gax]) for (k, phi, a) in vol_waves]
+    # grid only: the plane fields evaluated at the grid's voxel centres, [3][C][L][L] (row, column)
+    ptab = None
+    if cfg.grid_only:
+        ptab = torch.empty((3, C, L, L), dtype=torch.float64)
+        for pi in range(3):
+            ptab[pi, 0] = plane_field([plane_dens[pi]], M_DENSITY, gax)[0]
+            for ch, v in enumerate(plane_field(plane_waves[pi], M_APPEAR, gax)):
+                ptab[pi, 1 + ch] = v
 
     def grid_values(z0: torch.Tensor, y0: torch.Tensor, x0: torch.Tensor, n: int) -> torch.Tensor:
         """Pre-quantisation values of boxes of n^3 voxels starting at (z0, y0, x0): [nb, n, n, n, C]."""
@@ -259,11 +291,17 @@ def make_scene(name_or_cfg, seed: Optional[int] = None, mlp_seed: int = SEED_MLP
             v = torch.einsum("t,bzt,byt,bxt->bzyx", coef, fz[:, iz].permute(1, 2, 0),
                              fy[:, iy].permute(1, 2, 0), fx[:, ix].permute(1, 2, 0)).imag
             out[..., 1 + ch] = v
+        if ptab is not None:
+            # + P_x(y, z)[z][y] + P_y(x, z)[z][x] + P_z(x, y)[y][x] at every voxel centre
+            for c in range(C):
+                out[..., c] += (ptab[0, c][iz[:, :, None], iy[:, None, :]][:, :, :, None]
+                                + ptab[1, c][iz[:, :, None], ix[:, None, :]][:, :, None, :]
+                                + ptab[2, c][iy[:, :, None], ix[:, None, :]][:, None, :, :])
         return out
 
     scene = Scene(cfg=cfg, seed=seed, occ=occ, mlp=_mlp_weights(mlp_seed))
     if cfg.storage == "u8":
-        scene.planes = planes.numpy()
+        scene.planes = None if planes is None else planes.numpy()
         B = cfg.B
         nbx = L // B
         assert nbx * B == L

@@ -64,6 +64,27 @@ def test_upload_rejects_bad_desc(field, value):
     assert st == merf.ERR_INVALID_ARG and msg
 
 
+def test_grid_only_desc_passes_validation_and_dense_needs_planes():
+    """plane_res 0 is a grid-only uint8 scene: it passes validation (the device budget then
+    refuses it before anything is allocated); dense float storage still needs planes."""
+    L = merf.lib()
+    L.merf_set_device_budget(1)
+    try:
+        st, msg = _upload(_desc(plane_res=0))
+        assert st == merf.ERR_OOM and "budget" in msg
+    finally:
+        L.merf_set_device_budget(0)
+    d = _desc(plane_res=0, storage=1)
+    h = ct.c_void_p()
+    occ = [np.ones((16,) * 3, np.uint8)]
+    ptrs = (ct.c_void_p * 8)(*[o.ctypes.data for o in occ])
+    grid = np.zeros(16 ** 3 * 8, np.float32)
+    mlp = np.zeros(883, np.float32)
+    st = L.merf_scene_upload_dense(ct.byref(d), grid.ctypes.data, None, ct.cast(ptrs, ct.c_void_p),
+                                   mlp.ctypes.data, None, ct.byref(h))
+    assert st == merf.ERR_INVALID_ARG
+
+
 def test_upload_rejects_unsupported_mlp():
     st, _ = _upload(_desc(mlp_hidden=32))
     assert st == merf.ERR_UNSUPPORTED

@@ -1,5 +1,7 @@
 """Pins of the oracle's feature field t~ = V + P_x + P_y + P_z (Sec. 3.1, Eq. 3) and of the
 dequantisation (Sec. 4.2) -- CPU only."""
+import dataclasses
+
 import numpy as np
 
 import oracle
@@ -121,3 +123,32 @@ def test_block_sparse_equals_dense_and_missing_is_zero():
         misses += miss
         np.testing.assert_allclose(ta, tb, atol=2e-5)       # dense copy is float32
     assert misses > 0
+
+
+def test_grid_only_scene_is_the_grid_alone():
+    """R = 0 (the grid-only baseline of Sec. 6): t~ is the trilinear grid alone.  On an affine
+    grid the value is the dequantised affine byte with no plane terms, and a scene with planes
+    differs from its grid-only copy by exactly the bilinear plane terms, computed here apart."""
+    L = 16
+    sc = _affine_scene(L=L)
+    g = dataclasses.replace(sc, cfg=dataclasses.replace(sc.cfg, R=0, grid_only=True), planes=None)
+    osc, ogc = oracle.OracleScene(sc), oracle.OracleScene(g)
+    rng = np.random.default_rng(7)
+    R = sc.cfg.R
+    m = np.array([14.0] + [7.0] * 7)
+    planes = 2 * m * sc.planes.astype(np.float64) / 255 - m
+    for p in rng.uniform(-2 + 8 / L, 2 - 8 / L, size=(200, 3)):
+        t, _ = osc.field(p)
+        tg, _ = ogc.field(p)
+        u = (p + 2) * L / 4 - 0.5
+        np.testing.assert_allclose(tg[1], scenes.dequant(10 + 3 * u[0] + 5 * u[1] + 7 * u[2], 7.0), atol=1e-10)
+        # plane q: columns along axis (1, 0, 0)[q], rows along axis (2, 2, 1)[q]
+        want = np.zeros(8)
+        for q, (ca, ra) in enumerate([(1, 2), (0, 2), (0, 1)]):
+            uc, ur = (p[ca] + 2) * R / 4 - 0.5, (p[ra] + 2) * R / 4 - 0.5
+            c0, r0 = int(np.floor(uc)), int(np.floor(ur))
+            fc, fr = uc - c0, ur - r0
+            cl = lambda i: min(max(i, 0), R - 1)
+            want += ((1 - fc) * (1 - fr) * planes[q, cl(r0), cl(c0)] + fc * (1 - fr) * planes[q, cl(r0), cl(c0 + 1)]
+                     + (1 - fc) * fr * planes[q, cl(r0 + 1), cl(c0)] + fc * fr * planes[q, cl(r0 + 1), cl(c0 + 1)])
+        np.testing.assert_allclose(t - tg, want, atol=1e-9)
