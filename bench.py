@@ -244,6 +244,50 @@ def _differentiation(steps: int = 5):
             "backward_mrays_per_s": rays / (bwd / steps / 1e3) / 1e6}
 
 
+def _grid_only_variant(merf_ref, names=("snerg512", "snerg1024"), steps=5, warmup=3):
+    """The SNeRG++-style baseline the paper compares MERF with (Sec. 6): the same contents baked
+    as a grid-only scene (no planes) at L = 512 and 1024, rendered by the same kernel from the
+    same 8 cameras at 1920x1080 in FP32.  Per configuration: device memory, time, Mrays/s and the
+    algorithmic gather bytes (per evaluated sample 8 density bytes + the 4-byte index entry, per
+    sample with non-zero opacity 56 appearance bytes, per ray 12 output bytes)."""
+    import torch
+    from paper_2302_12249_b300 import merf, synth
+    cams = synth.config_cameras("paper")
+    n = cams.shape[0]
+    res = {"merf": merf_ref}
+    for name in names:
+        sc = synth.make_scene(name)
+        gs = merf.Scene(sc)
+        out = torch.empty((n, H_IMG, W_IMG, 3), dtype=torch.float32, device="cuda")
+        cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+        aux = torch.empty((n, H_IMG, W_IMG, merf.AUX_SIZE), dtype=torch.float32, device="cuda")
+        merf.render(gs, cams, W_IMG, H_IMG, STEP, out=out, aux=aux, counters=cnt)
+        torch.cuda.synchronize()
+        del aux
+        c = [int(v) for v in cnt.cpu().tolist()]
+        for _ in range(warmup):
+            merf.render(gs, cams, W_IMG, H_IMG, STEP, out=out)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            merf.render(gs, cams, W_IMG, H_IMG, STEP, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        alg = c[merf.CNT_EVAL] * (8 + B_INDEX) + c[merf.CNT_APPEAR] * 56 + c[merf.CNT_RAYS] * B_OUT
+        res[name] = {"L": sc.cfg.L, "device_mb": round(gs.device_bytes / 1e6, 1), "ms_per_step": ms,
+                     "mrays_per_s": n * W_IMG * H_IMG / (ms / 1e3) / 1e6,
+                     "evaluated_per_ray": c[merf.CNT_EVAL] / c[merf.CNT_RAYS],
+                     "gather_bytes_per_sample": 8 + B_INDEX + 56,
+                     "algorithmic_gb_per_s": alg / (ms / 1e3) / 1e9}
+        gs.close()
+        del sc, out
+    res["workload"] = ("same contents as grid-only scenes (3D grid alone, 16^3 blocks, no planes), the 8 ring "
+                       "cameras at 1920x1080, FP32; `merf` is this run's main line")
+    return res
+
+
 SERVE_RES = [(256, 256), (640, 360), (1280, 720), (1920, 1080)]
 
 
@@ -450,6 +494,13 @@ def run_ours(args):
     serving = None
     if rank == 0 and world == 1 and args.serve_requests > 0:
         serving = _serving(gs, args.serve_requests)
+    variants = None
+    if rank == 0 and world == 1 and not args.no_variants:
+        merf_ref = {"L": 512, "R": 2048, "device_mb": round(gs.device_bytes / 1e6, 1), "ms_per_step": ms_per_step,
+                    "mrays_per_s": value, "evaluated_per_ray": c[merf.CNT_EVAL] / c[merf.CNT_RAYS],
+                    "gather_bytes_per_sample": B_DENSITY + B_INDEX + B_APPEAR,
+                    "algorithmic_gb_per_s": achieved}
+        variants = _grid_only_variant(merf_ref)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -486,6 +537,8 @@ def run_ours(args):
             line["differentiation"] = differentiation
         if serving is not None:
             line["serving"] = serving
+        if variants is not None:
+            line["grid_only_variant"] = variants
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -503,6 +556,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-output measurement (profiling)")
     ap.add_argument("--no-precision", action="store_true", help="skip the FP16/BF16 comparison (profiling)")
     ap.add_argument("--serve-requests", type=int, default=10000, help="requests of the serving run (0 = skip)")
+    ap.add_argument("--no-variants", action="store_true", help="skip the grid-only comparison (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
