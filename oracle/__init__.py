@@ -53,7 +53,7 @@ class _Scene(ct.Structure):
 
 class _Opts(ct.Structure):
     _fields_ = [("step", ct.c_double), ("t_term", ct.c_double), ("early_term", ct.c_int),
-                ("decide_f32", ct.c_int), ("no_mlp", ct.c_int)]
+                ("decide_f32", ct.c_int), ("no_mlp", ct.c_int), ("contraction", ct.c_int)]
 
 
 class _Seg(ct.Structure):
@@ -92,8 +92,16 @@ def lib():
         L.orc_render.restype = ct.c_int
         L.orc_trace.argtypes = [ct.POINTER(_Scene), ct.c_void_p, ct.c_int, ct.c_int, ct.c_int,
                                 ct.c_void_p, ct.c_int, ct.c_double, ct.c_int, ct.c_double,
-                                ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int]
+                                ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_int]
         L.orc_trace.restype = ct.c_int
+        L.orc_contract_sph.argtypes = [D3, D3]
+        L.orc_sph_t_of_s.argtypes = [ct.c_double]
+        L.orc_sph_t_of_s.restype = ct.c_double
+        L.orc_sph_count.argtypes = [ct.c_double]
+        L.orc_sph_count.restype = ct.c_int
+        L.orc32_sph_count.argtypes = [ct.c_float]
+        L.orc32_sph_count.restype = ct.c_int
+        L.orc32_sph_point.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_float, ct.c_int, ct.c_void_p]
         L.orc_render_grad.argtypes = [ct.POINTER(_Scene), ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.c_void_p,
                                       ct.c_int, ct.POINTER(_Opts), ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]
         L.orc_render_grad.restype = ct.c_int
@@ -133,6 +141,30 @@ def contract(x) -> np.ndarray:
     p = (ct.c_double * 3)()
     lib().orc_contract(_d3(x), p)
     return np.array(p[:])
+
+
+def contract_sph(x) -> np.ndarray:
+    """The spherical contraction of mip-NeRF 360 (the ablation of Sec. 3.2 / Table 2 (c))."""
+    p = (ct.c_double * 3)()
+    lib().orc_contract_sph(_d3(x), p)
+    return np.array(p[:])
+
+
+def sph_t_of_s(s: float) -> float:
+    return lib().orc_sph_t_of_s(float(s))
+
+
+def sph_count(step: float, f32: bool = False) -> int:
+    return lib().orc32_sph_count(float(step)) if f32 else lib().orc_sph_count(float(step))
+
+
+def sph_point32(o, d, step: float, k: int) -> np.ndarray:
+    """FP32 position of dense-march sample k (the kernel's rounding sequence)."""
+    o32 = np.ascontiguousarray(o, dtype=np.float32)
+    d32 = np.ascontiguousarray(d, dtype=np.float32)
+    p = np.zeros(3, np.float32)
+    lib().orc32_sph_point(_ptr(o32), _ptr(d32), float(step), int(k), _ptr(p))
+    return p
 
 
 def contract_in_region(r: int, x) -> np.ndarray:
@@ -264,8 +296,10 @@ class OracleScene:
 
 def render(oscene: OracleScene, cams: np.ndarray, W: int, H: int, step: float,
            pix: Optional[np.ndarray] = None, t_term: float = 2e-4, early_term: bool = True,
-           decide_f32: bool = True, no_mlp: bool = False, threads: Optional[int] = None) -> np.ndarray:
-    """Render every pixel (or the (cam, col, row) triples in `pix`); returns [n, ORC_OUT] doubles."""
+           decide_f32: bool = True, no_mlp: bool = False, threads: Optional[int] = None,
+           contraction: int = 0) -> np.ndarray:
+    """Render every pixel (or the (cam, col, row) triples in `pix`); returns [n, ORC_OUT] doubles.
+    contraction 1: the spherical-contraction ablation, marched densely."""
     cams = np.ascontiguousarray(cams, dtype=np.float32).reshape(-1, 16)
     if pix is not None:
         pix = np.ascontiguousarray(pix, dtype=np.int32).reshape(-1, 3)
@@ -274,7 +308,7 @@ def render(oscene: OracleScene, cams: np.ndarray, W: int, H: int, step: float,
         n = cams.shape[0] * W * H
     out = np.zeros((n, ORC_OUT), dtype=np.float64)
     op = _Opts(step=step, t_term=t_term, early_term=int(early_term), decide_f32=int(decide_f32),
-               no_mlp=int(no_mlp))
+               no_mlp=int(no_mlp), contraction=int(contraction))
     lib().orc_render(ct.byref(oscene.s), _ptr(cams), cams.shape[0], W, H, _ptr(pix),
                      0 if pix is None else n, ct.byref(op), _ptr(out), threads or default_threads())
     return out
@@ -282,7 +316,7 @@ def render(oscene: OracleScene, cams: np.ndarray, W: int, H: int, step: float,
 
 def trace(oscene: OracleScene, cams: np.ndarray, W: int, H: int, step: float, words: int,
           pix: Optional[np.ndarray] = None, decide_f32: bool = True, eps: float = 2e-6,
-          threads: Optional[int] = None):
+          threads: Optional[int] = None, contraction: int = 0):
     """Evaluated lattice-sample sets (termination off) as bit masks [n, words] + FP64 face flags."""
     cams = np.ascontiguousarray(cams, dtype=np.float32).reshape(-1, 16)
     if pix is not None:
@@ -295,7 +329,7 @@ def trace(oscene: OracleScene, cams: np.ndarray, W: int, H: int, step: float, wo
     nlat = np.zeros(n, dtype=np.int32)
     lib().orc_trace(ct.byref(oscene.s), _ptr(cams), cams.shape[0], W, H, _ptr(pix),
                     0 if pix is None else n, float(step), int(decide_f32), float(eps),
-                    _ptr(mask), _ptr(flags), words, _ptr(nlat), threads or default_threads())
+                    _ptr(mask), _ptr(flags), words, _ptr(nlat), threads or default_threads(), int(contraction))
     return mask, flags, nlat
 
 

@@ -491,6 +491,68 @@ int orc32_sample_cell(const orc32_segs *sg, float step, int k, int N, int cell[3
 }
 
 /* ------------------------------------------------------------------------------------ */
+/* ablation: the spherical contraction (Eq. contract360) and its dense march               */
+
+void orc_contract_sph(const double x[3], double p[3])
+{
+    double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+    if (r <= 1.0) {
+        for (int a = 0; a < 3; ++a) p[a] = x[a];
+        return;
+    }
+    for (int a = 0; a < 3; ++a) p[a] = (2.0 - 1.0 / r) * x[a] / r;
+}
+
+/* Reading: the paper names no sampling for this contraction beyond "no AABB skipping"; samples
+ * are spaced uniformly in s, with mip-NeRF 360's inverse spacing t(s) = s (s <= 1), 1/(2 - s)
+ * (s > 1), so that s = 2 is the point at infinity. */
+double orc_sph_t_of_s(double s) { return s <= 1.0 ? s : 1.0 / (2.0 - s); }
+
+int orc_sph_count(double step)
+{
+    int k = 0;
+    while (((double)k + 1.0) * step < 2.0) ++k;
+    return k;
+}
+
+int orc32_sph_count(float step)
+{
+    int k = 0;
+    while (((float)k + 1.0f) * step < 2.0f) ++k;
+    return k;
+}
+
+/* FP32 replica of the kernel's sample position, each operation rounded once, in this order */
+void orc32_sph_point(const float o[3], const float d[3], float step, int k, float p[3])
+{
+    float s = ((float)k + 0.5f) * step;
+    float t = s <= 1.0f ? s : 1.0f / (2.0f - s);
+    float x[3];
+    for (int a = 0; a < 3; ++a) {
+        float td = t * d[a];
+        x[a] = o[a] + td;
+    }
+    float x0 = x[0] * x[0], x1 = x[1] * x[1], x2 = x[2] * x[2];
+    float r = sqrtf((x0 + x1) + x2);
+    if (r <= 1.0f) {
+        for (int a = 0; a < 3; ++a) p[a] = x[a];
+        return;
+    }
+    float w = (2.0f - 1.0f / r) / r;
+    for (int a = 0; a < 3; ++a) p[a] = x[a] * w;
+}
+
+static void cell32(const float p[3], int N, int cell[3])
+{
+    float sc = (float)N * 0.25f;
+    for (int a = 0; a < 3; ++a) {
+        float q = p[a] * sc;
+        int c = (int)floorf(q) + N / 2;
+        cell[a] = c < 0 ? 0 : (c > N - 1 ? N - 1 : c);
+    }
+}
+
+/* ------------------------------------------------------------------------------------ */
 /* one ray                                                                               */
 
 static int occ_at(const orc_scene *sc, const int cell[3])
@@ -515,9 +577,65 @@ static void cell64(const double p[3], int N, int cell[3], double *face_dist)
 
 static double sigmoid(double x) { return 1.0 / (1.0 + exp(-x)); }
 
+/* The same quadrature with the spherical contraction, every sample visited (no skipping). */
+static void render_ray_sph(const orc_scene *sc, const orc_opts *op, const float *cam, int i, int j,
+                           double *rec)
+{
+    double o[3], d[3];
+    orc_ray(cam, i, j, o, d);
+    float o32[3], d32[3];
+    orc32_ray(cam, i, j, o32, d32);
+    double step = op->step;
+    int nlat = op->decide_f32 ? orc32_sph_count((float)step) : orc_sph_count(step);
+    double T = 1.0, cd[3] = {0, 0, 0}, F[4] = {0, 0, 0, 0};
+    int neval = 0, napp = 0, term = 0;
+    int N = sc->occ_res[0];
+    for (int k = 0; k < nlat; ++k) {
+        double s = ((double)k + 0.5) * step, t = orc_sph_t_of_s(s);
+        double x[3], p[3];
+        for (int a = 0; a < 3; ++a) x[a] = o[a] + t * d[a];
+        orc_contract_sph(x, p);
+        int cell[3];
+        if (op->decide_f32) {
+            float p32[3];
+            orc32_sph_point(o32, d32, (float)step, k, p32);
+            cell32(p32, N, cell);
+        } else {
+            cell64(p, N, cell, NULL);
+        }
+        if (!occ_at(sc, cell)) continue;
+        double tt[8];
+        orc_field(sc, p, tt, NULL);
+        double tau = exp(tt[0]);
+        double dt = orc_sph_t_of_s(((double)k + 1.0) * step) - orc_sph_t_of_s((double)k * step);
+        double alpha = 1.0 - exp(-tau * dt);
+        ++neval;
+        if (alpha > 0.0) ++napp;
+        double w = alpha * T;
+        for (int c = 0; c < 3; ++c) cd[c] += w * sigmoid(tt[1 + c]);
+        for (int c = 0; c < 4; ++c) F[c] += w * sigmoid(tt[4 + c]);
+        T *= (1.0 - alpha);
+        if (op->early_term && T < op->t_term) { term = 1; break; }
+    }
+    double h[3] = {0, 0, 0};
+    if (!op->no_mlp) orc_mlp(sc->mlp, cd, F, d, h);
+    for (int c = 0; c < 3; ++c) { rec[ORC_RGB + c] = cd[c] + h[c]; rec[ORC_CD + c] = cd[c]; }
+    for (int c = 0; c < 4; ++c) rec[ORC_F + c] = F[c];
+    rec[ORC_T] = T;
+    rec[ORC_NLAT] = nlat;
+    rec[ORC_NEVAL] = neval;
+    rec[ORC_NAPP] = napp;
+    rec[ORC_TERM] = term;
+    rec[ORC_SEGS] = 0;
+}
+
 static void render_ray(const orc_scene *sc, const orc_opts *op, const float *cam, int i, int j,
                        double *rec)
 {
+    if (op->contraction == 1) {
+        render_ray_sph(sc, op, cam, i, j, rec);
+        return;
+    }
     double o[3], d[3];
     orc_seg segs[ORC_MAX_SEGS];
     orc_ray(cam, i, j, o, d);
@@ -783,7 +901,7 @@ typedef struct {
     int tid, nth;
     /* trace */
     double step, eps;
-    int decide_f32, words;
+    int decide_f32, words, contraction;
     uint32_t *mask, *flags;
     int32_t *nlat;
 } job;
@@ -854,6 +972,30 @@ static void *trace_worker(void *arg)
         uint32_t *fl = jb->flags ? jb->flags + (size_t)r * jb->words : NULL;
         memset(m, 0, sizeof(uint32_t) * jb->words);
         if (fl) memset(fl, 0, sizeof(uint32_t) * jb->words);
+        if (jb->contraction == 1) {       /* spherical contraction: every sample visited */
+            double o[3], d[3];
+            float o32[3], d32[3];
+            orc_ray(cam, i, j, o, d);
+            orc32_ray(cam, i, j, o32, d32);
+            int nl = jb->decide_f32 ? orc32_sph_count((float)jb->step) : orc_sph_count(jb->step);
+            jb->nlat[r] = nl;
+            for (int k = 0; k < nl && k < 32 * jb->words; ++k) {
+                double x[3], p[3], fd;
+                double t = orc_sph_t_of_s(((double)k + 0.5) * jb->step);
+                for (int a = 0; a < 3; ++a) x[a] = o[a] + t * d[a];
+                orc_contract_sph(x, p);
+                int cell[3];
+                cell64(p, N, cell, &fd);
+                if (jb->decide_f32) {
+                    float p32[3];
+                    orc32_sph_point(o32, d32, (float)jb->step, k, p32);
+                    cell32(p32, N, cell);
+                }
+                if (occ_at(sc, cell)) m[k >> 5] |= 1u << (k & 31);
+                if (fl && fd < jb->eps) fl[k >> 5] |= 1u << (k & 31);
+            }
+            continue;
+        }
         double o[3], d[3];
         orc_seg segs[ORC_MAX_SEGS];
         orc_ray(cam, i, j, o, d);
@@ -886,10 +1028,12 @@ static void *trace_worker(void *arg)
 
 int orc_trace(const orc_scene *sc, const float *cams, int n_cams, int W, int H,
               const int32_t *pix, int n_pix, double step, int decide_f32, double eps,
-              uint32_t *mask, uint32_t *flags, int words, int32_t *n_lattice, int n_threads)
+              uint32_t *mask, uint32_t *flags, int words, int32_t *n_lattice, int n_threads,
+              int contraction)
 {
     job jb;
     memset(&jb, 0, sizeof jb);
+    jb.contraction = contraction;
     jb.sc = sc; jb.cams = cams; jb.n_cams = n_cams; jb.W = W; jb.H = H;
     jb.pix = pix; jb.n_pix = n_pix; jb.step = step; jb.decide_f32 = decide_f32; jb.eps = eps;
     jb.mask = mask; jb.flags = flags; jb.words = words; jb.nlat = n_lattice;

@@ -53,6 +53,8 @@ typedef struct {
     int early_term;     /* 1: stop after the sample at which T drops below t_term */
     int decide_f32;     /* 1: lattice / occupancy decisions taken in FP32 (the kernel's precision) */
     int no_mlp;         /* 1: output C_d only (RGB = C_d) */
+    int contraction;    /* 0: contract_pi with its segment lattice (Sec. 3.2); 1: the spherical
+                           contraction of mip-NeRF 360 (Eq. contract360) marched densely */
 } orc_opts;
 
 typedef struct {
@@ -95,7 +97,18 @@ int orc_render_grad(const orc_scene *sc, const float *cams, int n_cams, int W, i
  * FP64 position lies within `eps` of a cell face. */
 int orc_trace(const orc_scene *sc, const float *cams, int n_cams, int W, int H,
               const int32_t *pix, int n_pix, double step, int decide_f32, double eps,
-              uint32_t *mask, uint32_t *flags, int words, int32_t *n_lattice, int n_threads);
+              uint32_t *mask, uint32_t *flags, int words, int32_t *n_lattice, int n_threads,
+              int contraction);
+
+/* Ablation (Sec. 3.2, Table 2 (c)): the spherical contraction of mip-NeRF 360 and its dense
+ * march.  orc_contract_sph maps |x|_2 <= 1 to itself and beyond to (2 - 1/|x|) x/|x|.  Sample k
+ * of a ray sits at s_k = (k + 1/2) step for (k + 1) step < 2, at ray parameter t(s) = s for
+ * s <= 1 and 1/(2 - s) beyond; its world step is t((k+1) step) - t(k step). */
+void   orc_contract_sph(const double x[3], double p[3]);
+double orc_sph_t_of_s(double s);
+int    orc_sph_count(double step);
+int    orc32_sph_count(float step);
+void   orc32_sph_point(const float o[3], const float d[3], float step, int k, float p[3]);
 
 /* FP32 decision replica (the kernel's traversal arithmetic, Sec. 3.2 + Sec. 5) */
 typedef struct {
