@@ -93,7 +93,13 @@ typedef struct merf_render_opts {
     float t_term;        /* early-termination threshold on transmittance (Sec. 5: 2e-4) */
     int32_t precision;   /* MERF_PREC_* */
     int32_t early_term;  /* 1: stop a ray after the sample at which T < t_term */
-    int32_t reserved;    /* must be 0 */
+    int32_t contraction; /* 0: contract_pi (Sec. 3.2) with its segment lattice and empty-space
+                            skipping.  1: the ablation of Sec. 3.2 / Table 2 (c), mip-NeRF 360's
+                            spherical contraction (Eq. contract360): rays bend, so every sample of
+                            a dense march -- s_k = (k + 1/2) step for (k + 1) step < 2, ray
+                            parameter t(s) = s (s <= 1), 1/(2 - s) beyond -- is visited and
+                            evaluated iff its finest occupancy cell is set.  FP32 only; not for
+                            merf_render_backward (MERF_ERR_UNSUPPORTED). */
 } merf_render_opts;
 
 typedef struct merf_scene merf_scene;  /* opaque; owns device memory */

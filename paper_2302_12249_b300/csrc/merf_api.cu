@@ -169,7 +169,10 @@ merf_status check_opts(const merf_render_opts *o)
         return fail(MERF_ERR_INVALID_ARG, "t_term %g must be in [0, 1)", (double)o->t_term);
     if (o->early_term != 0 && o->early_term != 1)
         return fail(MERF_ERR_INVALID_ARG, "early_term must be 0 or 1");
-    if (o->reserved != 0) return fail(MERF_ERR_INVALID_ARG, "reserved must be 0");
+    if (o->contraction != 0 && o->contraction != 1)
+        return fail(MERF_ERR_INVALID_ARG, "contraction %d must be 0 (contract_pi) or 1 (spherical)", o->contraction);
+    if (o->contraction == 1 && o->precision != MERF_PREC_FP32)
+        return fail(MERF_ERR_UNSUPPORTED, "the spherical-contraction ablation renders in FP32 only");
     if (o->precision != MERF_PREC_FP32 && o->precision != MERF_PREC_FP16 && o->precision != MERF_PREC_BF16)
         return fail(MERF_ERR_INVALID_ARG, "precision %d is not a MERF_PREC_* value", o->precision);
     return MERF_OK;
@@ -204,6 +207,7 @@ merf::RenderParams make_params(const merf_scene *s, const merf_render_opts *o, i
     P.step = o->step;
     P.t_term = o->t_term;
     P.early_term = o->early_term;
+    P.contraction = o->contraction;
     return P;
 }
 
@@ -235,7 +239,16 @@ merf_status launch_render(const merf_scene *s, const merf_camera *cams, int n, i
         for (int c = 0; c < nc; ++c) memcpy(P.cams.m[c], &cams[c0 + c], sizeof(merf_camera));
         const dim3 grid((W + merf::kTileW - 1) / merf::kTileW, (H + merf::kTileH - 1) / merf::kTileH, nc);
         const int geo = merf::gather_geometry(s->desc);
-        if (s->desc.storage == MERF_STORAGE_F32_DENSE)
+        if (o->contraction == 1) {          // spherical-contraction ablation (FP32, dense march)
+            if (s->desc.storage == MERF_STORAGE_F32_DENSE)
+                merf::render_kernel<1, 0, merf::kGeoRuntime, 1><<<grid, block, 0, st>>>(P);
+            else if (geo == merf::kGeoPaper)
+                merf::render_kernel<0, 0, merf::kGeoPaper, 1><<<grid, block, 0, st>>>(P);
+            else if (geo == merf::kGeoGridOnly)
+                merf::render_kernel<0, 0, merf::kGeoGridOnly, 1><<<grid, block, 0, st>>>(P);
+            else
+                merf::render_kernel<0, 0, merf::kGeoRuntime, 1><<<grid, block, 0, st>>>(P);
+        } else if (s->desc.storage == MERF_STORAGE_F32_DENSE)
             merf::render_kernel<1, 0, merf::kGeoRuntime><<<grid, block, 0, st>>>(P);
         else if (o->precision == MERF_PREC_FP16)
             launch_u8<1>(geo, grid, block, st, P);
@@ -535,6 +548,7 @@ merf_status merf_render_backward(const merf_scene *scene, const merf_camera *cam
     if (scene->desc.storage != MERF_STORAGE_F32_DENSE)
         return fail(MERF_ERR_UNSUPPORTED, "the adjoint is defined for dense float scenes");
     if (opts->precision != MERF_PREC_FP32) return fail(MERF_ERR_UNSUPPORTED, "the adjoint runs in FP32");
+    if (opts->contraction != 0) return fail(MERF_ERR_UNSUPPORTED, "the adjoint follows contract_pi only");
     merf::RenderParams R = make_params(scene, opts, W, H);
     merf::BackwardParams P;
     memset(&P, 0, sizeof P);

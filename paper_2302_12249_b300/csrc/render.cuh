@@ -38,6 +38,7 @@ struct RenderParams {
     int W, H, cam0;
     float step, t_term;
     int early_term;
+    int contraction;                  // 0: contract_pi (Sec. 3.2); 1: spherical ablation, dense
     CamBlock cams;
 };
 
@@ -393,6 +394,30 @@ struct RayState {
 };
 
 // March one pixel ray: traversal, gather, activations and front-to-back compositing.
+// Pre-activation density and appearance exponents of the field at a contracted point: all
+// channels in one tap-major pass; the appearance values are used only when the opacity is
+// non-zero (Sec. 5), which changes nothing else (weight alpha T = 0).
+template <int kStorage, int kPrec, int kGeo>
+__device__ __forceinline__ void eval_field(const FieldView &fv, float p0, float p1, float p2, float &dens, AppArg &ya)
+{
+    if constexpr (kStorage == 0) {
+        Taps tp;
+        gather_u8<kGeo>(fv, p0, p1, p2, tp);
+        float2 k[4];
+        if constexpr (kPrec == 0) byte_sums_u8<kTaps<kGeo>>(tp, k);
+        else byte_sums_lp<kPrec, kTaps<kGeo>>(tp, k);   // FP16 / BF16 appearance; density FP32
+        const float wsum = tp.wv + (float)kPlaneSources<kGeo>;
+        dens = dequant_density(k[0].x, wsum);
+        ya = app_arg_u8(k, wsum);
+    } else {
+        float all[8];
+        field_f32(fv, p0, p1, p2, all);
+        dens = all[0];
+        ya = app_arg(all + 1);
+    }
+}
+
+// March one pixel ray: traversal, gather, activations and front-to-back compositing.
 template <int kStorage, int kPrec, int kGeo = kGeoRuntime>
 __device__ __forceinline__ void march_ray(const FieldView &fv, const OccView &occ, const float *cam, int i, int j,
                                           float step, float t_term, int early_term, RayState &r)
@@ -410,30 +435,7 @@ __device__ __forceinline__ void march_ray(const FieldView &fv, const OccView &oc
         if (!wk.next_sample(occ, p0, p1, p2)) break;
         float dens;
         AppArg ya;
-        Taps tp;
-        // all channels in one tap-major pass; the appearance values are used only when the
-        // opacity is non-zero (Sec. 5), which changes nothing else (weight alpha T = 0)
-        if constexpr (kStorage == 0 && kPrec == 0) {
-            gather_u8<kGeo>(fv, p0, p1, p2, tp);
-            float2 k[4];
-            byte_sums_u8<kTaps<kGeo>>(tp, k);
-            const float wsum = tp.wv + (float)kPlaneSources<kGeo>;
-            dens = dequant_density(k[0].x, wsum);
-            ya = app_arg_u8(k, wsum);
-        } else if constexpr (kStorage == 0) {
-            // FP16 / BF16 appearance arithmetic; density in FP32 exactly as above
-            gather_u8<kGeo>(fv, p0, p1, p2, tp);
-            float2 k[4];
-            byte_sums_lp<kPrec, kTaps<kGeo>>(tp, k);
-            const float wsum = tp.wv + (float)kPlaneSources<kGeo>;
-            dens = dequant_density(k[0].x, wsum);
-            ya = app_arg_u8(k, wsum);
-        } else {
-            float all[8];
-            field_f32(fv, p0, p1, p2, all);
-            dens = all[0];
-            ya = app_arg(all + 1);
-        }
+        eval_field<kStorage, kPrec, kGeo>(fv, p0, p1, p2, dens, ya);
         const float tau = __expf(dens);
         const float dw = wk.delta_world(wk.k);
         const float alpha = 1.0f - __expf(-tau * dw);
@@ -445,6 +447,45 @@ __device__ __forceinline__ void march_ray(const FieldView &fv, const OccView &oc
             if (early_term && r.T < t_term) { r.term = 1; break; }
         }
         ++wk.k;
+    }
+    r.cd[0] = acc.c0; r.cd[1] = acc.c12.x; r.cd[2] = acc.c12.y;
+    r.F[0] = acc.f01.x; r.F[1] = acc.f01.y; r.F[2] = acc.f23.x; r.F[3] = acc.f23.y;
+}
+
+// The spherical-contraction ablation: the same field, quadrature and compositing, with every
+// sample of the dense march visited and its own finest occupancy cell tested (no skipping).
+template <int kStorage, int kGeo>
+__device__ __forceinline__ void march_ray_sph(const FieldView &fv, const OccView &occ, const float *cam, int i,
+                                              int j, float step, float t_term, int early_term, RayState &r)
+{
+    float o[3];
+    ray_f32(cam, i, j, o, r.d);
+    const int n = sph_count(step);
+    r.nlat = n;
+    Accum acc;
+    acc.c0 = 0.0f;
+    acc.c12 = acc.f01 = acc.f23 = make_float2(0.0f, 0.0f);
+    const int N0 = occ.res[0];
+    const float sc0 = (float)N0 * 0.25f;
+    const int h0 = N0 >> 1;
+    for (int k = 0; k < n; ++k) {
+        float p[3];
+        sph_point(o, r.d, step, k, p);
+        const int c0 = cell_of(p[0], sc0, h0, N0), c1 = cell_of(p[1], sc0, h0, N0), c2 = cell_of(p[2], sc0, h0, N0);
+        if (__ldg(occ.level[0] + ((size_t)c2 * N0 + c1) * N0 + c0) == 0) continue;
+        float dens;
+        AppArg ya;
+        eval_field<kStorage, 0, kGeo>(fv, p[0], p[1], p[2], dens, ya);
+        const float tau = __expf(dens);
+        const float dw = sph_t(F_MUL(F_ADD((float)k, 1.0f), step)) - sph_t(F_MUL((float)k, step));
+        const float alpha = 1.0f - __expf(-tau * dw);
+        ++r.neval;
+        if (alpha > 0.0f) {
+            ++r.napp;
+            composite(acc, alpha * r.T, ya);
+            r.T = r.T * (1.0f - alpha);
+            if (early_term && r.T < t_term) { r.term = 1; break; }
+        }
     }
     r.cd[0] = acc.c0; r.cd[1] = acc.c12.x; r.cd[2] = acc.c12.y;
     r.F[0] = acc.f01.x; r.F[1] = acc.f01.y; r.F[2] = acc.f23.x; r.F[3] = acc.f23.y;
@@ -492,9 +533,9 @@ __device__ __forceinline__ void deferred_mlp(MlpSmem<kPrec> &ms, const RayState 
 template <int kStorage, int kPrec>
 constexpr int kMinBlocks = kStorage != 0 ? 4 : 6;
 
-template <int kStorage, int kPrec, int kGeo>   // storage 0: uint8 block-sparse, 1: float32 dense;
-                                               // precision 0: FP32, 1: FP16, 2: BF16 (uint8 only);
-                                               // kGeo: gather geometry (kGeoRuntime / kGeoPaper)
+template <int kStorage, int kPrec, int kGeo, int kSph = 0>
+// storage 0: uint8 block-sparse, 1: float32 dense; precision 0: FP32, 1: FP16, 2: BF16 (uint8
+// only); kGeo: gather geometry; kSph 1: the spherical-contraction ablation (FP32)
 __global__ void __launch_bounds__(kThreads, (kMinBlocks<kStorage, kPrec>)) render_kernel(const __grid_constant__ RenderParams P)
 {
     __shared__ MlpSmem<kPrec> ms;
@@ -507,7 +548,12 @@ __global__ void __launch_bounds__(kThreads, (kMinBlocks<kStorage, kPrec>)) rende
     const bool inside = (i < P.W) && (j < P.H);
     RayState r;
     ray_state_init(r);
-    if (inside) march_ray<kStorage, kPrec, kGeo>(P.fv, P.occ, P.cams.m[cl], i, j, P.step, P.t_term, P.early_term, r);
+    if (inside) {
+        if constexpr (kSph == 0)
+            march_ray<kStorage, kPrec, kGeo>(P.fv, P.occ, P.cams.m[cl], i, j, P.step, P.t_term, P.early_term, r);
+        else
+            march_ray_sph<kStorage, kGeo>(P.fv, P.occ, P.cams.m[cl], i, j, P.step, P.t_term, P.early_term, r);
+    }
     float h[3];
     deferred_mlp<kPrec>(ms, r, inside, h);
     if (inside) {
@@ -553,6 +599,21 @@ static __global__ void __launch_bounds__(kThreads) trace_kernel(const __grid_con
     for (int w = 0; w < P.words; ++w) row[w] = 0u;
     float o[3], d[3];
     ray_f32(P.cams.m[cl], i, j, o, d);
+    if (P.contraction == 1) {          // spherical ablation: every sample of the dense march
+        const int n = sph_count(P.step);
+        P.nlat[pix] = n;
+        const int N0 = P.occ.res[0];
+        const float sc0 = (float)N0 * 0.25f;
+        const int h0 = N0 >> 1;
+        for (int k = 0; k < n && k < 32 * P.words; ++k) {
+            float p[3];
+            sph_point(o, d, P.step, k, p);
+            const int c0 = cell_of(p[0], sc0, h0, N0), c1 = cell_of(p[1], sc0, h0, N0),
+                      c2 = cell_of(p[2], sc0, h0, N0);
+            if (__ldg(P.occ.level[0] + ((size_t)c2 * N0 + c1) * N0 + c0) != 0) row[k >> 5] |= 1u << (k & 31);
+        }
+        return;
+    }
     Walker wk;
     wk.init(o, d, P.step);
     P.nlat[pix] = wk.nlat;

@@ -252,6 +252,39 @@ __device__ __forceinline__ int cell_of(float p, float scale, int half, int N)
     return min(max(c, 0), N - 1);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Ablation (Sec. 3.2, Table 2 (c)): the spherical contraction of mip-NeRF 360,
+// contract(x) = x for |x|_2 <= 1 and (2 - 1/|x|_2) x / |x|_2 beyond.  It bends straight rays, so
+// there is no segment lattice and no AABB exit: the ray is marched densely, sample k at
+// s_k = (k + 1/2) delta_s for (k + 1) delta_s < 2, at ray parameter t(s) = s for s <= 1 and
+// 1 / (2 - s) beyond (mip-NeRF 360's inverse spacing, s = 2 being the point at infinity), each
+// sample evaluated iff its finest occupancy cell is set.  Positions are decisions (they pick the
+// cell), so they use the same IEEE-rounded operations, in a fixed order, as the FP32 restatement
+// the tests compare against.
+
+// number of samples: k with (k + 1) delta_s < 2
+__device__ __forceinline__ int sph_count(float step)
+{
+    int n = (int)F_DIV(2.0f, step);
+    while (n > 0 && !(F_MUL(F_ADD((float)(n - 1), 1.0f), step) < 2.0f)) --n;
+    while (F_MUL(F_ADD((float)n, 1.0f), step) < 2.0f) ++n;
+    return n;
+}
+
+__device__ __forceinline__ float sph_t(float s) { return s <= 1.0f ? s : F_DIV(1.0f, F_SUB(2.0f, s)); }
+
+__device__ __forceinline__ void sph_point(const float o[3], const float d[3], float step, int k, float p[3])
+{
+    const float t = sph_t(F_MUL(F_ADD((float)k, 0.5f), step));
+    const float x0 = F_ADD(o[0], F_MUL(t, d[0])), x1 = F_ADD(o[1], F_MUL(t, d[1])),
+                x2 = F_ADD(o[2], F_MUL(t, d[2]));
+    const float r = F_SQRT(F_ADD(F_ADD(F_MUL(x0, x0), F_MUL(x1, x1)), F_MUL(x2, x2)));
+    const float w = r <= 1.0f ? 1.0f : F_DIV(F_SUB(2.0f, F_DIV(1.0f, r)), r);
+    p[0] = r <= 1.0f ? x0 : F_MUL(x0, w);
+    p[1] = r <= 1.0f ? x1 : F_MUL(x1, w);
+    p[2] = r <= 1.0f ? x2 : F_MUL(x2, w);
+}
+
 // Walk state of one ray.
 struct Walker {
     Segs sg;

@@ -46,7 +46,7 @@ class Desc(ct.Structure):
 
 class Opts(ct.Structure):
     _fields_ = [("step", ct.c_float), ("t_term", ct.c_float), ("precision", ct.c_int32),
-                ("early_term", ct.c_int32), ("reserved", ct.c_int32)]
+                ("early_term", ct.c_int32), ("contraction", ct.c_int32)]
 
 
 class ServerOpts(ct.Structure):
@@ -127,8 +127,13 @@ def _dev_ptr(t: torch.Tensor, dtype, numel: int, name: str):
     return ct.c_void_p(t.data_ptr())
 
 
-def opts(step: float, t_term: float = 2e-4, early_term: bool = True, precision: int = PREC_FP32) -> Opts:
-    return Opts(step=step, t_term=t_term, precision=precision, early_term=int(early_term), reserved=0)
+CONTRACT_PI, CONTRACT_SPHERICAL = 0, 1   # merf_render_opts.contraction
+
+
+def opts(step: float, t_term: float = 2e-4, early_term: bool = True, precision: int = PREC_FP32,
+         contraction: int = CONTRACT_PI) -> Opts:
+    return Opts(step=step, t_term=t_term, precision=precision, early_term=int(early_term),
+                contraction=int(contraction))
 
 
 def cameras(cams: np.ndarray) -> np.ndarray:
@@ -192,13 +197,14 @@ class Scene:
 def render(scene: Scene, cams: np.ndarray, W: int, H: int, step: float, out: Optional[torch.Tensor] = None,
            t_term: float = 2e-4, early_term: bool = True, precision: int = PREC_FP32,
            aux: Optional[torch.Tensor] = None, counters: Optional[torch.Tensor] = None,
-           stream=None) -> torch.Tensor:
-    """Render n cameras into a CUDA float32 tensor [n, H, W, 3]."""
+           stream=None, contraction: int = CONTRACT_PI) -> torch.Tensor:
+    """Render n cameras into a CUDA float32 tensor [n, H, W, 3].  contraction CONTRACT_SPHERICAL
+    selects the spherical-contraction ablation (dense march, FP32)."""
     cams = cameras(cams)
     n = cams.shape[0]
     if out is None:
         out = torch.empty((n, H, W, 3), dtype=torch.float32, device="cuda")
-    o = opts(step, t_term, early_term, precision)
+    o = opts(step, t_term, early_term, precision, contraction)
     op = _dev_ptr(out, torch.float32, n * H * W * 3, "out")
     ap = _dev_ptr(aux, torch.float32, n * H * W * AUX_SIZE, "aux") if aux is not None else None
     cp = _dev_ptr(counters, torch.int64, 4, "counters") if counters is not None else None
@@ -242,13 +248,14 @@ def render_host_noalloc(scene: Scene, cams: np.ndarray, W: int, H: int, step: fl
     return host_out
 
 
-def trace(scene: Scene, cams: np.ndarray, W: int, H: int, step: float, words: int, stream=None):
+def trace(scene: Scene, cams: np.ndarray, W: int, H: int, step: float, words: int, stream=None,
+          contraction: int = CONTRACT_PI):
     """Evaluated lattice-sample bit masks [n*H*W, words] (uint32 as int32) and lattice counts."""
     cams = cameras(cams)
     n = cams.shape[0]
     mask = torch.empty((n * H * W, words), dtype=torch.int32, device="cuda")
     nlat = torch.empty((n * H * W,), dtype=torch.int32, device="cuda")
-    o = opts(step, early_term=False)
+    o = opts(step, early_term=False, contraction=contraction)
     _check(lib().merf_trace(scene.handle, _np_ptr(cams), n, W, H, ct.c_void_p(mask.data_ptr()), words,
                             ct.c_void_p(nlat.data_ptr()), ct.byref(o), _stream(stream)))
     return mask, nlat

@@ -137,8 +137,16 @@ def test_render_rejects_null_and_bad_sizes():
     assert L.merf_render(fake, bad.ctypes.data, 1, 4, 4, None, ct.byref(o), None) == merf.ERR_INVALID_ARG
 
 
+def test_spherical_ablation_is_fp32_only():
+    L = merf.lib()
+    o = merf.opts(1 / 64, precision=merf.PREC_FP16, contraction=merf.CONTRACT_SPHERICAL)
+    cams = synth.config_cameras("tiny")
+    assert L.merf_render(ct.c_void_p(1), cams.ctypes.data, 1, 4, 4, ct.c_void_p(1), ct.byref(o), None) == \
+        merf.ERR_UNSUPPORTED
+
+
 @pytest.mark.parametrize("kw", [dict(step=0.0), dict(step=float("nan")), dict(t_term=1.5),
-                                dict(early_term=2), dict(reserved=1)])
+                                dict(early_term=2), dict(contraction=2), dict(contraction=-1)])
 def test_render_rejects_bad_opts(kw):
     L = merf.lib()
     o = merf.opts(1 / 64)
