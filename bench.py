@@ -122,10 +122,24 @@ def _dist():
     return None, 0, 1, 0
 
 
-def _cpu_baseline(scene, cams, seconds: float = 12.0):
-    """The FP64 oracle on the host cores, on random pixels of the same frames, for ~`seconds`."""
+def _oracle_leg(scene, cams):
+    """The one part of the benchmark that runs the FP64 CPU oracle (host cores): the CPU
+    baseline, the reference values the precision form is scored against, and the distinct data
+    one 1080p frame reads (camera 0 of the workload, its own evaluated samples)."""
     import oracle
     osc = oracle.OracleScene(scene)
+    cpu = _cpu_baseline(oracle, osc, cams)
+    pcams, pix = _precision_pixels()
+    lo = oracle.render(osc, pcams, W_IMG, H_IMG, STEP, pix=pix, t_term=2e-4 * 0.999)[:, 0:3]
+    hi = oracle.render(osc, pcams, W_IMG, H_IMG, STEP, pix=pix, t_term=2e-4 * 1.001)[:, 0:3]
+    t0 = time.perf_counter()
+    fp = oracle.footprint(osc, cams[:1], W_IMG, H_IMG, STEP)
+    fp["seconds"] = time.perf_counter() - t0
+    return cpu, (pix, lo, hi), fp
+
+
+def _cpu_baseline(oracle, osc, cams, seconds: float = 12.0):
+    """The FP64 oracle on the host cores, on random pixels of the same frames, for ~`seconds`."""
     threads = oracle.default_threads()
     rng = np.random.default_rng(12345)
     rays, t0 = 0, time.perf_counter()
@@ -171,23 +185,31 @@ def _frames_720p(gs, steps=10, warmup=3):
             "ms_per_step": ms, "workload": f"{cams.shape[0]} ring cameras x {W}x{H}, FP32"}
 
 
-def _precision_form(gs, scene, n_cams=64, steps=2, n_pix=2000):
+PRECISION_CAMS, PRECISION_PIX = 64, 2000
+
+
+def _precision_pixels():
+    """The precision form's 64 ring cameras and the 2000 pixels its error is measured on."""
+    from paper_2302_12249_b300 import synth
+    cams = synth.ring_cameras(PRECISION_CAMS, W_IMG, H_IMG, radius=1.5, seed=synth.SEED_CAMERA + 1)
+    rng = np.random.default_rng(99)
+    pix = np.stack([rng.integers(0, PRECISION_CAMS, PRECISION_PIX), rng.integers(0, W_IMG, PRECISION_PIX),
+                    rng.integers(0, H_IMG, PRECISION_PIX)], 1).astype(np.int32)
+    return cams, pix
+
+
+def _precision_form(gs, ref=None, steps=2):
     """Precision form: the same scene rendered from 64 ring cameras at 1920x1080 in FP32, FP16 and
     BF16 (uint8 features, appearance arithmetic and deferred MLP in 16 bits on tensor cores,
     density/transmittance/compositing in FP32).  Time per step and, on sampled pixels, the
-    error against the FP64 oracle (max |dRGB| per channel and PSNR)."""
+    error against the FP64 oracle (max |dRGB| per channel and PSNR) when the oracle leg supplied
+    its reference values `ref` = (pixels, lower, upper threshold renders)."""
     import torch
-    import oracle
-    from paper_2302_12249_b300 import merf, synth
-    cams = synth.ring_cameras(n_cams, W_IMG, H_IMG, radius=1.5, seed=synth.SEED_CAMERA + 1)
+    from paper_2302_12249_b300 import merf
+    cams, pix = _precision_pixels()
+    n_cams, n_pix = cams.shape[0], pix.shape[0]
     out = torch.empty((n_cams, H_IMG, W_IMG, 3), dtype=torch.float32, device="cuda")
-    rng = np.random.default_rng(99)
-    pix = np.stack([rng.integers(0, n_cams, n_pix), rng.integers(0, W_IMG, n_pix),
-                    rng.integers(0, H_IMG, n_pix)], 1).astype(np.int32)
     lin = torch.from_numpy((pix[:, 0].astype(np.int64) * H_IMG + pix[:, 2]) * W_IMG + pix[:, 1]).cuda()
-    osc = oracle.OracleScene(scene)
-    lo = oracle.render(osc, cams, W_IMG, H_IMG, STEP, pix=pix, t_term=2e-4 * 0.999)[:, 0:3]
-    hi = oracle.render(osc, cams, W_IMG, H_IMG, STEP, pix=pix, t_term=2e-4 * 1.001)[:, 0:3]
     res = {}
     for name, prec in (("fp32", merf.PREC_FP32), ("fp16", merf.PREC_FP16), ("bf16", merf.PREC_BF16)):
         merf.render(gs, cams, W_IMG, H_IMG, STEP, out=out, precision=prec)
@@ -199,13 +221,15 @@ def _precision_form(gs, scene, n_cams=64, steps=2, n_pix=2000):
         b.record()
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / steps
-        rgb = out.reshape(-1, 3)[lin].double().cpu().numpy()
-        e_lo, e_hi = np.abs(rgb - lo).max(axis=1), np.abs(rgb - hi).max(axis=1)
-        ref = np.where((e_lo <= e_hi)[:, None], lo, hi)
-        mse = float(np.mean((rgb - ref) ** 2))
-        res[name] = {"ms_per_step": ms, "mrays_per_s": n_cams * W_IMG * H_IMG / (ms / 1e3) / 1e6,
-                     "max_abs_err": float(np.abs(rgb - ref).max()),
-                     "psnr_db": (10 * math.log10(1.0 / mse)) if mse > 0 else None}
+        res[name] = {"ms_per_step": ms, "mrays_per_s": n_cams * W_IMG * H_IMG / (ms / 1e3) / 1e6}
+        if ref is not None:
+            _, lo, hi = ref
+            rgb = out.reshape(-1, 3)[lin].double().cpu().numpy()
+            e_lo, e_hi = np.abs(rgb - lo).max(axis=1), np.abs(rgb - hi).max(axis=1)
+            closest = np.where((e_lo <= e_hi)[:, None], lo, hi)
+            mse = float(np.mean((rgb - closest) ** 2))
+            res[name]["max_abs_err"] = float(np.abs(rgb - closest).max())
+            res[name]["psnr_db"] = (10 * math.log10(1.0 / mse)) if mse > 0 else None
     res["workload"] = f"{n_cams} ring cameras x 1920x1080, {steps} timed steps each; error on {n_pix} sampled pixels"
     res["fp16_speedup_vs_fp32"] = res["fp32"]["ms_per_step"] / res["fp16"]["ms_per_step"]
     return res
@@ -450,13 +474,14 @@ def run_ours(args):
     cams = cams[:args.cams]
     n_cams = cams.shape[0]
     rays_per_step = n_cams * W_IMG * H_IMG
+    prec = {"fp32": merf.PREC_FP32, "fp16": merf.PREC_FP16, "bf16": merf.PREC_BF16}[args.precision]
     out = torch.empty((n_cams, H_IMG, W_IMG, 3), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
     # untimed pass with counters: units of work per launch for the algorithmic byte count
     cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
     aux = torch.empty((n_cams, H_IMG, W_IMG, merf.AUX_SIZE), dtype=torch.float32, device="cuda")
-    merf.render(gs, cams, W_IMG, H_IMG, STEP, out=out, aux=aux, counters=cnt)
+    merf.render(gs, cams, W_IMG, H_IMG, STEP, out=out, aux=aux, counters=cnt, precision=prec)
     torch.cuda.synchronize()
     c = [int(v) for v in cnt.cpu().tolist()]
     del aux
@@ -464,7 +489,7 @@ def run_ours(args):
                  c[merf.CNT_RAYS] * B_OUT)
 
     for _ in range(args.warmup):
-        merf.render(gs, cams, W_IMG, H_IMG, STEP, out=out)
+        merf.render(gs, cams, W_IMG, H_IMG, STEP, out=out, precision=prec)
     torch.cuda.synchronize()
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
@@ -478,7 +503,7 @@ def run_ours(args):
     t_start.record(stream)
     for s in range(args.steps):
         ev[s][0].record(stream)
-        merf.render(gs, cams, W_IMG, H_IMG, STEP, out=out)
+        merf.render(gs, cams, W_IMG, H_IMG, STEP, out=out, precision=prec)
         ev[s][1].record(stream)
     t_end.record(stream)
     torch.cuda.synchronize()
@@ -502,12 +527,12 @@ def run_ours(args):
     if not args.no_e2e:
         staging = torch.empty_like(out)
         host = torch.empty(out.shape, dtype=torch.float32, pin_memory=True)
-        merf.render_host(gs, cams, W_IMG, H_IMG, STEP, staging, host)
+        merf.render_host(gs, cams, W_IMG, H_IMG, STEP, staging, host, precision=prec)
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            merf.render_host(gs, cams, W_IMG, H_IMG, STEP, staging, host)
+            merf.render_host(gs, cams, W_IMG, H_IMG, STEP, staging, host, precision=prec)
         e2e_s = time.perf_counter() - t0
         if dist:
             t = torch.tensor([e2e_s], device="cuda")
@@ -519,12 +544,12 @@ def run_ours(args):
     p720 = None
     if rank == 0 and world == 1 and not args.no_precision:
         p720 = _frames_720p(gs)
-    cpu = None
+    cpu = prec_ref = footprint = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = _cpu_baseline(scene, cams)
+        cpu, prec_ref, footprint = _oracle_leg(scene, synth.config_cameras("paper"))
     precision = None
     if rank == 0 and world == 1 and not args.no_precision:
-        precision = _precision_form(gs, scene)
+        precision = _precision_form(gs, prec_ref)
     differentiation = None
     if rank == 0 and world == 1 and not args.no_precision:
         differentiation = _differentiation()
@@ -543,8 +568,10 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "rays_per_step_per_gpu": rays_per_step,
+                "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16", "bf16": "bf16"}[args.precision],
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD.replace("FP32 path", f"{args.precision.upper()} path"),
+                           "rays_per_step_per_gpu": rays_per_step,
                            "scene_device_mb": round(gs.device_bytes / 1e6, 1),
                            "block_fraction": round(scene.stats["block_fraction"], 4),
                            "l2": "inputs larger than L2 (scene and per-step output each exceed 126 MB); no flush",
@@ -560,13 +587,19 @@ def run_ours(args):
                              "frac": achieved / peak,
                              "traffic": (TRAFFIC_BYTES_PER_LAUNCH
                                          if _sources_sha256() == TRAFFIC_SOURCES_SHA256 and n_cams == N_CAMS
-                                         else None),
-                             "kernel": "render_kernel<0,0> (FP32)", "kernel_ms": mean_kern_ms,
+                                         and args.precision == "fp32" else None),
+                             "kernel": f"render_kernel<0,{prec},1,0> ({args.precision.upper()})",
+                             "kernel_ms": mean_kern_ms,
                              "peak_source": peak_src},
                 "gpu_launches": args.steps,
                 "e2e": e2e, "clocks": ck}
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        if footprint is not None:
+            line["footprint_1080p_frame"] = dict(
+                footprint, algorithmic_bytes=alg_bytes / n_cams,
+                dram_bytes=(TRAFFIC_BYTES_PER_LAUNCH / N_CAMS if line["roofline"]["traffic"] else None),
+                frame="camera 0 of the workload, its evaluated samples, counted by the FP64 oracle")
         if p720 is not None:
             line["frames_720p"] = p720
         if precision is not None:
@@ -597,6 +630,8 @@ def main():
     ap.add_argument("--no-precision", action="store_true", help="skip the FP16/BF16 comparison (profiling)")
     ap.add_argument("--serve-requests", type=int, default=10000, help="requests of the serving run (0 = skip)")
     ap.add_argument("--no-variants", action="store_true", help="skip the grid-only comparison (profiling)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"],
+                    help="arithmetic of the main line (default FP32; the precision form is also reported)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -94,6 +94,9 @@ def lib():
                                 ct.c_void_p, ct.c_int, ct.c_double, ct.c_int, ct.c_double,
                                 ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_int]
         L.orc_trace.restype = ct.c_int
+        L.orc_footprint.argtypes = [ct.POINTER(_Scene), ct.c_void_p, ct.c_int, ct.c_int, ct.c_int,
+                                    ct.c_void_p, ct.c_int, ct.POINTER(_Opts), ct.c_void_p, ct.c_int]
+        L.orc_footprint.restype = ct.c_int
         L.orc_contract_sph.argtypes = [D3, D3]
         L.orc_sph_t_of_s.argtypes = [ct.c_double]
         L.orc_sph_t_of_s.restype = ct.c_double
@@ -312,6 +315,25 @@ def render(oscene: OracleScene, cams: np.ndarray, W: int, H: int, step: float,
     lib().orc_render(ct.byref(oscene.s), _ptr(cams), cams.shape[0], W, H, _ptr(pix),
                      0 if pix is None else n, ct.byref(op), _ptr(out), threads or default_threads())
     return out
+
+
+def footprint(oscene: OracleScene, cams: np.ndarray, W: int, H: int, step: float,
+              pix: Optional[np.ndarray] = None, t_term: float = 2e-4, early_term: bool = True,
+              threads: Optional[int] = None) -> dict:
+    """Distinct grid voxels, plane texels and index entries read by the evaluated samples of the
+    listed rays (uint8 scenes); bytes = 8 per voxel or texel, 4 per index entry."""
+    cams = np.ascontiguousarray(cams, dtype=np.float32).reshape(-1, 16)
+    if pix is not None:
+        pix = np.ascontiguousarray(pix, dtype=np.int32).reshape(-1, 3)
+    op = _Opts(step=step, t_term=t_term, early_term=int(early_term), decide_f32=1, no_mlp=0, contraction=0)
+    counts = np.zeros(3, np.uint64)
+    st = lib().orc_footprint(ct.byref(oscene.s), _ptr(cams), cams.shape[0], W, H, _ptr(pix),
+                             0 if pix is None else pix.shape[0], ct.byref(op), _ptr(counts),
+                             threads or default_threads())
+    if st != 0:
+        raise ValueError("footprint needs a uint8 block-sparse scene")
+    g, p, i = (int(v) for v in counts)
+    return {"grid_voxels": g, "plane_texels": p, "index_entries": i, "bytes": 8 * (g + p) + 4 * i}
 
 
 def trace(oscene: OracleScene, cams: np.ndarray, W: int, H: int, step: float, words: int,

@@ -577,6 +577,37 @@ static void cell64(const double p[3], int N, int cell[3], double *face_dist)
 
 static double sigmoid(double x) { return 1.0 / (1.0 + exp(-x)); }
 
+/* bit sets of the data read (orc_footprint) */
+typedef struct {
+    uint64_t *grid, *planes, *index;
+} orc_marks;
+
+static void set_bit(uint64_t *w, size_t i) { __atomic_fetch_or(w + (i >> 6), 1ull << (i & 63), __ATOMIC_RELAXED); }
+
+static void mark_sample(const orc_scene *sc, const double p[3], orc_marks *mk)
+{
+    int ix[2], iy[2], iz[2];
+    double w;
+    lin(p[0], sc->L, &ix[0], &ix[1], &w);
+    lin(p[1], sc->L, &iy[0], &iy[1], &w);
+    lin(p[2], sc->L, &iz[0], &iz[1], &w);
+    int B = sc->B, nb = sc->L / B;
+    set_bit(mk->index, ((size_t)(iz[0] / B) * nb + iy[0] / B) * nb + ix[0] / B);
+    for (int c = 0; c < 8; ++c) {
+        int x = ix[c & 1], y = iy[(c >> 1) & 1], z = iz[c >> 2];
+        if (sc->index_grid[((size_t)(z / B) * nb + y / B) * nb + x / B] >= 0)
+            set_bit(mk->grid, ((size_t)z * sc->L + y) * sc->L + x);
+    }
+    static const int col_axis[3] = {1, 0, 0}, row_axis[3] = {2, 2, 1};
+    for (int q = 0; q < (sc->R > 0 ? 3 : 0); ++q) {
+        int u[2], v[2];
+        lin(p[col_axis[q]], sc->R, &u[0], &u[1], &w);
+        lin(p[row_axis[q]], sc->R, &v[0], &v[1], &w);
+        for (int c = 0; c < 4; ++c)
+            set_bit(mk->planes, ((size_t)q * sc->R + v[c >> 1]) * sc->R + u[c & 1]);
+    }
+}
+
 /* The same quadrature with the spherical contraction, every sample visited (no skipping). */
 static void render_ray_sph(const orc_scene *sc, const orc_opts *op, const float *cam, int i, int j,
                            double *rec)
@@ -630,7 +661,7 @@ static void render_ray_sph(const orc_scene *sc, const orc_opts *op, const float 
 }
 
 static void render_ray(const orc_scene *sc, const orc_opts *op, const float *cam, int i, int j,
-                       double *rec)
+                       double *rec, orc_marks *mk)
 {
     if (op->contraction == 1) {
         render_ray_sph(sc, op, cam, i, j, rec);
@@ -672,6 +703,7 @@ static void render_ray(const orc_scene *sc, const orc_opts *op, const float *cam
 
         double tt[8];
         orc_field(sc, p, tt, NULL);
+        if (mk) mark_sample(sc, p, mk);
         double tau = exp(tt[0]);
         double dt = orc_t_of_s(segs, ns, o, d, ((double)k + 1.0) * step) -
                     orc_t_of_s(segs, ns, o, d, (double)k * step);
@@ -904,6 +936,7 @@ typedef struct {
     int decide_f32, words, contraction;
     uint32_t *mask, *flags;
     int32_t *nlat;
+    orc_marks *marks;      /* footprint: NULL when only rendering */
 } job;
 
 static void pixel_of(const job *jb, long r, int *cam, int *i, int *j)
@@ -926,7 +959,7 @@ static void *render_worker(void *arg)
     for (long r = jb->tid; r < n; r += jb->nth) {
         int c, i, j;
         pixel_of(jb, r, &c, &i, &j);
-        render_ray(jb->sc, jb->op, jb->cams + 16 * c, i, j, jb->out + ORC_OUT * r);
+        render_ray(jb->sc, jb->op, jb->cams + 16 * c, i, j, jb->out + ORC_OUT * r, jb->marks);
     }
     return NULL;
 }
@@ -955,6 +988,39 @@ int orc_render(const orc_scene *sc, const float *cams, int n_cams, int W, int H,
     jb.sc = sc; jb.op = opts; jb.cams = cams; jb.n_cams = n_cams; jb.W = W; jb.H = H;
     jb.pix = pix; jb.n_pix = n_pix; jb.out = out;
     run_jobs(&jb, render_worker, n_threads);
+    return 0;
+}
+
+int orc_footprint(const orc_scene *sc, const float *cams, int n_cams, int W, int H,
+                  const int32_t *pix, int n_pix, const orc_opts *opts, uint64_t counts[3], int n_threads)
+{
+    if (sc->storage != 0) return -1;
+    size_t nv = (size_t)sc->L * sc->L * sc->L, np = (size_t)3 * sc->R * sc->R, nb = (size_t)sc->L / sc->B;
+    nb = nb * nb * nb;
+    orc_marks mk;
+    mk.grid = (uint64_t *)calloc(nv / 64 + 1, 8);
+    mk.planes = (uint64_t *)calloc(np / 64 + 1, 8);
+    mk.index = (uint64_t *)calloc(nb / 64 + 1, 8);
+    if (!mk.grid || !mk.planes || !mk.index) {
+        free(mk.grid); free(mk.planes); free(mk.index);
+        return -2;
+    }
+    long n = pix ? n_pix : (long)n_cams * W * H;
+    double *out = (double *)malloc(sizeof(double) * ORC_OUT * (size_t)(n > 0 ? n : 1));
+    job jb;
+    memset(&jb, 0, sizeof jb);
+    jb.sc = sc; jb.op = opts; jb.cams = cams; jb.n_cams = n_cams; jb.W = W; jb.H = H;
+    jb.pix = pix; jb.n_pix = n_pix; jb.out = out; jb.marks = &mk;
+    run_jobs(&jb, render_worker, n_threads);
+    free(out);
+    uint64_t *sets[3] = {mk.grid, mk.planes, mk.index};
+    size_t words[3] = {nv / 64 + 1, np / 64 + 1, nb / 64 + 1};
+    for (int k = 0; k < 3; ++k) {
+        uint64_t c = 0;
+        for (size_t w = 0; w < words[k]; ++w) c += (uint64_t)__builtin_popcountll(sets[k][w]);
+        counts[k] = c;
+    }
+    free(mk.grid); free(mk.planes); free(mk.index);
     return 0;
 }
 

@@ -100,6 +100,14 @@ int orc_trace(const orc_scene *sc, const float *cams, int n_cams, int W, int H,
               uint32_t *mask, uint32_t *flags, int words, int32_t *n_lattice, int n_threads,
               int contraction);
 
+/* Distinct data a set of rays reads (the reuse beside the bandwidth roofline): the render's own
+ * evaluated samples (opts as in orc_render) each mark the eight grid voxels of their trilinear
+ * interpolation that lie in stored blocks, the index-grid entry of their lowest corner's block,
+ * and the four texels of each plane (clamped indices, as read).  counts[0..2] = distinct grid
+ * voxels, plane texels, index entries.  uint8 block-sparse scenes only. */
+int orc_footprint(const orc_scene *sc, const float *cams, int n_cams, int W, int H,
+                  const int32_t *pix, int n_pix, const orc_opts *opts, uint64_t counts[3], int n_threads);
+
 /* Ablation (Sec. 3.2, Table 2 (c)): the spherical contraction of mip-NeRF 360 and its dense
  * march.  orc_contract_sph maps |x|_2 <= 1 to itself and beyond to (2 - 1/|x|) x/|x|.  Sample k
  * of a ray sits at s_k = (k + 1/2) step for (k + 1) step < 2, at ray parameter t(s) = s for
