@@ -46,7 +46,7 @@ B_DENSITY, B_INDEX, B_APPEAR, B_OUT = 20, 4, 140, 12
 # measured with (otherwise null).
 TRAFFIC_BYTES_PER_LAUNCH = (402.82 + 617.59) * 1e6
 TRAFFIC_SOURCES = ("field.cuh", "merf_api.cu", "render.cuh", "scene.h", "traverse.cuh")
-TRAFFIC_SOURCES_SHA256 = "4d15bfb0bbfb99d3cb26385cf25dadf20a6aa6eec8251f8a0bfaea24d862b3ea"
+TRAFFIC_SOURCES_SHA256 = "4eb984d2eeed3b7472e169d77b704d91e2faf079cdfd6448be9957820657af3d"
 
 
 def _sources_sha256() -> str:

@@ -148,11 +148,13 @@ merf_status merf_render_aux(const merf_scene *scene, const merf_camera *cams, in
                             int H, float *out, float *aux, unsigned long long *counters,
                             const merf_render_opts *opts, void *stream);
 
-/* Render into host memory: renders like merf_render into the caller's device buffer
- * `d_staging` (float32 [n_cams][H][W][3]) and copies it to `h_out` (host, same shape;
- * page-locked for the copy to be asynchronous).  Cameras are rendered one launch each on
- * `stream` while the previous camera's image is copied on a library-owned copy stream (created on
- * the first call on each device).  Returns after every copy has completed. */
+/* Render into host memory `h_out` (host float32 [n_cams][H][W][3]).  If h_out is page-locked
+ * memory the device can address (cudaHostAlloc, or cudaHostRegister'ed, under unified
+ * addressing) the kernel writes the image there directly in one launch; `d_staging` is unused
+ * and may be NULL.  Otherwise the call renders like merf_render into the caller's device buffer
+ * `d_staging` (same shape), one launch per camera on `stream`, while the previous camera's image
+ * is copied to h_out on a library-owned copy stream (created on the first call on each device).
+ * Returns when the image is in h_out. */
 merf_status merf_render_host(const merf_scene *scene, const merf_camera *cams, int n_cams,
                              int W, int H, float *d_staging, float *h_out,
                              const merf_render_opts *opts, void *stream);

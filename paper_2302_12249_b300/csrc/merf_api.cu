@@ -411,17 +411,28 @@ HostCopy g_host_copy[64];
 merf_status merf_render_host(const merf_scene *scene, const merf_camera *cams, int n_cams, int W, int H,
                              float *d_staging, float *h_out, const merf_render_opts *opts, void *stream)
 {
-    if (!h_out || !d_staging) return fail(MERF_ERR_INVALID_ARG, "h_out / d_staging is NULL");
+    if (!h_out) return fail(MERF_ERR_INVALID_ARG, "h_out is NULL");
     merf_status st = check_frame(scene, cams, n_cams, W, H);
     if (st) return st;
     if ((st = check_opts(opts))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    // Page-locked host memory that the device can address (cudaHostAlloc, or registered with
+    // cudaHostRegister, under unified addressing): the kernel stores the image there directly,
+    // one launch for all cameras, no staging buffer and no copy.
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, h_out) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer) {
+        if ((st = launch_render(scene, cams, n_cams, W, H, (float *)pa.devicePointer, nullptr, nullptr, opts, s)))
+            return st;
+        const cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return fail(MERF_ERR_CUDA, "render_host: %s", cudaGetErrorString(e));
+        return ok();
+    }
+    cudaGetLastError();   // a pageable pointer is not an error here
+    if (!d_staging) return fail(MERF_ERR_INVALID_ARG, "d_staging is NULL and h_out is not page-locked");
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return fail(MERF_ERR_UNSUPPORTED, "device ordinal %d", dev);
-    cudaStream_t s = (cudaStream_t)stream;
     const size_t per = (size_t)W * H * 3;
-    // Camera c renders on the caller's stream while camera c-1's image streams to the host on a
-    // second stream, so the device-to-host copies hide behind the rendering.
     std::lock_guard<std::mutex> lk(g_host_copy_mu);
     HostCopy &hc = g_host_copy[dev];
     cudaError_t e = cudaSuccess;
@@ -432,6 +443,8 @@ merf_status merf_render_host(const merf_scene *scene, const merf_camera *cams, i
         if (e == cudaSuccess) hc.events.push_back(ev);
     }
     if (e != cudaSuccess) return fail(MERF_ERR_CUDA, "render_host resources: %s", cudaGetErrorString(e));
+    // Otherwise camera c renders on the caller's stream into d_staging while camera c-1's image
+    // is copied to the host on a second stream, so the copies hide behind the rendering.
     for (int c = 0; c < n_cams; ++c) {
         if ((st = launch_render(scene, cams + c, 1, W, H, d_staging + c * per, nullptr, nullptr, opts, s))) return st;
         e = cudaEventRecord(hc.events[c], s);

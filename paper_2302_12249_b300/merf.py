@@ -216,10 +216,11 @@ def render(scene: Scene, cams: np.ndarray, W: int, H: int, step: float, out: Opt
     return out
 
 
-def render_host(scene: Scene, cams: np.ndarray, W: int, H: int, step: float, staging: torch.Tensor,
+def render_host(scene: Scene, cams: np.ndarray, W: int, H: int, step: float, staging: Optional[torch.Tensor],
                 host_out: torch.Tensor, t_term: float = 2e-4, early_term: bool = True,
                 precision: int = PREC_FP32, stream=None) -> torch.Tensor:
-    """Render into host memory through the library's host-output entry point."""
+    """Render into host memory through the library's host-output entry point (`staging` may be
+    None when host_out is page-locked: the kernel then writes it directly)."""
     cams = cameras(cams)
     n = cams.shape[0]
     if host_out.is_cuda or host_out.dtype != torch.float32 or not host_out.is_contiguous() or \
@@ -227,7 +228,8 @@ def render_host(scene: Scene, cams: np.ndarray, W: int, H: int, step: float, sta
         raise ValueError("host_out must be a contiguous host float32 tensor [n, H, W, 3]")
     o = opts(step, t_term, early_term, precision)
     _check(lib().merf_render_host(scene.handle, _np_ptr(cams), n, W, H,
-                                  _dev_ptr(staging, torch.float32, n * H * W * 3, "staging"),
+                                  None if staging is None else _dev_ptr(staging, torch.float32, n * H * W * 3,
+                                                                        "staging"),
                                   ct.c_void_p(host_out.data_ptr()), ct.byref(o), _stream(stream)))
     return host_out
 

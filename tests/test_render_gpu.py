@@ -134,13 +134,19 @@ def test_deterministic(tiny):
 
 
 def test_render_host_matches_device(tiny):
+    """Page-locked output (written by the kernel directly, no staging) and pageable output
+    (staged per camera and copied) both equal the device render."""
     gs, _ = tiny
-    cams = synth.config_cameras("tiny")
-    dev = merf.render(gs, cams, 64, 64, 1 / 64)
-    staging = torch.empty_like(dev)
-    host = torch.empty(dev.shape, dtype=torch.float32, pin_memory=True)
-    merf.render_host(gs, cams, 64, 64, 1 / 64, staging, host)
-    assert torch.equal(host, dev.cpu())
+    cams = synth.sphere_cameras(3, 50, 37, radius=2.8, seed=12)
+    dev = merf.render(gs, cams, 50, 37, 1 / 64)
+    pinned = torch.full(dev.shape, -1.0, dtype=torch.float32, pin_memory=True)
+    merf.render_host(gs, cams, 50, 37, 1 / 64, None, pinned)
+    assert torch.equal(pinned, dev.cpu())
+    pageable = torch.full(dev.shape, -1.0, dtype=torch.float32)
+    merf.render_host(gs, cams, 50, 37, 1 / 64, torch.empty_like(dev), pageable)
+    assert torch.equal(pageable, dev.cpu())
+    with pytest.raises(merf.MerfError):
+        merf.render_host(gs, cams, 50, 37, 1 / 64, None, torch.empty(dev.shape, dtype=torch.float32))
 
 
 def test_counters_match_aux(tiny):
