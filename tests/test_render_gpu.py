@@ -96,6 +96,27 @@ def test_camera_inside_unit_cube_and_axis_aligned(tiny):
     np.testing.assert_array_equal(mask.cpu().numpy().view(np.uint32), m_o)
 
 
+def test_unusual_geometry_and_far_cameras():
+    """Run-time gather geometry off the usual sizes (L = 96 in 32^3 blocks, R = 200 planes, two
+    occupancy levels 32^3 / 8^3) and cameras far outside the scene (world distance 10 to 1000),
+    whose rays start near the edge of contracted space."""
+    cfg = synth.SceneConfig("odd", L=96, B=32, R=200, occ_res=(32, 8), n_blobs=24, inner_blobs=None,
+                            step=1.0 / 64, peak_opacity=3.0)
+    sc = synth.make_scene(cfg, seed=1234)
+    gs, osc = merf.Scene(sc), oracle.OracleScene(sc)
+    recs = [synth.camera_record(synth.look_at(np.array(e, float), (0, 0, 0)), 23, 17)
+            for e in [(10.0, 0.3, 0.2), (-40.0, 25.0, 8.0), (0.5, -1000.0, 3.0), (2.2, 1.9, -1.7)]]
+    cams = np.stack(recs)
+    rgb, aux = parity.gpu_render(gs, cams, 23, 17, cfg.step)
+    lo, hi = parity.oracle_rgb(osc, cams, 23, 17, cfg.step)
+    assert parity.max_err(rgb, lo, hi).max() <= parity.RGB_TOL
+    words = _words(aux[:, merf.AUX_NLAT])
+    mask, nlat = merf.trace(gs, cams, 23, 17, cfg.step, words=words)
+    m_o, _, n_o = oracle.trace(osc, cams, 23, 17, cfg.step, words=words, decide_f32=True)
+    np.testing.assert_array_equal(nlat.cpu().numpy(), n_o)
+    np.testing.assert_array_equal(mask.cpu().numpy().view(np.uint32), m_o)
+
+
 def test_empty_and_full_occupancy():
     """No occupied cell: C = h(0, 0, d).  Every cell occupied: nothing is skipped."""
     for occ_val in (0, 1):
