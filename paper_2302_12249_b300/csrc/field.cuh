@@ -380,18 +380,22 @@ __device__ __forceinline__ void field_f32(const FieldView &fv, float p0, float p
     texel_coord(p0, sL, hL, L, x0, fx);
     texel_coord(p1, sL, hL, L, y0, fy);
     texel_coord(p2, sL, hL, L, z0, fz);
+    // eight channels as four packed FP32 pairs (each lane rounds as the scalar fmaf does)
+    float2 acc[4];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) out[c] = 0.0f;
+    for (int j = 0; j < 4; ++j) acc[j] = make_float2(0.0f, 0.0f);
+    const float4 *g0 = fv.grid_f32 + (((size_t)z0 * L + y0) * L + x0) * 2;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
         const float w = (cx ? fx : 1.0f - fx) * (cy ? fy : 1.0f - fy) * (cz ? fz : 1.0f - fz);
-        const float4 *q = fv.grid_f32 + (((size_t)(z0 + cz) * L + (y0 + cy)) * L + (x0 + cx)) * 2;
+        const float4 *q = g0 + ((size_t)(cz * L + cy) * L + cx) * 2;
         const float4 a = __ldg(q), b = __ldg(q + 1);
-        out[0] = fmaf(w, a.x, out[0]); out[1] = fmaf(w, a.y, out[1]);
-        out[2] = fmaf(w, a.z, out[2]); out[3] = fmaf(w, a.w, out[3]);
-        out[4] = fmaf(w, b.x, out[4]); out[5] = fmaf(w, b.y, out[5]);
-        out[6] = fmaf(w, b.z, out[6]); out[7] = fmaf(w, b.w, out[7]);
+        const float2 ww = make_float2(w, w);
+        acc[0] = __ffma2_rn(ww, make_float2(a.x, a.y), acc[0]);
+        acc[1] = __ffma2_rn(ww, make_float2(a.z, a.w), acc[1]);
+        acc[2] = __ffma2_rn(ww, make_float2(b.x, b.y), acc[2]);
+        acc[3] = __ffma2_rn(ww, make_float2(b.z, b.w), acc[3]);
     }
     const float sR = (float)fv.R * 0.25f;
     const int hR = fv.R >> 1, R = fv.R;
@@ -403,17 +407,24 @@ __device__ __forceinline__ void field_f32(const FieldView &fv, float p0, float p
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         const int ca = q == 0 ? 1 : 0, ra = q == 2 ? 1 : 2;
+        const float4 *t0 = fv.planes_f32 + (((size_t)q * R + u0[ra]) * R + u0[ca]) * 2;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int cu = c & 1, cv = c >> 1;
             const float w = (cu ? fu[ca] : 1.0f - fu[ca]) * (cv ? fu[ra] : 1.0f - fu[ra]);
-            const float4 *t = fv.planes_f32 + (((size_t)q * R + u0[ra] + cv) * R + u0[ca] + cu) * 2;
+            const float4 *t = t0 + ((size_t)cv * R + cu) * 2;
             const float4 a = __ldg(t), b = __ldg(t + 1);
-            out[0] = fmaf(w, a.x, out[0]); out[1] = fmaf(w, a.y, out[1]);
-            out[2] = fmaf(w, a.z, out[2]); out[3] = fmaf(w, a.w, out[3]);
-            out[4] = fmaf(w, b.x, out[4]); out[5] = fmaf(w, b.y, out[5]);
-            out[6] = fmaf(w, b.z, out[6]); out[7] = fmaf(w, b.w, out[7]);
+            const float2 ww = make_float2(w, w);
+            acc[0] = __ffma2_rn(ww, make_float2(a.x, a.y), acc[0]);
+            acc[1] = __ffma2_rn(ww, make_float2(a.z, a.w), acc[1]);
+            acc[2] = __ffma2_rn(ww, make_float2(b.x, b.y), acc[2]);
+            acc[3] = __ffma2_rn(ww, make_float2(b.z, b.w), acc[3]);
         }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        out[2 * j] = acc[j].x;
+        out[2 * j + 1] = acc[j].y;
     }
 }
 

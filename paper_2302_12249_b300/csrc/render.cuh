@@ -528,10 +528,11 @@ __device__ __forceinline__ void deferred_mlp(MlpSmem<kPrec> &ms, const RayState 
     }
 }
 
-// Resident CTAs per SM the register allocation is bounded for (measured on the 8 x 1080p
-// paper-scale workload: the uint8 kernels are fastest at 6, i.e. 80 registers per thread).
+// Resident CTAs per SM the register allocation is bounded for (measured: the uint8 kernels on
+// the 8 x 1080p paper-scale workload and the dense float kernel on 4 x 512^2 are fastest at 6,
+// i.e. 80 registers per thread).
 template <int kStorage, int kPrec>
-constexpr int kMinBlocks = kStorage != 0 ? 4 : 6;
+constexpr int kMinBlocks = 6;
 
 template <int kStorage, int kPrec, int kGeo, int kSph = 0>
 // storage 0: uint8 block-sparse, 1: float32 dense; precision 0: FP32, 1: FP16, 2: BF16 (uint8
