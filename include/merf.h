@@ -204,6 +204,14 @@ merf_status merf_render_backward(const merf_scene *scene, const merf_camera *cam
                                  const float *d_out, float *g_grid, float *g_planes, float *g_mlp,
                                  const merf_render_opts *opts, void *stream);
 
+/* merf_render_backward without the recomputed forward march: `aux` is the per-pixel record
+ * (device float32 [n_cams][H][W][MERF_AUX_SIZE]) that merf_render_aux wrote for the same scene
+ * parameters, cameras and options; its C_d and F stand in for the first march.  NULL: as
+ * merf_render_backward.  The paper has no counterpart (it trains through other means). */
+merf_status merf_render_backward_aux(const merf_scene *scene, const merf_camera *cams, int n_cams, int W, int H,
+                                     const float *d_out, const float *aux, float *g_grid, float *g_planes,
+                                     float *g_mlp, const merf_render_opts *opts, void *stream);
+
 /* ----------------------------------------------------------------------------------------
  * Serving: a render server holding several resident scenes and batching requests of mixed
  * scenes and resolutions continuously.  The paper renders one view at a time in a browser; this

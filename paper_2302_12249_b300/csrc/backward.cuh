@@ -1,8 +1,8 @@
 // backward.cuh -- hand-written adjoint of the renderer for dense float scenes (sm_103a).
 //
 // For L with dL/dC given per pixel, one thread per ray:
-//   1. recompute the forward march (same arithmetic, hence the same samples, opacities and
-//      termination) to get C_d, F;
+//   1. take C_d, F from the forward pass's per-pixel record, or recompute the forward march
+//      (same arithmetic, hence the same samples, opacities and termination);
 //   2. run the deferred MLP forward and backward in FP32: dL/dC_d = dL/dC + (dh/dC_d)^T dL/dC,
 //      dL/dF = (dh/dF)^T dL/dC, and the weight gradients, summed over the warp's pixels as small
 //      matrix products in shared memory and accumulated per CTA;
@@ -27,6 +27,7 @@ struct BackwardParams {
     OccView occ;
     const float *mlp;
     const float *d_out;     // [n][H][W][3] dL/dC
+    const float *aux;       // forward's [n][H][W][kAuxSize] (C_d, F, ...) or null: march again
     float *g_grid;          // [L][L][L][8]
     float *g_planes;        // [3][R][R][8]
     float *g_mlp;           // [883]
@@ -247,7 +248,15 @@ static __global__ void __launch_bounds__(kThreads, 4) backward_kernel(const __gr
         gC[0] = P.d_out[pix * 3 + 0];
         gC[1] = P.d_out[pix * 3 + 1];
         gC[2] = P.d_out[pix * 3 + 2];
-        march_ray<1, 0>(P.fv, P.occ, cam, i, j, P.step, P.t_term, P.early_term, r);
+        if (P.aux) {   // C_d and F as the forward pass composited them
+            const float *a = P.aux + pix * kAuxSize;
+            r.cd[0] = a[0]; r.cd[1] = a[1]; r.cd[2] = a[2];
+            r.F[0] = a[3]; r.F[1] = a[4]; r.F[2] = a[5]; r.F[3] = a[6];
+            float o[3];
+            ray_f32(cam, i, j, o, r.d);
+        } else {
+            march_ray<1, 0>(P.fv, P.occ, cam, i, j, P.step, P.t_term, P.early_term, r);
+        }
     }
     // the whole warp: MLP backward per lane, weight gradients reduced across the warp
     float gx7[7];

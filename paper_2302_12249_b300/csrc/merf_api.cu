@@ -554,6 +554,14 @@ merf_status merf_render_backward(const merf_scene *scene, const merf_camera *cam
                                  const float *d_out, float *g_grid, float *g_planes, float *g_mlp,
                                  const merf_render_opts *opts, void *stream)
 {
+    return merf_render_backward_aux(scene, cams, n_cams, W, H, d_out, nullptr, g_grid, g_planes, g_mlp, opts,
+                                    stream);
+}
+
+merf_status merf_render_backward_aux(const merf_scene *scene, const merf_camera *cams, int n_cams, int W, int H,
+                                     const float *d_out, const float *aux, float *g_grid, float *g_planes,
+                                     float *g_mlp, const merf_render_opts *opts, void *stream)
+{
     merf_status st = check_frame(scene, cams, n_cams, W, H);
     if (st) return st;
     if ((st = check_opts(opts))) return st;
@@ -569,6 +577,7 @@ merf_status merf_render_backward(const merf_scene *scene, const merf_camera *cam
     P.occ = R.occ;
     P.mlp = R.mlp;
     P.d_out = d_out;
+    P.aux = aux;
     P.g_grid = g_grid;
     P.g_planes = g_planes;
     P.g_mlp = g_mlp;

@@ -26,7 +26,7 @@ CNT_RAYS, CNT_LATTICE, CNT_EVAL, CNT_APPEAR = 0, 1, 2, 3
 
 EXPORTS = ("merf_scene_upload", "merf_scene_upload_dense", "merf_scene_free", "merf_scene_device_bytes",
            "merf_render", "merf_render_aux", "merf_render_host", "merf_render_host_noalloc", "merf_trace",
-           "merf_set_device_budget", "merf_scene_set_dense", "merf_render_backward", "merf_server_create", "merf_server_submit", "merf_server_wait",
+           "merf_set_device_budget", "merf_scene_set_dense", "merf_render_backward", "merf_render_backward_aux", "merf_server_create", "merf_server_submit", "merf_server_wait",
            "merf_server_get_stats", "merf_server_destroy",
            "merf_last_error", "merf_version")
 
@@ -85,6 +85,8 @@ def lib():
         L.merf_set_device_budget.restype = None
         L.merf_scene_set_dense.argtypes = [vp, vp, vp, vp, vp]
         L.merf_render_backward.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp, ct.POINTER(Opts), vp]
+        L.merf_render_backward_aux.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp, vp, ct.POINTER(Opts), vp]
+        L.merf_render_backward_aux.restype = ct.c_int
         L.merf_scene_set_dense.restype = ct.c_int
         L.merf_render_backward.restype = ct.c_int
         L.merf_server_create.argtypes = [vp, i32, ct.POINTER(ServerOpts), ct.POINTER(vp)]
@@ -273,24 +275,31 @@ def set_dense(scene: Scene, grid: torch.Tensor, planes: torch.Tensor, mlp: torch
 
 def render_backward(scene: Scene, cams: np.ndarray, W: int, H: int, step: float, d_out: torch.Tensor,
                     g_grid: torch.Tensor, g_planes: torch.Tensor, g_mlp: torch.Tensor, t_term: float = 2e-4,
-                    early_term: bool = True, stream=None):
-    """Accumulate dL/dgrid, dL/dplanes, dL/dmlp (zeroed by the caller) for dL/dC = d_out."""
+                    early_term: bool = True, stream=None, aux: Optional[torch.Tensor] = None):
+    """Accumulate dL/dgrid, dL/dplanes, dL/dmlp (zeroed by the caller) for dL/dC = d_out.  `aux`:
+    the forward render's per-pixel record (render(..., aux=...)), which saves the recomputed march."""
     cams = cameras(cams)
     n = cams.shape[0]
     L, R = scene.desc.grid_res, scene.desc.plane_res
     o = opts(step, t_term, early_term, PREC_FP32)
-    _check(lib().merf_render_backward(scene.handle, _np_ptr(cams), n, W, H,
-                                      _dev_ptr(d_out, torch.float32, n * H * W * 3, "d_out"),
-                                      _dev_ptr(g_grid, torch.float32, L ** 3 * 8, "g_grid"),
-                                      _dev_ptr(g_planes, torch.float32, 3 * R * R * 8, "g_planes"),
-                                      _dev_ptr(g_mlp, torch.float32, 883, "g_mlp"), ct.byref(o), _stream(stream)))
+    _check(lib().merf_render_backward_aux(scene.handle, _np_ptr(cams), n, W, H,
+                                          _dev_ptr(d_out, torch.float32, n * H * W * 3, "d_out"),
+                                          None if aux is None else _dev_ptr(aux, torch.float32,
+                                                                            n * H * W * AUX_SIZE, "aux"),
+                                          _dev_ptr(g_grid, torch.float32, L ** 3 * 8, "g_grid"),
+                                          _dev_ptr(g_planes, torch.float32, 3 * R * R * 8, "g_planes"),
+                                          _dev_ptr(g_mlp, torch.float32, 883, "g_mlp"), ct.byref(o),
+                                          _stream(stream)))
 
 
 class _RenderFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, grid, planes, mlp, scene, cams, W, H, step, t_term, early_term):
         set_dense(scene, grid.detach(), planes.detach(), mlp.detach())
-        out = render(scene, cams, W, H, step, t_term=t_term, early_term=early_term)
+        n = cams.shape[0]
+        aux = torch.empty((n, H, W, AUX_SIZE), dtype=torch.float32, device="cuda")
+        out = render(scene, cams, W, H, step, t_term=t_term, early_term=early_term, aux=aux)
+        ctx.aux = aux        # C_d and F per pixel: the adjoint needs no second forward march
         ctx.scene, ctx.cams, ctx.args = scene, cams, (W, H, step, t_term, early_term)
         ctx.shapes = (grid.shape, planes.shape, mlp.shape)
         return out
@@ -303,7 +312,8 @@ class _RenderFn(torch.autograd.Function):
         g_planes = torch.zeros(ps, dtype=torch.float32, device="cuda")
         g_mlp = torch.zeros(ms, dtype=torch.float32, device="cuda")
         render_backward(ctx.scene, ctx.cams, W, H, step, g_out.contiguous(), g_grid, g_planes, g_mlp, t_term,
-                        early_term)
+                        early_term, aux=ctx.aux)
+        ctx.aux = None
         return g_grid, g_planes, g_mlp, None, None, None, None, None, None, None
 
 
