@@ -46,7 +46,7 @@ B_DENSITY, B_INDEX, B_APPEAR, B_OUT = 20, 4, 140, 12
 # measured with (otherwise null).
 TRAFFIC_BYTES_PER_LAUNCH = (402.82 + 617.59) * 1e6
 TRAFFIC_SOURCES = ("field.cuh", "merf_api.cu", "render.cuh", "scene.h", "traverse.cuh")
-TRAFFIC_SOURCES_SHA256 = "e179e85735d85ef7a0612f36027c47209676f1fbf6327cd33eff9be313953395"
+TRAFFIC_SOURCES_SHA256 = "e01221ae11217f62866debca90db2e985218760374fa3d4109b5bba074891af1"
 
 
 def _sources_sha256() -> str:

@@ -7,7 +7,8 @@
 // byte values and dequantises the sum once per channel:
 //     t~_c = (2 m_c / 255) * sum_w w k_c  -  m_c * (W_V + 3),
 // with W_V the weight of the 3D-grid corners that are stored (a voxel of a block that is not
-// stored contributes nothing).
+// stored contributes nothing).  A grid-only scene (no planes, R = 0: the SNeRG++-style baseline
+// of Sec. 6) has t~ = V and the offset m_c W_V.
 //
 // Layout in HBM.  Every texel is 8 bytes (one uint2: channels 0..3 in .x, 4..7 in .y), so a
 // single 64-bit load fetches density and appearance of a corner.  The 3D grid is
@@ -17,8 +18,10 @@
 // that is not stored.  Each atlas slot holds (B+1)^3 voxels [z][y][x]: the block plus a
 // one-voxel apron copied from its +x/+y/+z neighbours, so the eight corners of any sample
 // whose lowest corner lies in the block are one base address plus constant offsets.
-// Clamp-to-edge is folded into the integer coordinate and weight (lowest corner kept in
-// [0, N-2]), so no lookup leaves the array.
+// For the 3D grid, clamp-to-edge is folded into the integer coordinate and weight (lowest corner
+// kept in [0, N-2]), so no lookup leaves the array.  The planes are stored [3][R+2][R+2] with a
+// one-texel border that repeats their edge texels, so their taps need no clamp.  The occupancy
+// grids are not read here (the traversal tests them before a sample is evaluated).
 #pragma once
 
 #include <cuda_bf16.h>

@@ -5,10 +5,13 @@
 // texels of each evaluated sample, all eight channels interpolated in one tap-major pass (the
 // appearance values enter the result only when the sample's opacity is non-zero, Sec. 5),
 // front-to-back compositing of C_d and F with early termination (Eq. 1, Eq. 2, Sec. 5), and
-// finally the deferred MLP h(C_d, F, d) (Sec. 2, App. B), whose
-// 883 weights are staged once per CTA in shared memory and read as warp-wide broadcasts.
-// A warp covers an 8 x 4 pixel tile and a CTA a 16 x 8 tile, so neighbouring rays walk
-// neighbouring texels together and share L1 lines.
+// finally the deferred MLP h(C_d, F, d) (Sec. 2, App. B), whose 883 weights are staged once per
+// CTA in shared memory (FP32: per pixel on the CUDA cores; FP16 / BF16: per warp on the tensor
+// cores).  A warp covers an 8 x 4 pixel tile and a CTA a 16 x 8 tile, so neighbouring rays walk
+// neighbouring texels together and share L1 lines.  Template parameters select the storage
+// (uint8 block-sparse / dense float), the precision (FP32 / FP16 / BF16 appearance arithmetic
+// and MLP), the gather geometry (the paper's / grid-only / run-time strides) and the contraction
+// (contract_pi, or the spherical ablation's dense march).
 #pragma once
 
 #include "field.cuh"
