@@ -470,7 +470,8 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD + "; each step renders 4096 random pixel rays of it",
+            "config": {"workload": WORKLOAD.replace("FP32 path", "FP64 oracle") +
+                                   "; each step renders 4096 random pixel rays of it",
                        "parallelism": "host threads"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"{per_step} random pixel rays per step, FP64 oracle, {threads} threads"},
