@@ -1,7 +1,8 @@
 """FP64 CPU oracle of the MERF real-time renderer -- TEST INFRASTRUCTURE ONLY.
 
-Only tests, ``__graft_entry__.smoke()`` and the CPU-baseline / reference legs of
-``bench.py`` may import this package.  The product path (the CUDA library and its
+Only tests, ``__graft_entry__.smoke()`` and ``bench.py``'s oracle leg (its CPU
+baseline, the reference values the precision form is scored against, the footprint
+count) and reference arm may import this package.  The product path (the CUDA library and its
 binding) never imports, links or executes anything here, and this package imports
 nothing from the product.
 

@@ -1,7 +1,7 @@
 /* merf_oracle.c -- plain FP64 CPU oracle of the MERF real-time renderer.
  *
- * TEST INFRASTRUCTURE ONLY: only tests, the smoke check and the benchmark's CPU-baseline
- * leg may build, load or call this file.  The product (the CUDA library) never does.
+ * TEST INFRASTRUCTURE ONLY: only tests, the smoke check and the benchmark's oracle leg and
+ * reference arm may build, load or call this file.  The product (the CUDA library) never does.
  *
  * It computes, per pixel ray and with no empty-space hierarchy and no other acceleration,
  * exactly what the paper defines:

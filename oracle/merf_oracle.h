@@ -1,8 +1,9 @@
 /* merf_oracle.h -- plain FP64 CPU oracle of the MERF real-time renderer.
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link or call this
- * code: it exists so that tests, the smoke check and the benchmark's CPU baseline can
- * check the CUDA renderer against a slow, obviously correct restatement of the paper.
+ * code: it exists so that tests, the smoke check and the benchmark's oracle leg (CPU
+ * baseline, precision-form reference values, footprint) and reference arm can check and
+ * time the CUDA renderer against a slow, obviously correct restatement of the paper.
  * It shares no code, header, table or constant generator with the CUDA library.
  *
  * Sections cited are those of "MERF: Memory-Efficient Radiance Fields for Real-time View
