@@ -46,6 +46,11 @@ B_DENSITY, B_INDEX, B_APPEAR, B_OUT = 20, 4, 140, 12
 # measured with (otherwise null).
 TRAFFIC_BYTES_PER_LAUNCH = (402.82 + 617.59) * 1e6
 TRAFFIC_SOURCES = ("field.cuh", "merf_api.cu", "render.cuh", "scene.h", "traverse.cuh")
+# Warp-level instructions (smsp__inst_executed.sum) of the same timed launch from an ncu capture
+# (1 pass, full size), for the issue-rate roofline: the kernel is bound by instruction issue, and
+# an SM's four schedulers issue at most one warp instruction per clock each.
+INST_PER_LAUNCH = 44.191268013e9
+SMS, SCHEDULERS_PER_SM = 148, 4
 TRAFFIC_SOURCES_SHA256 = "e01221ae11217f62866debca90db2e985218760374fa3d4109b5bba074891af1"
 
 
@@ -605,6 +610,13 @@ def run_ours(args):
                 "e2e": e2e, "clocks": ck}
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        if (line["roofline"]["traffic"] is not None and ck and ck.get("sm_mhz")):
+            issue = INST_PER_LAUNCH / (mean_kern_ms / 1e3) / 1e9
+            peak_issue = SMS * SCHEDULERS_PER_SM * ck["sm_mhz"] / 1e3
+            line["roofline_issue"] = {"bound": "issue", "achieved": issue, "peak": peak_issue, "unit": "Ginst/s",
+                                      "frac": issue / peak_issue, "inst_per_launch": INST_PER_LAUNCH,
+                                      "peak_from": f"{SMS} SMs x {SCHEDULERS_PER_SM} schedulers x 1 warp "
+                                                   f"instruction per clock at the sampled {ck['sm_mhz']:.0f} MHz"}
         if footprint is not None:
             line["footprint_1080p_frame"] = dict(
                 footprint, algorithmic_bytes=alg_bytes / n_cams,
