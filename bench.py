@@ -44,14 +44,14 @@ B_DENSITY, B_INDEX, B_APPEAR, B_OUT = 20, 4, 140, 12
 # launch from an ncu capture of this workload; reported as roofline.traffic only while the
 # render kernel's sources (device code, launch and scene layout) hash to the value they were
 # measured with (otherwise null).
-TRAFFIC_BYTES_PER_LAUNCH = (402.82 + 617.59) * 1e6
+TRAFFIC_BYTES_PER_LAUNCH = (401.84 + 617.93) * 1e6
 TRAFFIC_SOURCES = ("field.cuh", "merf_api.cu", "render.cuh", "scene.h", "traverse.cuh")
 # Warp-level instructions (smsp__inst_executed.sum) of the same timed launch from an ncu capture
 # (1 pass, full size), for the issue-rate roofline: the kernel is bound by instruction issue, and
 # an SM's four schedulers issue at most one warp instruction per clock each.
-INST_PER_LAUNCH = 44.191268013e9
+INST_PER_LAUNCH = 44.122176210e9
 SMS, SCHEDULERS_PER_SM = 148, 4
-TRAFFIC_SOURCES_SHA256 = "e01221ae11217f62866debca90db2e985218760374fa3d4109b5bba074891af1"
+TRAFFIC_SOURCES_SHA256 = "5437e6f18ad7634b6136193efffac4e04ff807d68f7bea172dc3db61fb23eee6"
 
 
 def _sources_sha256() -> str:

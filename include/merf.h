@@ -272,6 +272,16 @@ void merf_server_destroy(merf_server *srv);
 /* Device-memory budget for merf_scene_upload* (bytes; 0 = unlimited, the default). */
 void merf_set_device_budget(size_t bytes);
 
+/* Synchronise `stream` and report the device status word.  In the bounds-checked build
+ * (libmerf_debug.so, compiled with MERF_DEBUG_BOUNDS) every kernel checks each data-dependent
+ * index into the index grid, atlas, planes, occupancy levels and dense arrays; an index out of
+ * range is skipped (the texel reads as zero, the cell as empty) and recorded, never trapped.
+ * Returns MERF_ERR_DEVICE_BOUNDS (merf_last_error names what was out of range) if anything was
+ * recorded since the last call, and clears the word.  self_test != 0 (bounds-checked build only,
+ * else MERF_ERR_UNSUPPORTED) first records a self-test bit from a one-thread kernel, to exercise
+ * the reporting path.  In the release build the word is never set. */
+merf_status merf_check_device(void *stream, int self_test);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *merf_last_error(void);
 

@@ -58,7 +58,8 @@ __device__ __forceinline__ void scatter_f32(const FieldView &fv, float *g_grid, 
     for (int c = 0; c < 8; ++c) {
         const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
         const float w = (cx ? fx : 1.0f - fx) * (cy ? fy : 1.0f - fy) * (cz ? fz : 1.0f - fz);
-        if (w != 0.0f) atomic_add8(g_grid + (((size_t)(z0 + cz) * L + (y0 + cy)) * L + (x0 + cx)) * 8, g, w);
+        const size_t gi = ((size_t)(z0 + cz) * L + (y0 + cy)) * L + (x0 + cx);
+        if (w != 0.0f && MERF_IN_RANGE(gi, (long long)L * L * L, kBadDense)) atomic_add8(g_grid + gi * 8, g, w);
     }
     const float sR = (float)fv.R * 0.25f;
     const int hR = fv.R >> 1, R = fv.R;
@@ -74,7 +75,8 @@ __device__ __forceinline__ void scatter_f32(const FieldView &fv, float *g_grid, 
         for (int c = 0; c < 4; ++c) {
             const int cu = c & 1, cv = c >> 1;
             const float w = (cu ? fu[ca] : 1.0f - fu[ca]) * (cv ? fu[ra] : 1.0f - fu[ra]);
-            if (w != 0.0f) atomic_add8(g_planes + (((size_t)q * R + u0[ra] + cv) * R + u0[ca] + cu) * 8, g, w);
+            const size_t pi = ((size_t)q * R + u0[ra] + cv) * R + u0[ca] + cu;
+            if (w != 0.0f && MERF_IN_RANGE(pi, 3LL * R * R, kBadDense)) atomic_add8(g_planes + pi * 8, g, w);
         }
     }
 }

@@ -29,6 +29,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "debug.cuh"
+
 namespace merf {
 
 struct FieldView {
@@ -38,6 +40,7 @@ struct FieldView {
     const float4 *grid_f32;      // dense storage: [L][L][L][2]
     const float4 *planes_f32;    // dense storage: [3][R][R][2]
     int L, B, log2B, nb, R;
+    int n_blocks;                // stored blocks (atlas slots)
 };
 
 // Lowest corner i0 and weight f of the upper corner for the continuous texel index
@@ -123,10 +126,12 @@ __device__ __forceinline__ void gather_grid_slow(const FieldView &fv, int x0, in
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         const int x = x0 + (c & 1), y = y0 + ((c >> 1) & 1), z = z0 + (c >> 2);
-        const int ent = __ldg(fv.index_grid + ((z >> sh) * nb + (y >> sh)) * nb + (x >> sh));
-        if (ent >= 0) {
-            const size_t slot = (size_t)(ent & 0xffffff);
-            t.v[c] = __ldg(fv.atlas + ((slot * B1 + (z & msk)) * B1 + (y & msk)) * B1 + (x & msk));
+        const int gi = ((z >> sh) * nb + (y >> sh)) * nb + (x >> sh);
+        const int ent = MERF_IN_RANGE(gi, nb * nb * nb, kBadIndexGrid) ? __ldg(fv.index_grid + gi) : -1;
+        const size_t slot = (size_t)(ent & 0xffffff);
+        const size_t ai = ((slot * B1 + (z & msk)) * B1 + (y & msk)) * B1 + (x & msk);
+        if (ent >= 0 && MERF_IN_RANGE(ai, (long long)fv.n_blocks * B1 * B1 * B1, kBadAtlas)) {
+            t.v[c] = __ldg(fv.atlas + ai);
             gmask |= 1u << c;
         } else {
             t.v[c] = make_uint2(0u, 0u);
@@ -160,10 +165,19 @@ __device__ __forceinline__ void gather_u8(const FieldView &fv, float p0, float p
     texel_coord(p1, sL, hL, L, y0, t.fy);
     texel_coord(p2, sL, hL, L, z0, t.fz);
     const int msk = (1 << sh) - 1, B1 = (1 << sh) + 1;
-    const int ent = __ldg(fv.index_grid + ((z0 >> sh) * nb + (y0 >> sh)) * nb + (x0 >> sh));
+    const int gi = ((z0 >> sh) * nb + (y0 >> sh)) * nb + (x0 >> sh);
+    const int ent = MERF_IN_RANGE(gi, nb * nb * nb, kBadIndexGrid) ? __ldg(fv.index_grid + gi) : -1;
     if (ent >= 0) {
         const int lx = x0 & msk, ly = y0 & msk, lz = z0 & msk;
-        const uint2 *base = fv.atlas + ((size_t)(ent & 0xffffff) * B1 + lz) * B1 * B1 + ly * B1 + lx;
+        const size_t ai = ((size_t)(ent & 0xffffff) * B1 + lz) * B1 * B1 + ly * B1 + lx;
+        // bounds-checked build: the farthest corner is ai + B1^2 + B1 + 1
+        if (!MERF_IN_RANGE(ai + B1 * B1 + B1 + 1, (long long)fv.n_blocks * B1 * B1 * B1, kBadAtlas)) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) t.v[c] = make_uint2(0u, 0u);
+            t.wv = 0.0f;
+            goto grid_done;
+        }
+        const uint2 *base = fv.atlas + ai;
         const int sy = B1, sz = B1 * B1;
         t.v[0] = __ldg(base);
         t.v[1] = __ldg(base + 1);
@@ -189,6 +203,7 @@ __device__ __forceinline__ void gather_u8(const FieldView &fv, float p0, float p
     } else {
         gather_grid_slow(fv, x0, y0, z0, t);
     }
+grid_done:;
     if constexpr (kGeo == kGeoGridOnly) return;
     const float sR = (float)Rg * 0.25f;
     const int hR = Rg >> 1, R = Rg, Rp = Rg + 2;
@@ -200,7 +215,12 @@ __device__ __forceinline__ void gather_u8(const FieldView &fv, float p0, float p
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         const int ca = q == 0 ? 1 : 0, ra = q == 2 ? 1 : 2;
-        const uint2 *base = fv.planes + ((size_t)q * Rp + u0[ra]) * Rp + u0[ca];
+        const size_t pi = ((size_t)q * Rp + u0[ra]) * Rp + u0[ca];
+        if (!MERF_IN_RANGE(pi + Rp + 1, 3LL * Rp * Rp, kBadPlane)) {
+            t.v[8 + 4 * q + 0] = t.v[8 + 4 * q + 1] = t.v[8 + 4 * q + 2] = t.v[8 + 4 * q + 3] = make_uint2(0u, 0u);
+            continue;
+        }
+        const uint2 *base = fv.planes + pi;
         t.v[8 + 4 * q + 0] = __ldg(base);
         t.v[8 + 4 * q + 1] = __ldg(base + 1);
         t.v[8 + 4 * q + 2] = __ldg(base + Rp);
@@ -387,12 +407,15 @@ __device__ __forceinline__ void field_f32(const FieldView &fv, float p0, float p
     float2 acc[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[j] = make_float2(0.0f, 0.0f);
-    const float4 *g0 = fv.grid_f32 + (((size_t)z0 * L + y0) * L + x0) * 2;
+    const size_t gidx = ((size_t)z0 * L + y0) * L + x0;
+    const bool g_ok = MERF_IN_RANGE(gidx + (size_t)L * L + L + 1, (long long)L * L * L, kBadDense);
+    const float4 *g0 = fv.grid_f32 + gidx * 2;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
         const float w = (cx ? fx : 1.0f - fx) * (cy ? fy : 1.0f - fy) * (cz ? fz : 1.0f - fz);
         const float4 *q = g0 + ((size_t)(cz * L + cy) * L + cx) * 2;
+        if (!g_ok) continue;
         const float4 a = __ldg(q), b = __ldg(q + 1);
         const float2 ww = make_float2(w, w);
         acc[0] = __ffma2_rn(ww, make_float2(a.x, a.y), acc[0]);
@@ -410,7 +433,9 @@ __device__ __forceinline__ void field_f32(const FieldView &fv, float p0, float p
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         const int ca = q == 0 ? 1 : 0, ra = q == 2 ? 1 : 2;
-        const float4 *t0 = fv.planes_f32 + (((size_t)q * R + u0[ra]) * R + u0[ca]) * 2;
+        const size_t pidx = ((size_t)q * R + u0[ra]) * R + u0[ca];
+        if (!MERF_IN_RANGE(pidx + R + 1, 3LL * R * R, kBadDense)) continue;
+        const float4 *t0 = fv.planes_f32 + pidx * 2;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int cu = c & 1, cv = c >> 1;

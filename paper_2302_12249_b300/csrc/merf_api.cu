@@ -211,6 +211,10 @@ merf::RenderParams make_params(const merf_scene *s, const merf_render_opts *o, i
     return P;
 }
 
+#ifdef MERF_DEBUG_BOUNDS
+__global__ void status_self_test_kernel() { atomicOr(&merf::g_status, merf::kStatusSelfTest); }
+#endif
+
 template <int kPrec>
 void launch_u8(int geo, dim3 grid, dim3 block, cudaStream_t st, const merf::RenderParams &P)
 {
@@ -603,6 +607,38 @@ void merf_set_device_budget(size_t bytes) { g_budget = bytes; }
 
 const char *merf_last_error(void) { return g_err.c_str(); }
 
+#ifdef MERF_DEBUG_BOUNDS
+const char *merf_version(void) { return "merf-b300 0.1 (sm_103a, bounds-checked build)"; }
+#else
 const char *merf_version(void) { return "merf-b300 0.1 (sm_103a)"; }
+#endif
+
+merf_status merf_check_device(void *stream, int self_test)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+#ifdef MERF_DEBUG_BOUNDS
+    if (self_test) {
+        status_self_test_kernel<<<1, 1, 0, s>>>();
+        if (cudaGetLastError() != cudaSuccess) return fail(MERF_ERR_CUDA, "self-test launch failed");
+    }
+#else
+    if (self_test) return fail(MERF_ERR_UNSUPPORTED, "the status self-test needs the bounds-checked build");
+#endif
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(MERF_ERR_CUDA, "check_device: %s", cudaGetErrorString(e));
+#ifdef MERF_DEBUG_BOUNDS
+    unsigned int word = 0, zero = 0;
+    e = cudaMemcpyFromSymbol(&word, merf::g_status, sizeof word);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(merf::g_status, &zero, sizeof zero);
+    if (e != cudaSuccess) return fail(MERF_ERR_CUDA, "check_device: %s", cudaGetErrorString(e));
+    word |= merf::take_server_status();
+    if (word)
+        return fail(MERF_ERR_DEVICE_BOUNDS, "device status 0x%08x:%s%s%s%s%s%s", word,
+                    (word & merf::kBadIndexGrid) ? " index-grid" : "", (word & merf::kBadAtlas) ? " atlas" : "",
+                    (word & merf::kBadPlane) ? " plane" : "", (word & merf::kBadOcc) ? " occupancy" : "",
+                    (word & merf::kBadDense) ? " dense" : "", (word & merf::kStatusSelfTest) ? " self-test" : "");
+#endif
+    return ok();
+}
 
 }  // extern "C"

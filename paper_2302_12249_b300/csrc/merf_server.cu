@@ -319,6 +319,20 @@ struct merf_server {
     }
 };
 
+namespace merf {
+unsigned int take_server_status()
+{
+#ifdef MERF_DEBUG_BOUNDS
+    unsigned int word = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&word, g_status, sizeof word) != cudaSuccess) return 0;
+    cudaMemcpyToSymbol(g_status, &zero, sizeof zero);
+    return word;
+#else
+    return 0;
+#endif
+}
+}  // namespace merf
+
 namespace {
 
 template <int kPrec, int kGeo>

@@ -475,7 +475,8 @@ __device__ __forceinline__ void march_ray_sph(const FieldView &fv, const OccView
         float p[3];
         sph_point(o, r.d, step, k, p);
         const int c0 = cell_of(p[0], sc0, h0, N0), c1 = cell_of(p[1], sc0, h0, N0), c2 = cell_of(p[2], sc0, h0, N0);
-        if (__ldg(occ.level[0] + ((size_t)c2 * N0 + c1) * N0 + c0) == 0) continue;
+        const size_t oi = ((size_t)c2 * N0 + c1) * N0 + c0;
+        if (!MERF_IN_RANGE(oi, (long long)N0 * N0 * N0, kBadOcc) || __ldg(occ.level[0] + oi) == 0) continue;
         float dens;
         AppArg ya;
         eval_field<kStorage, 0, kGeo>(fv, p[0], p[1], p[2], dens, ya);
@@ -614,7 +615,9 @@ static __global__ void __launch_bounds__(kThreads) trace_kernel(const __grid_con
             sph_point(o, d, P.step, k, p);
             const int c0 = cell_of(p[0], sc0, h0, N0), c1 = cell_of(p[1], sc0, h0, N0),
                       c2 = cell_of(p[2], sc0, h0, N0);
-            if (__ldg(P.occ.level[0] + ((size_t)c2 * N0 + c1) * N0 + c0) != 0) row[k >> 5] |= 1u << (k & 31);
+            const size_t oi = ((size_t)c2 * N0 + c1) * N0 + c0;
+            if (MERF_IN_RANGE(oi, (long long)N0 * N0 * N0, kBadOcc) && __ldg(P.occ.level[0] + oi) != 0)
+                row[k >> 5] |= 1u << (k & 31);
         }
         return;
     }

@@ -35,6 +35,7 @@ inline void scene_views(const merf_scene *s, FieldView &fv, OccView &occ)
         fv.B = d.block_size;
         fv.log2B = log2_int(d.block_size);
         fv.nb = d.grid_res / d.block_size;
+        fv.n_blocks = d.n_blocks;
         fv.index_grid = (const int32_t *)s->index_grid;
         fv.atlas = (const uint2 *)s->atlas;
         fv.planes = (const uint2 *)s->planes;
@@ -65,6 +66,10 @@ inline int gather_geometry(const merf_scene_desc &d)
     if (d.storage == MERF_STORAGE_U8_SPARSE && d.plane_res == 0) return kGeoGridOnly;
     return kGeoRuntime;
 }
+
+// Bounds-checked build: read and clear the server translation unit's device status word (0 in
+// the release build).
+unsigned int take_server_status();
 
 // Thread-local error message of the C ABI (defined in merf_api.cu).
 merf_status set_error(merf_status s, const char *fmt, ...);

@@ -25,6 +25,8 @@
 #include <math_constants.h>
 #include <stdint.h>
 
+#include "debug.cuh"
+
 namespace merf {
 
 constexpr int kMaxSegs = 16;
@@ -377,11 +379,13 @@ struct Walker {
             position(k, p0, p1, p2);
             const int c0 = cell_of(p0, sc0, h0, N0), c1 = cell_of(p1, sc0, h0, N0),
                       c2 = cell_of(p2, sc0, h0, N0);
-            if (__ldg(occ.level[0] + ((size_t)c2 * N0 + c1) * N0 + c0) != 0) return true;
+            const size_t oi = ((size_t)c2 * N0 + c1) * N0 + c0;
+            if (MERF_IN_RANGE(oi, (long long)N0 * N0 * N0, kBadOcc) && __ldg(occ.level[0] + oi) != 0) return true;
             int sh = 0;
             for (int l = occ.n - 1; l > 0; --l) {
                 const int s = occ.shift[l], Nl = occ.res[l];
-                if (__ldg(occ.level[l] + ((size_t)(c2 >> s) * Nl + (c1 >> s)) * Nl + (c0 >> s)) == 0) {
+                const size_t li = ((size_t)(c2 >> s) * Nl + (c1 >> s)) * Nl + (c0 >> s);
+                if (!MERF_IN_RANGE(li, (long long)Nl * Nl * Nl, kBadOcc) || __ldg(occ.level[l] + li) == 0) {
                     sh = s;
                     break;
                 }

@@ -27,7 +27,7 @@ CNT_RAYS, CNT_LATTICE, CNT_EVAL, CNT_APPEAR = 0, 1, 2, 3
 EXPORTS = ("merf_scene_upload", "merf_scene_upload_dense", "merf_scene_free", "merf_scene_device_bytes",
            "merf_render", "merf_render_aux", "merf_render_host", "merf_render_host_noalloc", "merf_trace",
            "merf_set_device_budget", "merf_scene_set_dense", "merf_render_backward", "merf_render_backward_aux", "merf_server_create", "merf_server_submit", "merf_server_wait",
-           "merf_server_get_stats", "merf_server_destroy",
+           "merf_server_get_stats", "merf_server_destroy", "merf_check_device",
            "merf_last_error", "merf_version")
 
 
@@ -61,13 +61,23 @@ class ServerStats(ct.Structure):
 
 
 _lib = None
+_debug = False
+
+
+def use_debug_build():
+    """Load the bounds-checked library (libmerf_debug.so) instead of the release one; call before
+    the first use of the library in this process."""
+    global _debug
+    if _lib is not None:
+        raise RuntimeError("the library is already loaded")
+    _debug = True
 
 
 def lib():
     """Load libmerf.so, building it in-tree with nvcc first if it is missing or stale."""
     global _lib
     if _lib is None:
-        path = _build.build()
+        path = _build.build(debug=True) if _debug else _build.build()
         L = ct.CDLL(path)
         vp, i32 = ct.c_void_p, ct.c_int
         L.merf_scene_upload.argtypes = [ct.POINTER(Desc), vp, vp, vp, vp, vp, vp, ct.POINTER(vp)]
@@ -87,6 +97,8 @@ def lib():
         L.merf_render_backward.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp, ct.POINTER(Opts), vp]
         L.merf_render_backward_aux.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp, vp, ct.POINTER(Opts), vp]
         L.merf_render_backward_aux.restype = ct.c_int
+        L.merf_check_device.argtypes = [vp, i32]
+        L.merf_check_device.restype = ct.c_int
         L.merf_scene_set_dense.restype = ct.c_int
         L.merf_render_backward.restype = ct.c_int
         L.merf_server_create.argtypes = [vp, i32, ct.POINTER(ServerOpts), ct.POINTER(vp)]
@@ -324,6 +336,12 @@ def render_differentiable(scene: Scene, grid: torch.Tensor, planes: torch.Tensor
     the result is differentiable with respect to them through the library's adjoint kernel.
     The scene's device copy of the parameters is replaced by these values."""
     return _RenderFn.apply(grid, planes, mlp, scene, cameras(cams), W, H, step, t_term, early_term)
+
+
+def check_device(stream=None, self_test: bool = False):
+    """Synchronise and raise MerfError(ERR_DEVICE_BOUNDS) if a kernel of the bounds-checked build
+    recorded an out-of-range index since the last check (never in the release build)."""
+    _check(lib().merf_check_device(_stream(stream), int(self_test)))
 
 
 def set_device_budget(nbytes: int):

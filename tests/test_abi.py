@@ -26,6 +26,16 @@ def test_header_declarations_are_exported():
     assert set(names) == set(merf.EXPORTS)
 
 
+def test_bounds_checked_library_exports_the_header_and_release_refuses_self_test():
+    from paper_2302_12249_b300 import build as _b
+    dbg = ct.CDLL(_b.build(debug=True))
+    for name in merf.EXPORTS:
+        assert hasattr(dbg, name), name
+    dbg.merf_version.restype = ct.c_char_p
+    assert b"bounds-checked" in dbg.merf_version()
+    assert merf.lib().merf_check_device(None, 1) == merf.ERR_UNSUPPORTED
+
+
 def test_version_string():
     assert "sm_103a" in merf.version()
 
