@@ -38,9 +38,10 @@ typedef enum merf_status {
     MERF_ERR_INVALID_ARG = 1,   /* a pointer, size, layout or option is invalid */
     MERF_ERR_OOM = 2,           /* device allocation failed or exceeds the device budget */
     MERF_ERR_CUDA = 3,          /* a CUDA runtime call failed (message in merf_last_error) */
-    MERF_ERR_TIMEOUT = 4,       /* a bounded device-side wait expired */
+    MERF_ERR_TIMEOUT = 4,       /* a bounded wait expired (merf_server_wait) */
     MERF_ERR_DEVICE_BOUNDS = 5, /* a kernel detected an out-of-range index and skipped it */
-    MERF_ERR_UNSUPPORTED = 6    /* a valid request this build does not implement */
+    MERF_ERR_UNSUPPORTED = 6,   /* a valid request this build does not implement */
+    MERF_ERR_CANCELLED = 7      /* the server request was withdrawn by merf_server_cancel */
 } merf_status;
 
 enum { MERF_STORAGE_U8_SPARSE = 0, MERF_STORAGE_F32_DENSE = 1 };
@@ -226,7 +227,8 @@ merf_status merf_render_backward_aux(const merf_scene *scene, const merf_camera 
  * while the GPU is busy join the next iteration and their tiles share launches with the
  * requests already running.  A finished request's image is copied to its host buffer on a copy
  * stream; it completes when that copy has landed.  No device-side wait exists: every kernel
- * terminates on its own once the tile list is exhausted. */
+ * terminates on its own once the tile list is exhausted.  A request not yet being copied out can
+ * be cancelled; its pool space is released once no iteration in flight can still write it. */
 typedef struct merf_server merf_server;
 
 typedef struct merf_server_opts {
@@ -241,8 +243,12 @@ typedef struct merf_server_opts {
 
 typedef struct merf_server_stats {
     unsigned long long submitted, completed, rays, iterations, tiles;
+    unsigned long long cancelled;         /* requests withdrawn by merf_server_cancel */
     size_t pool_bytes, peak_pool_bytes;   /* pool size and its peak reservation */
+    size_t pool_used_bytes;               /* reserved now (admitted requests, cancelled ones in flight) */
     int32_t peak_admitted;                /* most requests admitted at once */
+    int32_t admitted;                     /* requests holding pool space now */
+    int32_t queued;                       /* requests waiting for admission now */
     int32_t reserved;
 } merf_server_stats;
 
@@ -261,8 +267,17 @@ merf_status merf_server_submit(merf_server *srv, int scene, const merf_camera *c
 /* Block until request req_id completes (or timeout_s elapses: MERF_ERR_TIMEOUT, the request
  * stays pending and may be waited for again).  On completion *latency_s (may be NULL) receives
  * the time from submission to the image being in host memory, and the request is released: wait
- * once per request. */
+ * once per request.  A cancelled request returns MERF_ERR_CANCELLED (latency: to its release), one
+ * that failed on the device MERF_ERR_CUDA. */
 merf_status merf_server_wait(merf_server *srv, uint64_t req_id, double timeout_s, double *latency_s);
+
+/* Withdraw request req_id.  *cancelled = 1 if it was still waiting for admission or rendering
+ * (its tiles may still be running): from this call on, its h_out is never written, and
+ * merf_server_wait returns MERF_ERR_CANCELLED once no iteration in flight carries its tiles (its
+ * pool space is free again then).  *cancelled = 0 if its image is already being copied out or it
+ * has completed: it finishes normally.  MERF_ERR_INVALID_ARG for an unknown (or already waited
+ * for) request.  The request must still be waited for, once, to release it. */
+merf_status merf_server_cancel(merf_server *srv, uint64_t req_id, int *cancelled);
 
 merf_status merf_server_get_stats(merf_server *srv, merf_server_stats *out);
 

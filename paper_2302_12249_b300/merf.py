@@ -15,7 +15,7 @@ import torch
 
 from . import build as _build
 
-MERF_OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_DEVICE_BOUNDS, ERR_UNSUPPORTED = range(7)
+MERF_OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_DEVICE_BOUNDS, ERR_UNSUPPORTED, ERR_CANCELLED = range(8)
 STORAGE_U8_SPARSE, STORAGE_F32_DENSE = 0, 1
 PREC_FP32, PREC_FP16, PREC_BF16 = 0, 1, 2
 MAX_OCC_LEVELS = 8
@@ -27,7 +27,7 @@ CNT_RAYS, CNT_LATTICE, CNT_EVAL, CNT_APPEAR = 0, 1, 2, 3
 EXPORTS = ("merf_scene_upload", "merf_scene_upload_dense", "merf_scene_free", "merf_scene_device_bytes",
            "merf_render", "merf_render_aux", "merf_render_host", "merf_render_host_noalloc", "merf_trace",
            "merf_set_device_budget", "merf_scene_set_dense", "merf_render_backward", "merf_render_backward_aux", "merf_server_create", "merf_server_submit", "merf_server_wait",
-           "merf_server_get_stats", "merf_server_destroy", "merf_check_device",
+           "merf_server_cancel", "merf_server_get_stats", "merf_server_destroy", "merf_check_device",
            "merf_last_error", "merf_version")
 
 
@@ -56,8 +56,10 @@ class ServerOpts(ct.Structure):
 
 class ServerStats(ct.Structure):
     _fields_ = [("submitted", ct.c_ulonglong), ("completed", ct.c_ulonglong), ("rays", ct.c_ulonglong),
-                ("iterations", ct.c_ulonglong), ("tiles", ct.c_ulonglong), ("pool_bytes", ct.c_size_t),
-                ("peak_pool_bytes", ct.c_size_t), ("peak_admitted", ct.c_int32), ("reserved", ct.c_int32)]
+                ("iterations", ct.c_ulonglong), ("tiles", ct.c_ulonglong), ("cancelled", ct.c_ulonglong),
+                ("pool_bytes", ct.c_size_t), ("peak_pool_bytes", ct.c_size_t), ("pool_used_bytes", ct.c_size_t),
+                ("peak_admitted", ct.c_int32), ("admitted", ct.c_int32), ("queued", ct.c_int32),
+                ("reserved", ct.c_int32)]
 
 
 _lib = None
@@ -105,9 +107,11 @@ def lib():
         L.merf_server_submit.argtypes = [vp, i32, vp, i32, i32, vp, ct.POINTER(ct.c_uint64)]
         L.merf_server_wait.argtypes = [vp, ct.c_uint64, ct.c_double, ct.POINTER(ct.c_double)]
         L.merf_server_get_stats.argtypes = [vp, ct.POINTER(ServerStats)]
+        L.merf_server_cancel.argtypes = [vp, ct.c_uint64, ct.POINTER(ct.c_int)]
         L.merf_server_destroy.argtypes = [vp]
         L.merf_server_destroy.restype = None
-        for name in ("merf_server_create", "merf_server_submit", "merf_server_wait", "merf_server_get_stats"):
+        for name in ("merf_server_create", "merf_server_submit", "merf_server_wait", "merf_server_cancel",
+                     "merf_server_get_stats"):
             getattr(L, name).restype = ct.c_int
         L.merf_last_error.restype = ct.c_char_p
         L.merf_version.restype = ct.c_char_p
@@ -386,6 +390,13 @@ class Server:
         self._outs.pop(rid, None)
         _check(st)
         return lat.value
+
+    def cancel(self, rid: int) -> bool:
+        """Withdraw a request (True) unless its image is already on its way out (False); either way
+        it must still be waited for, and a withdrawn one raises MerfError(ERR_CANCELLED) there."""
+        c = ct.c_int()
+        _check(lib().merf_server_cancel(self.handle, ct.c_uint64(rid), ct.byref(c)))
+        return bool(c.value)
 
     def stats(self) -> dict:
         s = ServerStats()

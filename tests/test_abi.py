@@ -186,3 +186,5 @@ def test_server_create_and_submit_reject_bad_arguments():
     cam = synth.config_cameras("tiny")
     assert L.merf_server_submit(None, 0, cam.ctypes.data, 4, 4, None, ct.byref(rid)) == merf.ERR_INVALID_ARG
     assert L.merf_server_wait(None, 1, 0.0, None) == merf.ERR_INVALID_ARG
+    assert L.merf_server_cancel(None, 1, ct.byref(ct.c_int())) == merf.ERR_INVALID_ARG
+    assert L.merf_server_get_stats(None, ct.byref(merf.ServerStats())) == merf.ERR_INVALID_ARG

@@ -118,3 +118,29 @@ def test_wait_timeout_then_completion(scenes):
     srv.wait(rid, timeout=120.0)
     srv.close()
     assert (out - _reference(scenes[0], cam, 640, 480, merf.PREC_FP16)).abs().max().item() <= parity.RGB_TOL
+
+
+def test_cancellation(scenes):
+    """Requests withdrawn while queued or rendering end with ERR_CANCELLED and leave their host
+    buffers unwritten; the others complete with merf_render's images, and the pool is free again."""
+    W, H, n = 128, 96, 16
+    srv = merf.Server(scenes, pool_bytes=2 * W * H * 3 * 4 + 4096, step=1 / 64, max_tiles_per_iter=8)
+    cams = synth.sphere_cameras(n, W, H, radius=2.5, seed=91)
+    outs = [_host(W, H).fill_(float("nan")) for _ in range(n)]
+    ids = [srv.submit(k % 2, cams[k], W, H, outs[k]) for k in range(n)]
+    withdrawn = {k for k in range(1, n, 2) if srv.cancel(ids[k])}
+    assert len(withdrawn) >= n // 2 - 2                 # all but those already on their way out
+    for k in range(n):
+        if k in withdrawn:
+            with pytest.raises(merf.MerfError) as e:
+                srv.wait(ids[k])
+            assert e.value.status == merf.ERR_CANCELLED
+            assert torch.isnan(outs[k]).all()
+        else:
+            srv.wait(ids[k])
+            ref = _reference(scenes[k % 2], cams[k], W, H, merf.PREC_FP16)
+            assert (outs[k] - ref).abs().max().item() <= parity.RGB_TOL
+    st = srv.stats()
+    srv.close()
+    assert st["cancelled"] == len(withdrawn) and st["completed"] == n - len(withdrawn)
+    assert (st["pool_used_bytes"], st["admitted"], st["queued"]) == (0, 0, 0)
