@@ -51,7 +51,7 @@ TRAFFIC_SOURCES = ("field.cuh", "merf_api.cu", "render.cuh", "scene.h", "travers
 # an SM's four schedulers issue at most one warp instruction per clock each.
 INST_PER_LAUNCH = 44.122176210e9
 SMS, SCHEDULERS_PER_SM = 148, 4
-TRAFFIC_SOURCES_SHA256 = "5437e6f18ad7634b6136193efffac4e04ff807d68f7bea172dc3db61fb23eee6"
+TRAFFIC_SOURCES_SHA256 = "45a30e2bd388b1bdc62a410951070672904c78f0edb1834337fd5999d5aab1a3"
 
 
 def _sources_sha256() -> str:

@@ -14,6 +14,7 @@
 #include "merf.h"
 #include "backward.cuh"
 #include "render.cuh"
+#include "nvtx.h"
 #include "scene.h"
 
 namespace {
@@ -288,6 +289,7 @@ merf_status merf_scene_upload(const merf_scene_desc *desc, const int32_t *index_
                               const uint8_t *planes, const uint8_t *const *occ_levels, const float *mlp_weights,
                               void *stream, merf_scene **out)
 {
+    const merf::NvtxRange nvtx_range("merf_scene_upload");
     merf_status st = check_desc(desc, MERF_STORAGE_U8_SPARSE);
     if (st) return st;
     if (!out) return fail(MERF_ERR_INVALID_ARG, "out is NULL");
@@ -365,6 +367,7 @@ merf_status merf_scene_upload_dense(const merf_scene_desc *desc, const float *gr
                                     const uint8_t *const *occ_levels, const float *mlp_weights, void *stream,
                                     merf_scene **out)
 {
+    const merf::NvtxRange nvtx_range("merf_scene_upload_dense");
     merf_status st = check_desc(desc, MERF_STORAGE_F32_DENSE);
     if (st) return st;
     if (!out) return fail(MERF_ERR_INVALID_ARG, "out is NULL");
@@ -389,6 +392,7 @@ size_t merf_scene_device_bytes(const merf_scene *scene) { return scene ? scene->
 merf_status merf_render_aux(const merf_scene *scene, const merf_camera *cams, int n_cams, int W, int H, float *out,
                             float *aux, unsigned long long *counters, const merf_render_opts *opts, void *stream)
 {
+    const merf::NvtxRange nvtx_range("merf_render");
     merf_status st = check_frame(scene, cams, n_cams, W, H);
     if (st) return st;
     if ((st = check_opts(opts))) return st;
@@ -415,6 +419,7 @@ HostCopy g_host_copy[64];
 merf_status merf_render_host(const merf_scene *scene, const merf_camera *cams, int n_cams, int W, int H,
                              float *d_staging, float *h_out, const merf_render_opts *opts, void *stream)
 {
+    const merf::NvtxRange nvtx_range("merf_render_host");
     if (!h_out) return fail(MERF_ERR_INVALID_ARG, "h_out is NULL");
     merf_status st = check_frame(scene, cams, n_cams, W, H);
     if (st) return st;
@@ -478,6 +483,7 @@ float *g_noalloc_ptr[kMaxDevices] = {};
 merf_status merf_trace(const merf_scene *scene, const merf_camera *cams, int n_cams, int W, int H, uint32_t *mask,
                        int words, int32_t *n_lattice, const merf_render_opts *opts, void *stream)
 {
+    const merf::NvtxRange nvtx_range("merf_trace");
     merf_status st = check_frame(scene, cams, n_cams, W, H);
     if (st) return st;
     if ((st = check_opts(opts))) return st;
@@ -503,6 +509,7 @@ merf_status merf_trace(const merf_scene *scene, const merf_camera *cams, int n_c
 merf_status merf_render_host_noalloc(const merf_scene *scene, const merf_camera *cams, int n_cams, int W, int H,
                                      float *h_out, const merf_render_opts *opts, void *stream)
 {
+    const merf::NvtxRange nvtx_range("merf_render_host_noalloc");
     if (!h_out) return fail(MERF_ERR_INVALID_ARG, "h_out is NULL");
     merf_status st = check_frame(scene, cams, n_cams, W, H);
     if (st) return st;
@@ -566,6 +573,7 @@ merf_status merf_render_backward_aux(const merf_scene *scene, const merf_camera 
                                      const float *d_out, const float *aux, float *g_grid, float *g_planes,
                                      float *g_mlp, const merf_render_opts *opts, void *stream)
 {
+    const merf::NvtxRange nvtx_range("merf_render_backward");
     merf_status st = check_frame(scene, cams, n_cams, W, H);
     if (st) return st;
     if ((st = check_opts(opts))) return st;

@@ -15,6 +15,7 @@
 #include <cstring>
 
 #include "merf.h"
+#include "nvtx.h"
 #include "render.cuh"
 #include "scene.h"
 #include "serve_sched.h"
@@ -128,6 +129,7 @@ public:
 
     bool launch(int b) override
     {
+        const NvtxRange nvtx_range("merf_server_iteration");
         return cudaGraphLaunch(exec[b], s_comp) == cudaSuccess && cudaEventRecord(ev_iter[b], s_comp) == cudaSuccess;
     }
 
@@ -149,6 +151,7 @@ public:
 
     bool copy_out(ServeRequest &r) override
     {
+        const NvtxRange nvtx_range("merf_server_copy_out");
         return cudaMemcpyAsync(r.h_out, d_pool + r.pool_off, r.floats * sizeof(float), cudaMemcpyDeviceToHost,
                                s_copy) == cudaSuccess &&
                cudaEventRecord((cudaEvent_t)r.dev, s_copy) == cudaSuccess;
