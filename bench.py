@@ -51,7 +51,7 @@ TRAFFIC_SOURCES = ("field.cuh", "merf_api.cu", "render.cuh", "scene.h", "travers
 # an SM's four schedulers issue at most one warp instruction per clock each.
 INST_PER_LAUNCH = 44.122176210e9
 SMS, SCHEDULERS_PER_SM = 148, 4
-TRAFFIC_SOURCES_SHA256 = "45a30e2bd388b1bdc62a410951070672904c78f0edb1834337fd5999d5aab1a3"
+TRAFFIC_SOURCES_SHA256 = "3e9214ec27caaafff2cb49ecd07e51f10e61aa7f38049def501d2144b326fe63"
 
 
 def _sources_sha256() -> str:

@@ -136,6 +136,33 @@ void merf_scene_free(merf_scene *scene);
 /* Device bytes held by a scene. */
 size_t merf_scene_device_bytes(const merf_scene *scene);
 
+/* Scene files: one baked scene as a raw binary file -- the arrays merf_scene_upload(_dense) takes,
+ * behind a 256-byte header, all little-endian.  After the header each array starts at the next
+ * multiple of 64 bytes, in this order:
+ *   uint8 storage:  index_grid int32 [(L/B)^3], atlas uint8 [n_blocks][B][B][B][8],
+ *                   planes uint8 [3][R][R][8] (absent when R = 0);
+ *   float storage:  grid float32 [L][L][L][8], planes float32 [3][R][R][8];
+ *   then both:      occupancy levels uint8 [N_l][N_l][N_l] (finest first), MLP float32 [883].
+ * The file ends at the end of the MLP. */
+typedef struct merf_scene_file_header {
+    char magic[8];               /* "MERFSCN1" */
+    uint32_t version;            /* 1 */
+    uint32_t header_bytes;       /* 256 */
+    uint64_t file_bytes;         /* size of the whole file */
+    float step;                  /* lattice step the scene was made for (informational) */
+    int32_t seed;                /* generator seed (informational) */
+    char name[32];               /* NUL-padded name (informational) */
+    merf_scene_desc desc;        /* as for merf_scene_upload(_dense) */
+    uint8_t reserved[120];       /* zero */
+} merf_scene_file_header;
+
+/* Map a scene file and upload it: merf_scene_upload or merf_scene_upload_dense on its arrays, with
+ * their validation, results and errors (asynchronous on `stream` in the same way).
+ * MERF_ERR_INVALID_ARG if the file cannot be opened or mapped, its magic, version or header size
+ * is not the format's, its descriptor is invalid or has more blocks than the index grid, or its
+ * size differs from the one its descriptor implies. */
+merf_status merf_scene_load(const char *path, void *stream, merf_scene **out);
+
 /* Render n_cams images of W x H pixels into `out` (device float32 [n_cams][H][W][3],
  * written, never read): C = C_d + h(C_d, F, d) per pixel (Sec. 2).  `cams` is a host array
  * of n_cams cameras.  Asynchronous on `stream`. */

@@ -1,6 +1,11 @@
 // merf_api.cu -- the C ABI declared in include/merf.h: scene upload/validation, argument
 // checks and kernel launches.  Host code only; the device code is in render.cuh.
 #include <cuda_runtime.h>
+#include <errno.h>
+#include <fcntl.h>
+#include <sys/mman.h>
+#include <sys/stat.h>
+#include <unistd.h>
 
 #include <algorithm>
 #include <cmath>
@@ -377,6 +382,115 @@ merf_status merf_scene_upload_dense(const merf_scene_desc *desc, const float *gr
     const size_t L = desc->grid_res, R = desc->plane_res;
     return upload_common(desc, grid, L * L * L * 8 * sizeof(float), planes, 3 * R * R * 8 * sizeof(float),
                          nullptr, 0, occ_levels, mlp_weights, stream, out);
+}
+
+}  // extern "C"
+
+namespace {
+
+static_assert(sizeof(merf_scene_file_header) == 256, "scene file header is 256 bytes");
+
+// Byte offsets of a scene file's arrays (the header first, each array 64-byte aligned).
+struct SceneFileLayout {
+    size_t grid = 0, grid_bytes = 0;       // index grid (uint8 storage) or float grid
+    size_t atlas = 0, atlas_bytes = 0;     // uint8 storage only
+    size_t planes = 0, plane_bytes = 0;    // none for a grid-only scene
+    size_t occ[MERF_MAX_OCC_LEVELS] = {};
+    size_t mlp = 0, end = 0;
+};
+
+// desc has passed check_desc and n_blocks <= (L/B)^3, so no size below overflows.
+SceneFileLayout scene_file_layout(const merf_scene_desc &d)
+{
+    SceneFileLayout f;
+    size_t at = sizeof(merf_scene_file_header);
+    auto place = [&at](size_t &off, size_t n) {
+        off = (at + 63) & ~(size_t)63;
+        at = off + n;
+    };
+    const size_t L = d.grid_res, R = d.plane_res;
+    if (d.storage == MERF_STORAGE_U8_SPARSE) {
+        const size_t B = d.block_size, nb = L / B;
+        f.grid_bytes = nb * nb * nb * sizeof(int32_t);
+        place(f.grid, f.grid_bytes);
+        f.atlas_bytes = (size_t)d.n_blocks * B * B * B * MERF_CHANNELS;
+        place(f.atlas, f.atlas_bytes);
+        f.plane_bytes = 3 * R * R * MERF_CHANNELS;
+    } else {
+        f.grid_bytes = L * L * L * MERF_CHANNELS * sizeof(float);
+        place(f.grid, f.grid_bytes);
+        f.plane_bytes = 3 * R * R * MERF_CHANNELS * sizeof(float);
+    }
+    if (f.plane_bytes) place(f.planes, f.plane_bytes);
+    for (int l = 0; l < d.n_occ_levels; ++l) {
+        const size_t n = d.occ_res[l];
+        place(f.occ[l], n * n * n);
+    }
+    place(f.mlp, sizeof(float) * MERF_MLP_PARAMS);
+    f.end = at;
+    return f;
+}
+
+struct Mapping {
+    void *p = MAP_FAILED;
+    size_t n = 0;
+    ~Mapping()
+    {
+        if (p != MAP_FAILED) munmap(p, n);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+merf_status merf_scene_load(const char *path, void *stream, merf_scene **out)
+{
+    const merf::NvtxRange nvtx_range("merf_scene_load");
+    if (!out) return fail(MERF_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!path) return fail(MERF_ERR_INVALID_ARG, "path is NULL");
+    const int fd = open(path, O_RDONLY | O_CLOEXEC);
+    if (fd < 0) return fail(MERF_ERR_INVALID_ARG, "cannot open %s: %s", path, strerror(errno));
+    struct stat sb;
+    if (fstat(fd, &sb) != 0 || sb.st_size < (off_t)sizeof(merf_scene_file_header)) {
+        close(fd);
+        return fail(MERF_ERR_INVALID_ARG, "%s is shorter than a scene file header", path);
+    }
+    Mapping m;
+    m.n = (size_t)sb.st_size;
+    m.p = mmap(nullptr, m.n, PROT_READ, MAP_PRIVATE, fd, 0);
+    close(fd);
+    if (m.p == MAP_FAILED) return fail(MERF_ERR_INVALID_ARG, "cannot map %s: %s", path, strerror(errno));
+    merf_scene_file_header h;
+    memcpy(&h, m.p, sizeof h);
+    if (memcmp(h.magic, "MERFSCN1", 8) != 0) return fail(MERF_ERR_INVALID_ARG, "%s is not a MERF scene file", path);
+    if (h.version != 1 || h.header_bytes != sizeof h)
+        return fail(MERF_ERR_INVALID_ARG, "%s: version %u with a %u-byte header (1 and 256 expected)", path,
+                    h.version, h.header_bytes);
+    if (h.desc.storage != MERF_STORAGE_U8_SPARSE && h.desc.storage != MERF_STORAGE_F32_DENSE)
+        return fail(MERF_ERR_INVALID_ARG, "%s: storage %d", path, h.desc.storage);
+    merf_status st = check_desc(&h.desc, h.desc.storage);
+    if (st) return st;
+    if (h.desc.storage == MERF_STORAGE_U8_SPARSE) {
+        const long long nb = h.desc.grid_res / h.desc.block_size;
+        if (h.desc.n_blocks > nb * nb * nb)
+            return fail(MERF_ERR_INVALID_ARG, "%s: %d blocks for an index grid of %lld", path, h.desc.n_blocks,
+                        nb * nb * nb);
+    }
+    const SceneFileLayout f = scene_file_layout(h.desc);
+    if (h.file_bytes != m.n || f.end != m.n)
+        return fail(MERF_ERR_INVALID_ARG, "%s holds %zu bytes; its header says %llu and its descriptor needs %zu",
+                    path, m.n, (unsigned long long)h.file_bytes, f.end);
+    const uint8_t *base = (const uint8_t *)m.p;
+    const uint8_t *occ[MERF_MAX_OCC_LEVELS] = {};
+    for (int l = 0; l < h.desc.n_occ_levels; ++l) occ[l] = base + f.occ[l];
+    const float *mlp = (const float *)(base + f.mlp);
+    if (h.desc.storage == MERF_STORAGE_U8_SPARSE)
+        return merf_scene_upload(&h.desc, (const int32_t *)(base + f.grid), base + f.atlas,
+                                 f.plane_bytes ? base + f.planes : nullptr, occ, mlp, stream, out);
+    return merf_scene_upload_dense(&h.desc, (const float *)(base + f.grid), (const float *)(base + f.planes), occ,
+                                   mlp, stream, out);
 }
 
 void merf_scene_free(merf_scene *scene)

@@ -8,6 +8,7 @@ There is no CPU fallback: if the library cannot be built or loaded, every call r
 from __future__ import annotations
 
 import ctypes as ct
+import os
 from typing import Optional, Sequence
 
 import numpy as np
@@ -24,9 +25,10 @@ NOALLOC_STAGING_BYTES = 32 << 20
 AUX_CD, AUX_F, AUX_T, AUX_NLAT, AUX_NEVAL, AUX_NAPP, AUX_TERM = 0, 3, 7, 8, 9, 10, 11
 CNT_RAYS, CNT_LATTICE, CNT_EVAL, CNT_APPEAR = 0, 1, 2, 3
 
-EXPORTS = ("merf_scene_upload", "merf_scene_upload_dense", "merf_scene_free", "merf_scene_device_bytes",
-           "merf_render", "merf_render_aux", "merf_render_host", "merf_render_host_noalloc", "merf_trace",
-           "merf_set_device_budget", "merf_scene_set_dense", "merf_render_backward", "merf_render_backward_aux", "merf_server_create", "merf_server_submit", "merf_server_wait",
+EXPORTS = ("merf_scene_upload", "merf_scene_upload_dense", "merf_scene_load", "merf_scene_free",
+           "merf_scene_device_bytes", "merf_render", "merf_render_aux", "merf_render_host", "merf_render_host_noalloc",
+           "merf_trace", "merf_set_device_budget", "merf_scene_set_dense", "merf_render_backward",
+           "merf_render_backward_aux", "merf_server_create", "merf_server_submit", "merf_server_wait",
            "merf_server_cancel", "merf_server_get_stats", "merf_server_destroy", "merf_check_device",
            "merf_last_error", "merf_version")
 
@@ -108,6 +110,8 @@ def lib():
         L.merf_server_wait.argtypes = [vp, ct.c_uint64, ct.c_double, ct.POINTER(ct.c_double)]
         L.merf_server_get_stats.argtypes = [vp, ct.POINTER(ServerStats)]
         L.merf_server_cancel.argtypes = [vp, ct.c_uint64, ct.POINTER(ct.c_int)]
+        L.merf_scene_load.argtypes = [ct.c_char_p, vp, ct.POINTER(vp)]
+        L.merf_scene_load.restype = ct.c_int
         L.merf_server_destroy.argtypes = [vp]
         L.merf_server_destroy.restype = None
         for name in ("merf_server_create", "merf_server_submit", "merf_server_wait", "merf_server_cancel",
@@ -195,6 +199,19 @@ class Scene:
         self.handle = handle
         self.desc = d
         self.source = scene
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "Scene":
+        """Upload a scene file (merf_scene_load: the library maps, validates and uploads it)."""
+        handle = ct.c_void_p()
+        _check(lib().merf_scene_load(os.fsencode(path), _stream(stream), ct.byref(handle)))
+        self = cls.__new__(cls)
+        self.handle = handle
+        with open(path, "rb") as f:
+            head = f.read(64 + ct.sizeof(Desc))
+        self.desc = Desc.from_buffer_copy(head[64:])
+        self.source = None
+        return self
 
     @property
     def device_bytes(self) -> int:

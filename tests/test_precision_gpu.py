@@ -74,6 +74,28 @@ def test_paper_scale_sampled_error_bounds(paper, prec):
     assert _psnr(rgb, ref) > PSNR_MIN
 
 
+@pytest.mark.parametrize("prec", [pytest.param(merf.PREC_FP32, id="fp32")] + PRECS)
+def test_64_camera_launch_sampled(paper, prec):
+    """The precision workload in the launch the benchmark times: 64 ring cameras at 1920 x 1080 in
+    one call (132.7 M rays), pixels sampled across all cameras against the oracle -- the FP32 bar
+    for FP32, the per-channel and PSNR bars for the 16-bit forms."""
+    gs, osc = paper
+    W, H = 1920, 1080
+    cams = synth.ring_cameras(64, W, H, radius=1.5, seed=synth.SEED_CAMERA + 1)
+    out = merf.render(gs, cams, W, H, 1 / 256, precision=prec)
+    torch.cuda.synchronize()
+    pix, lin = parity.pick_pixels(64, W, H, 1500, seed=17)
+    rgb = out.reshape(-1, 3)[torch.from_numpy(lin).cuda()].double().cpu().numpy()
+    del out
+    lo, hi = parity.oracle_rgb(osc, cams, W, H, 1 / 256, pix=pix)
+    if prec == merf.PREC_FP32:
+        assert parity.max_err(rgb, lo, hi).max() <= parity.RGB_TOL
+    else:
+        ref = _closest(rgb, lo, hi)
+        assert np.abs(rgb - ref).max() <= CHANNEL_TOL
+        assert _psnr(rgb, ref) > PSNR_MIN
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_density_and_traversal_unchanged(tiny, prec):
     """Only appearance and the MLP change precision: evaluated samples, opacity and hence
