@@ -44,14 +44,14 @@ B_DENSITY, B_INDEX, B_APPEAR, B_OUT = 20, 4, 140, 12
 # launch from an ncu capture of this workload; reported as roofline.traffic only while the
 # render kernel's sources (device code, launch and scene layout) hash to the value they were
 # measured with (otherwise null).
-TRAFFIC_BYTES_PER_LAUNCH = (401.84 + 617.93) * 1e6
+TRAFFIC_BYTES_PER_LAUNCH = (399.80 + 616.40) * 1e6
 TRAFFIC_SOURCES = ("field.cuh", "merf_api.cu", "render.cuh", "scene.h", "traverse.cuh")
 # Warp-level instructions (smsp__inst_executed.sum) of the same timed launch from an ncu capture
 # (1 pass, full size), for the issue-rate roofline: the kernel is bound by instruction issue, and
 # an SM's four schedulers issue at most one warp instruction per clock each.
 INST_PER_LAUNCH = 44.122176210e9
 SMS, SCHEDULERS_PER_SM = 148, 4
-TRAFFIC_SOURCES_SHA256 = "3e9214ec27caaafff2cb49ecd07e51f10e61aa7f38049def501d2144b326fe63"
+TRAFFIC_SOURCES_SHA256 = "8f8e11ce23716c8d31adf56fc2c0b7e51f346f2cccb38fb60c99e95f81e07e99"
 
 
 def _sources_sha256() -> str:

@@ -319,9 +319,13 @@ void merf_set_device_budget(size_t bytes);
  * index into the index grid, atlas, planes, occupancy levels and dense arrays; an index out of
  * range is skipped (the texel reads as zero, the cell as empty) and recorded, never trapped.
  * Returns MERF_ERR_DEVICE_BOUNDS (merf_last_error names what was out of range) if anything was
- * recorded since the last call, and clears the word.  self_test != 0 (bounds-checked build only,
- * else MERF_ERR_UNSUPPORTED) first records a self-test bit from a one-thread kernel, to exercise
- * the reporting path.  In the release build the word is never set. */
+ * recorded since the last call, and clears the word.  In every build the FP16/BF16 kernels wait
+ * for their tensor-core MMAs on a barrier with a bounded number of polls; a wait that gives up
+ * (its pixels' MLP term then reads as zero) is recorded too, and reported as MERF_ERR_TIMEOUT.
+ * self_test exercises the reporting paths first: 1 (bounds-checked build only, else
+ * MERF_ERR_UNSUPPORTED) records a self-test bit from a one-thread kernel (the call returns
+ * MERF_ERR_DEVICE_BOUNDS); 2 (any build) runs the MLP's bounded barrier wait on a barrier that
+ * nothing arrives on, which gives up after 1000 polls (the call returns MERF_ERR_TIMEOUT). */
 merf_status merf_check_device(void *stream, int self_test);
 
 /* Message of the last failed call on this thread ("" if none). */

@@ -221,6 +221,16 @@ merf::RenderParams make_params(const merf_scene *s, const merf_render_opts *o, i
 __global__ void status_self_test_kernel() { atomicOr(&merf::g_status, merf::kStatusSelfTest); }
 #endif
 
+// A bounded wait that runs out: an mbarrier that nothing arrives on, polled 1000 times with the
+// same wait the tensor-core MLP uses; giving up is recorded as the MLP's would be.
+__global__ void wait_timeout_self_test_kernel()
+{
+    __shared__ alignas(8) uint64_t mbar;
+    merf::mbar_init(&mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!merf::mbar_wait(&mbar, 0, 1000)) merf::set_status(merf::kWaitTimeout);
+}
+
 template <int kPrec>
 void launch_u8(int geo, dim3 grid, dim3 block, cudaStream_t st, const merf::RenderParams &P)
 {
@@ -738,28 +748,36 @@ const char *merf_version(void) { return "merf-b300 0.1 (sm_103a)"; }
 merf_status merf_check_device(void *stream, int self_test)
 {
     cudaStream_t s = (cudaStream_t)stream;
+    if (self_test < 0 || self_test > 2) return fail(MERF_ERR_INVALID_ARG, "self_test %d not in 0..2", self_test);
+    if (self_test == 2) {
+        wait_timeout_self_test_kernel<<<1, 1, 0, s>>>();
+        if (cudaGetLastError() != cudaSuccess) return fail(MERF_ERR_CUDA, "self-test launch failed");
+    }
 #ifdef MERF_DEBUG_BOUNDS
-    if (self_test) {
+    if (self_test == 1) {
         status_self_test_kernel<<<1, 1, 0, s>>>();
         if (cudaGetLastError() != cudaSuccess) return fail(MERF_ERR_CUDA, "self-test launch failed");
     }
 #else
-    if (self_test) return fail(MERF_ERR_UNSUPPORTED, "the status self-test needs the bounds-checked build");
+    if (self_test == 1) return fail(MERF_ERR_UNSUPPORTED, "the bounds self-test needs the bounds-checked build");
 #endif
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(MERF_ERR_CUDA, "check_device: %s", cudaGetErrorString(e));
-#ifdef MERF_DEBUG_BOUNDS
     unsigned int word = 0, zero = 0;
     e = cudaMemcpyFromSymbol(&word, merf::g_status, sizeof word);
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(merf::g_status, &zero, sizeof zero);
     if (e != cudaSuccess) return fail(MERF_ERR_CUDA, "check_device: %s", cudaGetErrorString(e));
     word |= merf::take_server_status();
-    if (word)
-        return fail(MERF_ERR_DEVICE_BOUNDS, "device status 0x%08x:%s%s%s%s%s%s", word,
+    const unsigned bounds = merf::kBadIndexGrid | merf::kBadAtlas | merf::kBadPlane | merf::kBadOcc | merf::kBadDense |
+                            merf::kStatusSelfTest;
+    if (word & bounds)
+        return fail(MERF_ERR_DEVICE_BOUNDS, "device status 0x%08x:%s%s%s%s%s%s%s", word,
                     (word & merf::kBadIndexGrid) ? " index-grid" : "", (word & merf::kBadAtlas) ? " atlas" : "",
                     (word & merf::kBadPlane) ? " plane" : "", (word & merf::kBadOcc) ? " occupancy" : "",
-                    (word & merf::kBadDense) ? " dense" : "", (word & merf::kStatusSelfTest) ? " self-test" : "");
-#endif
+                    (word & merf::kBadDense) ? " dense" : "", (word & merf::kWaitTimeout) ? " wait-timeout" : "",
+                    (word & merf::kStatusSelfTest) ? " self-test" : "");
+    if (word & merf::kWaitTimeout)
+        return fail(MERF_ERR_TIMEOUT, "device status 0x%08x: a tensor-core completion wait gave up", word);
     return ok();
 }
 

@@ -45,8 +45,10 @@ __global__ void __launch_bounds__(kThreads, (kMinBlocks<0, kPrec>)) serve_kernel
 {
     __shared__ MlpSmem<kPrec> ms;
     __shared__ int s_tile;
+    ms.init();                          // the first barrier below publishes it
     const int n_tiles = P.work->n_tiles;
     int cur_scene = -1;
+    uint32_t phase = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(P.counter, 1);
@@ -71,7 +73,7 @@ __global__ void __launch_bounds__(kThreads, (kMinBlocks<0, kPrec>)) serve_kernel
         if (inside)
             march_ray<0, kPrec, kGeo>(P.scenes[sc].fv, P.scenes[sc].occ, R.cam, i, j, P.step, P.t_term, P.early_term, r);
         float h[3];
-        deferred_mlp<kPrec>(ms, r, inside, h);
+        deferred_mlp<kPrec>(ms, phase, r, inside, h);
         if (inside) {
             float *o = P.pool + R.out_off + ((size_t)j * R.W + i) * 3;
             o[0] = r.cd[0] + h[0];
@@ -80,18 +82,15 @@ __global__ void __launch_bounds__(kThreads, (kMinBlocks<0, kPrec>)) serve_kernel
         }
         __syncthreads();                // s_tile and the weights are reused next iteration
     }
+    ms.fini();
 }
 
 unsigned int take_server_status()
 {
-#ifdef MERF_DEBUG_BOUNDS
     unsigned int word = 0, zero = 0;
     if (cudaMemcpyFromSymbol(&word, g_status, sizeof word) != cudaSuccess) return 0;
     cudaMemcpyToSymbol(g_status, &zero, sizeof zero);
     return word;
-#else
-    return 0;
-#endif
 }
 
 // The device behind the scheduler: iteration slot b is work buffer b and captured graph b on the
@@ -210,14 +209,23 @@ merf_status capture(merf::CudaServeBackend *s, int b)
     return MERF_OK;
 }
 
+// One CTA per resident slot.  The launch bounds reserve registers for kMinBlocks CTAs per SM and
+// their shared memory and tensor memory (32 columns each) fit beside one another, but the
+// occupancy query answers 1 for the FP16/BF16 kernels, which allocate tensor memory at run time
+// (measured: 148 CTAs on 148 SMs and 2.8x less serving throughput), so the larger of the two is
+// taken.  The CTAs never wait for one another, so a slot that is not resident only starts late.
 template <int kPrec, int kGeo>
 int resident_grid()
 {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, merf::serve_kernel<kPrec, kGeo>, merf::kThreads, 0);
-    return std::max(1, sms) * std::max(1, per);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, merf::serve_kernel<kPrec, kGeo>, merf::kThreads, 0) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        per = 0;
+    }
+    return std::max(1, sms) * std::max(per, merf::kMinBlocks<0, kPrec>);
 }
 
 }  // namespace

@@ -6,8 +6,9 @@
 // appearance values enter the result only when the sample's opacity is non-zero, Sec. 5),
 // front-to-back compositing of C_d and F with early termination (Eq. 1, Eq. 2, Sec. 5), and
 // finally the deferred MLP h(C_d, F, d) (Sec. 2, App. B), whose 883 weights are staged once per
-// CTA in shared memory (FP32: per pixel on the CUDA cores; FP16 / BF16: per warp on the tensor
-// cores).  A warp covers an 8 x 4 pixel tile and a CTA a 16 x 8 tile, so neighbouring rays walk
+// CTA in shared memory (FP32: per pixel on the CUDA cores; FP16 / BF16: the CTA's 128 pixels as
+// one M = 128 tcgen05.mma tile, accumulated in tensor memory).  A warp covers an 8 x 4 pixel
+// tile and a CTA a 16 x 8 tile, so neighbouring rays walk
 // neighbouring texels together and share L1 lines.  Template parameters select the storage
 // (uint8 block-sparse / dense float), the precision (FP32 / FP16 / BF16 appearance arithmetic
 // and MLP), the gather geometry (the paper's / grid-only / run-time strides) and the contraction
@@ -16,6 +17,7 @@
 
 #include "field.cuh"
 #include "traverse.cuh"
+#include "umma.cuh"
 
 namespace merf {
 
@@ -163,30 +165,33 @@ __device__ __forceinline__ void mlp_f32(const float *w, const float cd[3], const
 }
 
 // ---------------------------------------------------------------------------------------------
-// The deferred MLP on tensor cores (precision form): one warp evaluates its 32 pixels with
-// mma.sync m16n8k16 (FP16 or BF16 operands, FP32 accumulation).  Layer 1 is [32 x 48] x [48 x 16]
-// (34 inputs zero-padded to 48), layer 2 [32 x 16] x [16 x 16], layer 3 [32 x 16] x [16 x 8]
-// (3 outputs zero-padded to 8).  A layer's FP32 accumulator fragments, after bias and ReLU, are
-// packed directly into the next layer's A fragments (the m16n8 C layout of two adjacent n-tiles
-// is the m16k16 A layout), so only the inputs and outputs pass through shared memory.
+// The deferred MLP on the tensor cores (precision form): the CTA's 128 pixels are one M = 128
+// tile of tcgen05.mma (kind::f16: FP16 or BF16 operands from shared memory, FP32 accumulator in
+// tensor memory).  Layer 1 is [128 x 48] x [48 x 16] (34 inputs zero-padded to 48, three K = 16
+// steps), layer 2 [128 x 16] x [16 x 16], layer 3 [128 x 16] x [16 x 16] (3 outputs zero-padded to
+// 16).  One thread issues each layer's MMAs and commits them to an mbarrier; every thread then
+// reads its own pixel's row of the accumulator (TMEM lane = pixel), adds the bias, applies ReLU
+// and writes its row of the next layer's A operand.  BF16 keeps only 8 significant bits, so in
+// that mode every operand is carried as an unevaluated sum hi + lo of two bfloat16 values and
+// each product takes three passes (hi*hi + lo*hi + hi*lo, all accumulated in FP32); FP16 uses one.
 
-constexpr int kW0Stride = 28, kW1Stride = 12, kXStride = 28;   // 32-bit words per row (padded)
+constexpr int kTmemCols = 32;               // the smallest TMEM allocation; N = 16 uses 16
+constexpr int kWaitPolls = 1 << 22;         // bounded wait for an MMA group (microseconds in practice)
 
-// BF16 keeps only 8 significant bits, so in that mode every operand is carried as an unevaluated
-// sum hi + lo of two bfloat16 values and each product takes three tensor-core passes
-// (hi*hi + lo*hi + hi*lo, all accumulated in FP32); FP16 uses one pass.
-// Shared memory is kept small (it is carved out of the same on-chip storage as the L1 cache
-// that serves the texel gathers): only BF16 stores low parts, and each warp stages the input
-// rows of one 16-pixel tile at a time.
 template <int kPrec>
-struct MlpTC {
-    static constexpr int kParts = kPrec == 2 ? 2 : 1;
-    uint32_t w0[kParts][16 * kW0Stride];   // W0^T [n][k], k < 48, 16-bit pairs; [1]: BF16 low parts
-    uint32_t w1[kParts][16 * kW1Stride];   // W1^T [n][k], k < 16
-    uint32_t w2[kParts][8 * kW1Stride];    // W2^T [n][k], n < 3 used
-    float b0[16], b1[16], b2[8];
-    uint32_t x[kParts][kThreads / 32][16 * kXStride];   // per-warp rows of one tile; [1]: BF16 low parts
+struct MlpUmma {
+    static constexpr int kParts = kPrec == 2 ? 2 : 1;     // [1]: BF16 low parts
+    // A operand.  Layer 1: the 128 x 48 rows (BF16: the high parts, then the low parts in a
+    // second round).  Layers 2 and 3: the 128 x 16 rows at 0, BF16 low parts at kLoOffset.
+    alignas(128) uint8_t x[128 * 48 * 2];
+    alignas(128) uint8_t w0[kParts][16 * 48 * 2];          // B: W0^T [n][k], K-major
+    alignas(128) uint8_t w1[kParts][16 * 16 * 2];          // W1^T
+    alignas(128) uint8_t w2[kParts][16 * 16 * 2];          // W2^T, rows n >= 3 zero
+    float b0[16], b1[16], b2[4];
+    alignas(8) uint64_t mbar;
+    uint32_t tmem;                                         // the CTA's accumulator columns
 };
+constexpr int kLoOffset = 128 * 16 * 2;
 
 template <int kPrec>
 __device__ __forceinline__ uint32_t pack16(float lo, float hi)
@@ -214,86 +219,150 @@ __device__ __forceinline__ uint32_t pack16_lo(float lo, float hi)
     return pack16<kPrec>(bf16_rest(lo), bf16_rest(hi));
 }
 
-template <int kPrec>
-__device__ __forceinline__ void mma16816(float d[4], const uint32_t a[4], uint32_t b0, uint32_t b1)
+// One 16-bit element pair (k, k + 1) of row n of a K-major B tile, with its BF16 low part.
+template <int kPrec, int K, int kBytes>
+__device__ __forceinline__ void put_w(uint8_t (&w)[MlpUmma<kPrec>::kParts][kBytes], int n, int k, float a, float b)
 {
-    if constexpr (kPrec == 1)
-        asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                     "{%0,%1,%2,%3};\n"
-                     : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                     : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-    else
-        asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                     "{%0,%1,%2,%3};\n"
-                     : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                     : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    const int off = kmajor_offset(n, k, K);
+    *reinterpret_cast<uint32_t *>(&w[0][off]) = pack16<kPrec>(a, b);
+    if constexpr (kPrec == 2) *reinterpret_cast<uint32_t *>(&w[1][off]) = pack16_lo<kPrec>(a, b);
 }
 
-// Stage the scene's FP32 weights as transposed 16-bit tiles (whole CTA, before a barrier).
+// TMEM columns and the completion barrier (before the CTA's first barrier).
 template <int kPrec>
-__device__ __forceinline__ void mlp_tc_load(MlpTC<kPrec> &ms, const float *w)
+__device__ __forceinline__ void mlp_umma_init(MlpUmma<kPrec> &ms)
+{
+    if (threadIdx.x < 32) tmem_alloc<kTmemCols>(&ms.tmem);
+    if (threadIdx.x == 0) {
+        mbar_init(&ms.mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+}
+
+// Every warp's accumulator reads are done; warp 0 frees the columns (all threads call it).
+template <int kPrec>
+__device__ __forceinline__ void mlp_umma_fini(MlpUmma<kPrec> &ms)
+{
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        tc_fence_after();
+        tmem_dealloc<kTmemCols>(ms.tmem);
+    }
+}
+
+// Stage the scene's FP32 weights as K-major 16-bit B tiles (whole CTA, before a barrier).
+template <int kPrec>
+__device__ __forceinline__ void mlp_umma_load(MlpUmma<kPrec> &ms, const float *w)
 {
     const float *W0 = w, *B0 = w + 544, *W1 = w + 560, *B1 = w + 816, *W2 = w + 832, *B2 = w + 880;
     for (int e = threadIdx.x; e < 16 * 24; e += kThreads) {
-        const int n = e / 24, kk = 2 * (e % 24);
-        const float a = kk < 34 ? __ldg(W0 + kk * 16 + n) : 0.0f;
-        const float b = kk + 1 < 34 ? __ldg(W0 + (kk + 1) * 16 + n) : 0.0f;
-        ms.w0[0][n * kW0Stride + e % 24] = pack16<kPrec>(a, b);
-        if constexpr (kPrec == 2) ms.w0[1][n * kW0Stride + e % 24] = pack16_lo<kPrec>(a, b);
+        const int n = e / 24, k = 2 * (e % 24);
+        const float a = k < 34 ? __ldg(W0 + k * 16 + n) : 0.0f;
+        const float b = k + 1 < 34 ? __ldg(W0 + (k + 1) * 16 + n) : 0.0f;
+        put_w<kPrec, 48>(ms.w0, n, k, a, b);
     }
     for (int e = threadIdx.x; e < 16 * 8; e += kThreads) {
-        const int n = e / 8, kk = 2 * (e % 8);
-        const float a = __ldg(W1 + kk * 16 + n), b = __ldg(W1 + (kk + 1) * 16 + n);
-        ms.w1[0][n * kW1Stride + e % 8] = pack16<kPrec>(a, b);
-        if constexpr (kPrec == 2) ms.w1[1][n * kW1Stride + e % 8] = pack16_lo<kPrec>(a, b);
-    }
-    for (int e = threadIdx.x; e < 8 * 8; e += kThreads) {
-        const int n = e / 8, kk = 2 * (e % 8);
-        const float a = n < 3 ? __ldg(W2 + kk * 3 + n) : 0.0f, b = n < 3 ? __ldg(W2 + (kk + 1) * 3 + n) : 0.0f;
-        ms.w2[0][n * kW1Stride + e % 8] = pack16<kPrec>(a, b);
-        if constexpr (kPrec == 2) ms.w2[1][n * kW1Stride + e % 8] = pack16_lo<kPrec>(a, b);
+        const int n = e / 8, k = 2 * (e % 8);
+        put_w<kPrec, 16>(ms.w1, n, k, __ldg(W1 + k * 16 + n), __ldg(W1 + (k + 1) * 16 + n));
+        const float a = n < 3 ? __ldg(W2 + k * 3 + n) : 0.0f, b = n < 3 ? __ldg(W2 + (k + 1) * 3 + n) : 0.0f;
+        put_w<kPrec, 16>(ms.w2, n, k, a, b);
     }
     for (int e = threadIdx.x; e < 16; e += kThreads) {
         ms.b0[e] = __ldg(B0 + e);
         ms.b1[e] = __ldg(B1 + e);
-        if (e < 8) ms.b2[e] = e < 3 ? __ldg(B2 + e) : 0.0f;
+        if (e < 4) ms.b2[e] = e < 3 ? __ldg(B2 + e) : 0.0f;
     }
 }
 
-template <int kPrec>
-__device__ __forceinline__ void relu_pack(const float c0[4], const float c1[4], uint32_t a[4], uint32_t al[4])
+// This thread's row (pixel) of a K-column A tile at `dst` (BF16 low parts if kLow): 8 elements
+// per 16-byte store.
+template <int kPrec, int K, bool kLow>
+__device__ __forceinline__ void put_row(uint8_t *dst, const float *v)
 {
-    const float v[8] = {fmaxf(c0[0], 0.0f), fmaxf(c0[1], 0.0f), fmaxf(c0[2], 0.0f), fmaxf(c0[3], 0.0f),
-                        fmaxf(c1[0], 0.0f), fmaxf(c1[1], 0.0f), fmaxf(c1[2], 0.0f), fmaxf(c1[3], 0.0f)};
+    const int t = threadIdx.x;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        a[r] = pack16<kPrec>(v[2 * r], v[2 * r + 1]);
-        if (kPrec == 2) al[r] = pack16_lo<kPrec>(v[2 * r], v[2 * r + 1]);
+    for (int c = 0; c < K / 8; ++c) {
+        uint32_t u[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            u[q] = kLow ? pack16_lo<kPrec>(v[8 * c + 2 * q], v[8 * c + 2 * q + 1])
+                        : pack16<kPrec>(v[8 * c + 2 * q], v[8 * c + 2 * q + 1]);
+        *reinterpret_cast<uint4 *>(dst + kmajor_offset(t, 8 * c, K)) = make_uint4(u[0], u[1], u[2], u[3]);
     }
 }
 
-// D += A B, with the BF16 split when kPrec == 2 (a/b: high parts, al/bl: low parts)
-template <int kPrec>
-__device__ __forceinline__ void mma_acc(float d[4], const uint32_t a[4], const uint32_t al[4], uint32_t b0,
-                                        uint32_t b1, uint32_t bl0, uint32_t bl1)
+// D (+)= A B over K (K / 16 MMAs of K = 16; two 128-byte core-matrix columns each), A and B
+// K-major tiles at shared addresses a and b.  Issuing thread only.
+template <int kPrec, int K>
+__device__ __forceinline__ void mma_k(uint32_t tmem, uint32_t a, uint32_t b, bool accumulate)
 {
-    mma16816<kPrec>(d, a, b0, b1);
-    if constexpr (kPrec == 2) {
-        mma16816<kPrec>(d, al, b0, b1);
-        mma16816<kPrec>(d, a, bl0, bl1);
+    constexpr uint32_t kId = umma_idesc_f16(128, 16, kPrec == 2), kSbo = (K / 8) * 128;
+#pragma unroll
+    for (int ks = 0; ks < K / 16; ++ks)
+        umma_f16(tmem, umma_smem_desc(a + 256u * ks, 128, kSbo), umma_smem_desc(b + 256u * ks, 128, kSbo), kId,
+                 accumulate || ks > 0);
+}
+
+// One round on the tensor cores: every thread's operand rows are published, thread 0 issues the
+// MMAs (`issue`) and commits them to the barrier, and all threads wait for them.  False if the
+// wait gave up (recorded in the device status word); uniform within each warp.
+template <int kPrec, typename Issue>
+__device__ __forceinline__ bool umma_round(MlpUmma<kPrec> &ms, uint32_t &phase, Issue issue)
+{
+    fence_async_smem();          // this thread's operand writes, to the tensor cores
+    tc_fence_before();
+    __syncthreads();             // all rows written; every earlier accumulator read done
+    tc_fence_after();
+    if (threadIdx.x == 0) {
+        issue();
+        umma_commit(&ms.mbar);
+    }
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(&ms.mbar, phase, kWaitPolls));
+    phase ^= 1u;
+    tc_fence_after();
+    if (!ok && (threadIdx.x & 31) == 0) set_status(kWaitTimeout);
+    return ok;
+}
+
+// This thread's accumulator row (nc = 16 or 4 columns), zeros if the MMAs did not complete.
+template <int nc>
+__device__ __forceinline__ void acc_row(uint32_t tmem, bool ok, float *acc)
+{
+    if (ok) {
+        if constexpr (nc == 16) tmem_ld16(tmem, 0, acc);
+        else tmem_ld4(tmem, 0, acc);
+    } else {
+#pragma unroll
+        for (int c = 0; c < nc; ++c) acc[c] = 0.0f;
     }
 }
 
-// All 32 lanes of the warp call this together (lanes without a pixel pass zeros).  The warp's
-// pixels form two 16-row tiles (lanes 0-15, 16-31), evaluated one after the other.
-template <int kPrec>
-__device__ __forceinline__ void mlp_tc(MlpTC<kPrec> &ms, const float cd[3], const float f[4], const float d[3],
-                                       float out[3])
+// A 16-input layer (2 or 3): D = H W, BF16 as hi*hi + lo*hi + hi*lo in one round.
+template <int kPrec, int nc>
+__device__ __forceinline__ void layer16(MlpUmma<kPrec> &ms, uint32_t &phase, uint8_t (&w)[MlpUmma<kPrec>::kParts][512],
+                                        const float h[16], float *acc)
 {
-    constexpr int hi = 0, lo = MlpTC<kPrec>::kParts - 1;
-    const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3, row = lane & 15;
-    uint32_t *xs = ms.x[hi][threadIdx.x >> 5];
-    uint32_t *xl = ms.x[lo][threadIdx.x >> 5];
+    put_row<kPrec, 16, false>(ms.x, h);
+    if constexpr (kPrec == 2) put_row<kPrec, 16, true>(ms.x + kLoOffset, h);
+    const uint32_t x = smem_addr(ms.x), wh = smem_addr(w[0]), wl = smem_addr(w[MlpUmma<kPrec>::kParts - 1]);
+    const uint32_t tm = ms.tmem;
+    const bool ok = umma_round(ms, phase, [&] {
+        mma_k<kPrec, 16>(tm, x, wh, false);
+        if constexpr (kPrec == 2) {
+            mma_k<kPrec, 16>(tm, x + kLoOffset, wh, true);
+            mma_k<kPrec, 16>(tm, x, wl, true);
+        }
+    });
+    acc_row<nc>(tm, ok, acc);
+}
+
+// h(C_d, F, d) of this thread's pixel; all 128 threads of the CTA call it together (threads
+// without a pixel pass zeros and ignore the result).
+template <int kPrec>
+__device__ __forceinline__ void mlp_umma(MlpUmma<kPrec> &ms, uint32_t &phase, const float cd[3], const float f[4],
+                                         const float d[3], float out[3])
+{
     float x[48];
     x[0] = cd[0]; x[1] = cd[1]; x[2] = cd[2];
     x[3] = f[0]; x[4] = f[1]; x[5] = f[2]; x[6] = f[3];
@@ -311,76 +380,31 @@ __device__ __forceinline__ void mlp_tc(MlpTC<kPrec> &ms, const float cd[3], cons
     }
 #pragma unroll
     for (int k = 34; k < 48; ++k) x[k] = 0.0f;
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-        __syncwarp();
-        if ((lane >> 4) == t) {
-#pragma unroll
-            for (int j = 0; j < 24; ++j) {
-                xs[row * kXStride + j] = pack16<kPrec>(x[2 * j], x[2 * j + 1]);
-                if constexpr (kPrec == 2) xl[row * kXStride + j] = pack16_lo<kPrec>(x[2 * j], x[2 * j + 1]);
-            }
-        }
-        __syncwarp();
-        // layer 1: [16 x 48] x [48 x 16]
-        float acc[2][4];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            acc[u][0] = acc[u][2] = ms.b0[8 * u + 2 * c];
-            acc[u][1] = acc[u][3] = ms.b0[8 * u + 2 * c + 1];
-        }
-#pragma unroll
-        for (int sl = 0; sl < 3; ++sl) {
-            const int r0 = g * kXStride + 8 * sl + c, r1 = r0 + 8 * kXStride;
-            const uint32_t a[4] = {xs[r0], xs[r1], xs[r0 + 4], xs[r1 + 4]};
-            uint32_t al[4] = {0u, 0u, 0u, 0u};
-            if constexpr (kPrec == 2) { al[0] = xl[r0]; al[1] = xl[r1]; al[2] = xl[r0 + 4]; al[3] = xl[r1 + 4]; }
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int wi = (8 * u + g) * kW0Stride + 8 * sl + c;
-                mma_acc<kPrec>(acc[u], a, al, ms.w0[hi][wi], ms.w0[hi][wi + 4], ms.w0[lo][wi], ms.w0[lo][wi + 4]);
-            }
-        }
-        // layer 2: [16 x 16] x [16 x 16]
-        float acc2[2][4];
-        {
-            uint32_t a[4], al[4];
-            relu_pack<kPrec>(acc[0], acc[1], a, al);
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                acc2[u][0] = acc2[u][2] = ms.b1[8 * u + 2 * c];
-                acc2[u][1] = acc2[u][3] = ms.b1[8 * u + 2 * c + 1];
-                const int wi = (8 * u + g) * kW1Stride + c;
-                mma_acc<kPrec>(acc2[u], a, al, ms.w1[hi][wi], ms.w1[hi][wi + 4], ms.w1[lo][wi], ms.w1[lo][wi + 4]);
-            }
-        }
-        // layer 3: [16 x 16] x [16 x 8]
-        float acc3[4];
-        {
-            uint32_t a[4], al[4];
-            relu_pack<kPrec>(acc2[0], acc2[1], a, al);
-            acc3[0] = acc3[2] = ms.b2[2 * c];
-            acc3[1] = acc3[3] = ms.b2[2 * c + 1];
-            const int wi = g * kW1Stride + c;
-            mma_acc<kPrec>(acc3, a, al, ms.w2[hi][wi], ms.w2[hi][wi + 4], ms.w2[lo][wi], ms.w2[lo][wi + 4]);
-        }
-        // the tile's 16 x 3 outputs go back to their pixels through shared memory
-        __syncwarp();
-        float *os = reinterpret_cast<float *>(xs);
-        if (c < 2) {
-            os[g * 4 + 2 * c] = acc3[0];
-            os[g * 4 + 2 * c + 1] = acc3[1];
-            os[(g + 8) * 4 + 2 * c] = acc3[2];
-            os[(g + 8) * 4 + 2 * c + 1] = acc3[3];
-        }
-        __syncwarp();
-        if ((lane >> 4) == t) {
-            out[0] = os[row * 4 + 0];
-            out[1] = os[row * 4 + 1];
-            out[2] = os[row * 4 + 2];
-        }
+    // layer 1 (BF16: hi*hi + hi*lo, then the low parts replace the high ones for lo*hi)
+    const uint32_t xa = smem_addr(ms.x), wh = smem_addr(ms.w0[0]), wl = smem_addr(ms.w0[MlpUmma<kPrec>::kParts - 1]);
+    const uint32_t tm = ms.tmem;
+    put_row<kPrec, 48, false>(ms.x, x);
+    bool ok = umma_round(ms, phase, [&] {
+        mma_k<kPrec, 48>(tm, xa, wh, false);
+        if constexpr (kPrec == 2) mma_k<kPrec, 48>(tm, xa, wl, true);
+    });
+    if constexpr (kPrec == 2) {
+        put_row<kPrec, 48, true>(ms.x, x);
+        ok = umma_round(ms, phase, [&] { mma_k<kPrec, 48>(tm, xa, wh, true); }) && ok;
     }
-    __syncwarp();
+    float h[16];
+    acc_row<16>(tm, ok, h);
+#pragma unroll
+    for (int o = 0; o < 16; ++o) h[o] = fmaxf(h[o] + ms.b0[o], 0.0f);
+    float h2[16];
+    layer16<kPrec, 16>(ms, phase, ms.w1, h, h2);
+#pragma unroll
+    for (int o = 0; o < 16; ++o) h2[o] = fmaxf(h2[o] + ms.b1[o], 0.0f);
+    float y[4];
+    layer16<kPrec, 4>(ms, phase, ms.w2, h2, y);
+    out[0] = y[0] + ms.b2[0];
+    out[1] = y[1] + ms.b2[1];
+    out[2] = y[2] + ms.b2[2];
 }
 
 __device__ __forceinline__ void pixel_of_thread(int &i, int &j)
@@ -510,25 +534,31 @@ struct MlpSmem;
 template <>
 struct MlpSmem<0> {
     float w[kMlpParams];
+    __device__ __forceinline__ void init() {}
     __device__ __forceinline__ void load(const float *mlp)
     {
         for (int t = threadIdx.x; t < kMlpParams; t += kThreads) w[t] = __ldg(mlp + t);
     }
+    __device__ __forceinline__ void fini() {}
 };
 template <int kPrec>
 struct MlpSmem {
-    MlpTC<kPrec> tc;
-    __device__ __forceinline__ void load(const float *mlp) { mlp_tc_load<kPrec>(tc, mlp); }
+    MlpUmma<kPrec> tc;
+    __device__ __forceinline__ void init() { mlp_umma_init<kPrec>(tc); }      // before the first barrier
+    __device__ __forceinline__ void load(const float *mlp) { mlp_umma_load<kPrec>(tc, mlp); }
+    __device__ __forceinline__ void fini() { mlp_umma_fini<kPrec>(tc); }      // all threads, at the end
 };
 
-// h(C_d, F, d) for every thread of the warp (all lanes call; `live` lanes own a pixel).
+// h(C_d, F, d) for this thread's pixel (every thread of the CTA calls; `live` ones own a pixel).
+// `phase`: parity of the tensor-core completion barrier, carried across calls.
 template <int kPrec>
-__device__ __forceinline__ void deferred_mlp(MlpSmem<kPrec> &ms, const RayState &r, bool live, float h[3])
+__device__ __forceinline__ void deferred_mlp(MlpSmem<kPrec> &ms, uint32_t &phase, const RayState &r, bool live,
+                                             float h[3])
 {
     if constexpr (kPrec == 0) {
         if (live) mlp_f32(ms.w, r.cd, r.F, r.d, h);
     } else {
-        mlp_tc<kPrec>(ms.tc, r.cd, r.F, r.d, h);     // whole warp, tensor cores
+        mlp_umma<kPrec>(ms.tc, phase, r.cd, r.F, r.d, h);     // whole CTA, tensor cores
     }
 }
 
@@ -544,6 +574,7 @@ template <int kStorage, int kPrec, int kGeo, int kSph = 0>
 __global__ void __launch_bounds__(kThreads, (kMinBlocks<kStorage, kPrec>)) render_kernel(const __grid_constant__ RenderParams P)
 {
     __shared__ MlpSmem<kPrec> ms;
+    ms.init();
     ms.load(P.mlp);
     __syncthreads();
 
@@ -560,7 +591,8 @@ __global__ void __launch_bounds__(kThreads, (kMinBlocks<kStorage, kPrec>)) rende
             march_ray_sph<kStorage, kGeo>(P.fv, P.occ, P.cams.m[cl], i, j, P.step, P.t_term, P.early_term, r);
     }
     float h[3];
-    deferred_mlp<kPrec>(ms, r, inside, h);
+    uint32_t phase = 0;
+    deferred_mlp<kPrec>(ms, phase, r, inside, h);
     if (inside) {
         const size_t pix = ((size_t)(P.cam0 + cl) * P.H + j) * P.W + i;
         P.out[pix * 3 + 0] = r.cd[0] + h[0];
@@ -590,6 +622,7 @@ __global__ void __launch_bounds__(kThreads, (kMinBlocks<kStorage, kPrec>)) rende
             atomicAdd(P.counters + 3, a);
         }
     }
+    ms.fini();
 }
 
 // Traversal only (no gather, no termination): the set of evaluated lattice samples per ray.

@@ -359,9 +359,10 @@ def render_differentiable(scene: Scene, grid: torch.Tensor, planes: torch.Tensor
     return _RenderFn.apply(grid, planes, mlp, scene, cameras(cams), W, H, step, t_term, early_term)
 
 
-def check_device(stream=None, self_test: bool = False):
-    """Synchronise and raise MerfError(ERR_DEVICE_BOUNDS) if a kernel of the bounds-checked build
-    recorded an out-of-range index since the last check (never in the release build)."""
+def check_device(stream=None, self_test: int = 0):
+    """Synchronise and raise MerfError if a kernel recorded a problem since the last check:
+    ERR_DEVICE_BOUNDS for an out-of-range index (bounds-checked build), ERR_TIMEOUT for a bounded
+    tensor-core wait that gave up (any build).  self_test 1 / 2 exercises those two reports."""
     _check(lib().merf_check_device(_stream(stream), int(self_test)))
 
 

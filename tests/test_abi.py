@@ -34,6 +34,8 @@ def test_bounds_checked_library_exports_the_header_and_release_refuses_self_test
     dbg.merf_version.restype = ct.c_char_p
     assert b"bounds-checked" in dbg.merf_version()
     assert merf.lib().merf_check_device(None, 1) == merf.ERR_UNSUPPORTED
+    assert merf.lib().merf_check_device(None, 3) == merf.ERR_INVALID_ARG
+    assert merf.lib().merf_check_device(None, -1) == merf.ERR_INVALID_ARG
 
 
 def test_version_string():

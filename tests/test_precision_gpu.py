@@ -131,3 +131,19 @@ def test_reduced_precision_rejected_for_dense_storage():
     with pytest.raises(merf.MerfError) as e:
         merf.render(gs, cams, 8, 8, sc.cfg.step, precision=merf.PREC_FP16)
     assert e.value.status == merf.ERR_UNSUPPORTED
+
+
+def test_bounded_wait_reports_timeout(tiny):
+    """The tensor-core MLP waits for its MMAs on a barrier with a bounded number of polls.  On a
+    barrier that nothing arrives on the same wait gives up; merf_check_device reports
+    ERR_TIMEOUT once, clears the word, and the context keeps working."""
+    gs, osc = tiny
+    merf.check_device()
+    with pytest.raises(merf.MerfError) as e:
+        merf.check_device(self_test=2)
+    assert e.value.status == merf.ERR_TIMEOUT and "gave up" in str(e.value)
+    merf.check_device()
+    cams = synth.config_cameras("tiny", W=32, H=24, n=1)
+    out = merf.render(gs, cams, 32, 24, 1 / 64, precision=merf.PREC_FP16)
+    merf.check_device()
+    assert torch.isfinite(out).all()
