@@ -51,7 +51,7 @@ TRAFFIC_SOURCES = ("field.cuh", "merf_api.cu", "render.cuh", "scene.h", "travers
 # an SM's four schedulers issue at most one warp instruction per clock each.
 INST_PER_LAUNCH = 44.122176210e9
 SMS, SCHEDULERS_PER_SM = 148, 4
-TRAFFIC_SOURCES_SHA256 = "8f8e11ce23716c8d31adf56fc2c0b7e51f346f2cccb38fb60c99e95f81e07e99"
+TRAFFIC_SOURCES_SHA256 = "f5a02094d260a09bffe35aa16023cb13796c80dff8a341b6440e07a863a63581"
 
 
 def _sources_sha256() -> str:

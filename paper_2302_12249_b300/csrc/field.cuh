@@ -293,7 +293,7 @@ __device__ __forceinline__ void byte_sums_u8(const Taps &t, float2 acc[4])
 // FP16: one byte permute gives a half2 of 1024 + byte for two channels (the half 0x64XX is
 // 1024 + XX), and the difference of two such halves is the exact byte difference.  BF16 (7
 // stored mantissa bits cannot hold 1024 + byte) takes the differences in FP32 from the packed
-// 2^23 + byte floats and converts them to bfloat16 exactly.
+// 2^23 + byte floats; their high halves are their exact bfloat16 values.
 
 __device__ __forceinline__ __half2 magic_h2(uint32_t w, uint32_t sel)
 {
@@ -358,8 +358,13 @@ __device__ __forceinline__ void lp_tap(const Taps &t, float2 &k01, LpAcc<kPrec> 
             const __nv_bfloat162 w2 = __float2bfloat162_rn(w);
 #pragma unroll
             for (int p = 0; p < 3; ++p) {
+                // d holds exact integers |d| <= 255, which bfloat16 keeps exactly; a bfloat16 is
+                // the high half of the FP32 word, so one byte permute packs the pair
                 const float2 d = __fadd2_rn(m[p], a.nfirst[p]);
-                a.corr[p] = __hfma2(w2, __float22bfloat162_rn(d), a.corr[p]);
+                const uint32_t u = __byte_perm(__float_as_uint(d.x), __float_as_uint(d.y), 0x7632u);
+                __nv_bfloat162 db;
+                memcpy(&db, &u, 4);
+                a.corr[p] = __hfma2(w2, db, a.corr[p]);
             }
         }
     }

@@ -120,6 +120,38 @@ __device__ __forceinline__ void composite(Accum &acc, float w, const AppArg &a)
     acc.f23 = __ffma2_rn(w2, sigmoid2(a.y67), acc.f23);
 }
 
+__device__ __forceinline__ float tanh_approx(float x)
+{
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// 16-bit forms: sigmoid(x) = (1 + tanh(x / 2)) / 2, so AppArg holds t = x / 2 =
+// (7 / 255) k - 3.5 W, and compositing accumulates only (w / 2) tanh(t); the constant halves
+// sum to (1 - T) / 2 per ray (the weights alpha_i T_i sum to 1 - T), added once at the end.
+__device__ __forceinline__ AppArg app_arg_u8_half(const float2 k[4], float wsum)
+{
+    const float A = 7.0f / 255.0f, b = -3.5f * wsum;
+    const float2 A2 = make_float2(A, A), b2 = make_float2(b, b);
+    AppArg a;
+    a.y1 = fmaf(k[0].y, A, b);
+    a.y23 = __ffma2_rn(k[1], A2, b2);
+    a.y45 = __ffma2_rn(k[2], A2, b2);
+    a.y67 = __ffma2_rn(k[3], A2, b2);
+    return a;
+}
+
+__device__ __forceinline__ void composite_tanh(Accum &acc, float w, const AppArg &a)
+{
+    const float hw = 0.5f * w;
+    const float2 hw2 = make_float2(hw, hw);
+    acc.c0 = fmaf(hw, tanh_approx(a.y1), acc.c0);
+    acc.c12 = __ffma2_rn(hw2, make_float2(tanh_approx(a.y23.x), tanh_approx(a.y23.y)), acc.c12);
+    acc.f01 = __ffma2_rn(hw2, make_float2(tanh_approx(a.y45.x), tanh_approx(a.y45.y)), acc.f01);
+    acc.f23 = __ffma2_rn(hw2, make_float2(tanh_approx(a.y67.x), tanh_approx(a.y67.y)), acc.f23);
+}
+
 // h(C_d, F, d): [C_d, F, d, sin d, cos d, sin 2d, cos 2d, sin 4d, cos 4d, sin 8d, cos 8d]
 // -> 16 ReLU -> 16 ReLU -> 3 (App. B: three layers, 16 hidden units, 4 frequencies).
 __device__ __forceinline__ void mlp_f32(const float *w, const float cd[3], const float f[4],
@@ -435,7 +467,8 @@ __device__ __forceinline__ void eval_field(const FieldView &fv, float p0, float 
         else byte_sums_lp<kPrec, kTaps<kGeo>>(tp, k);   // FP16 / BF16 appearance; density FP32
         const float wsum = tp.wv + (float)kPlaneSources<kGeo>;
         dens = dequant_density(k[0].x, wsum);
-        ya = app_arg_u8(k, wsum);
+        if constexpr (kPrec == 0) ya = app_arg_u8(k, wsum);
+        else ya = app_arg_u8_half(k, wsum);
     } else {
         float all[8];
         field_f32(fv, p0, p1, p2, all);
@@ -469,11 +502,19 @@ __device__ __forceinline__ void march_ray(const FieldView &fv, const OccView &oc
         ++r.neval;
         if (alpha > 0.0f) {
             ++r.napp;
-            composite(acc, alpha * r.T, ya);
+            if constexpr (kPrec == 0) composite(acc, alpha * r.T, ya);
+            else composite_tanh(acc, alpha * r.T, ya);
             r.T = r.T * (1.0f - alpha);
             if (early_term && r.T < t_term) { r.term = 1; break; }
         }
         ++wk.k;
+    }
+    if constexpr (kPrec != 0) {
+        const float h = 0.5f * (1.0f - r.T);
+        acc.c0 += h;
+        acc.c12 = __fadd2_rn(acc.c12, make_float2(h, h));
+        acc.f01 = __fadd2_rn(acc.f01, make_float2(h, h));
+        acc.f23 = __fadd2_rn(acc.f23, make_float2(h, h));
     }
     r.cd[0] = acc.c0; r.cd[1] = acc.c12.x; r.cd[2] = acc.c12.y;
     r.F[0] = acc.f01.x; r.F[1] = acc.f01.y; r.F[2] = acc.f23.x; r.F[3] = acc.f23.y;
