@@ -198,10 +198,12 @@ def test_dense_float_storage():
 # paper-scale scene (L = 512 in 16^3 blocks, R = 2048, four occupancy levels), 1920 x 1080,
 # in the launch configuration the benchmark times; sampled pixels are checked one by one.
 
-def test_paper_scale_sampled_pixels(paper):
+@pytest.mark.parametrize("W,H", [(1920, 1080), (1280, 720)])
+def test_paper_scale_sampled_pixels(paper, W, H):
+    """The 8 ring cameras at both of the workload's resolutions, each in one launch."""
     gs, osc = paper
-    cams = synth.config_cameras("paper")                    # 8 cameras, 1920 x 1080
-    W, H, step = 1920, 1080, 1 / 256
+    cams = synth.config_cameras("paper", W=W, H=H)          # 8 cameras
+    step = 1 / 256
     out = merf.render(gs, cams, W, H, step)
     aux = torch.zeros((cams.shape[0], H, W, merf.AUX_SIZE), device="cuda")
     out2 = merf.render(gs, cams, W, H, step, aux=aux)

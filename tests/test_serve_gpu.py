@@ -144,3 +144,40 @@ def test_cancellation(scenes):
     srv.close()
     assert st["cancelled"] == len(withdrawn) and st["completed"] == n - len(withdrawn)
     assert (st["pool_used_bytes"], st["admitted"], st["queued"]) == (0, 0, 0)
+
+
+def test_four_paper_scenes_mixed_resolutions_against_oracle(paper_scene):
+    """The serving workload at full size: four resident paper-scale scenes (seeds 1000-1003), orbit
+    cameras at 256x256, 640x360, 1280x720 and 1920x1080, all requests in flight together in FP16;
+    sampled pixels of every image against the FP64 oracle within the precision form's bars
+    (2e-3 per channel, PSNR > 50 dB)."""
+    import math
+    import oracle
+    scs = [paper_scene] + [synth.make_scene("paper", seed=synth.SEED_SCENE + k) for k in (1, 2, 3)]
+    srv = merf.Server([merf.Scene(s) for s in scs], pool_bytes=1 << 30, step=1 / 256, max_tiles_per_iter=16384,
+                      precision=merf.PREC_FP16)
+    rng = np.random.default_rng(5)
+    reqs = []
+    for k, (W, H) in enumerate([(256, 256), (640, 360), (1280, 720), (1920, 1080)] * 2):
+        r, az, el = rng.uniform(1.2, 3.0), rng.uniform(0, 2 * math.pi), math.radians(rng.uniform(-30, 30))
+        eye = [r * math.cos(el) * math.cos(az), r * math.cos(el) * math.sin(az), r * math.sin(el)]
+        cam = synth.camera_record(synth.look_at(eye), W, H)
+        out = _host(W, H).fill_(float("nan"))
+        s = (3 * k + 1) % 4
+        reqs.append((s, cam, W, H, out, srv.submit(s, cam, W, H, out)))
+    for *_, rid in reqs:
+        srv.wait(rid, timeout=300.0)
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(reqs) and st["peak_admitted"] >= 2
+    oscs = {}
+    for k, (s, cam, W, H, out, _) in enumerate(reqs):
+        osc = oscs.setdefault(s, oracle.OracleScene(scs[s]))
+        pix, lin = parity.pick_pixels(1, W, H, 250, seed=60 + k)
+        rgb = out.reshape(-1, 3)[torch.from_numpy(lin)].double().numpy()
+        lo, hi = parity.oracle_rgb(osc, cam[None], W, H, 1 / 256, pix=pix)
+        closer = np.where((np.abs(rgb - lo[:, 0:3]).max(1) <= np.abs(rgb - hi[:, 0:3]).max(1))[:, None],
+                          lo[:, 0:3], hi[:, 0:3])
+        err = np.abs(rgb - closer)
+        assert err.max() <= 2e-3, (k, W, H, err.max())
+        assert 10 * math.log10(1.0 / max(float(np.mean(err ** 2)), 1e-30)) > 50.0
