@@ -91,17 +91,7 @@ __device__ __forceinline__ void mlp_backward_f32(const float *w, const float cd[
     x[0] = cd[0]; x[1] = cd[1]; x[2] = cd[2];
     x[3] = f[0]; x[4] = f[1]; x[5] = f[2]; x[6] = f[3];
     x[7] = d[0]; x[8] = d[1]; x[9] = d[2];
-#pragma unroll
-    for (int l = 0; l < 4; ++l) {
-        const float fr = (float)(1 << l);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            float sn, cs;
-            sincosf(fr * d[k], &sn, &cs);
-            x[10 + 6 * l + k] = sn;
-            x[13 + 6 * l + k] = cs;
-        }
-    }
+    posenc(d, x);          // the forward's encoding, bit for bit
     const float *W0 = w, *b0 = w + 544, *W1 = w + 560, *b1 = w + 816, *W2 = w + 832;
 #pragma unroll
     for (int o = 0; o < 16; ++o) a1[o] = b0[o];

@@ -152,45 +152,97 @@ __device__ __forceinline__ void composite_tanh(Accum &acc, float w, const AppArg
     acc.f23 = __ffma2_rn(hw2, make_float2(tanh_approx(a.y67.x), tanh_approx(a.y67.y)), acc.f23);
 }
 
+// gamma(d) into x[10 .. 33]: sin and cos of 2^l d_k for l = 0..3 (App. B), at x[10 + 6 l + k] and
+// x[13 + 6 l + k].  The base frequency comes from sincosf; each doubled one from the previous by
+// sin 2a = (2 sin a) cos a and cos 2a = 1 - (2 sin a) sin a, one rounding each (2 sin a is exact).
+// A doubling about doubles the absolute error it inherits, which stays near 1e-6 after three.
+__device__ __forceinline__ void posenc(const float d[3], float *x)
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sincosf(d[k], &x[10 + k], &x[13 + k]);
+#pragma unroll
+    for (int l = 1; l < 4; ++l)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float s2 = 2.0f * x[10 + 6 * (l - 1) + k], c = x[13 + 6 * (l - 1) + k];
+            x[10 + 6 * l + k] = s2 * c;
+            x[13 + 6 * l + k] = fmaf(-s2, x[10 + 6 * (l - 1) + k], 1.0f);
+        }
+}
+
 // h(C_d, F, d): [C_d, F, d, sin d, cos d, sin 2d, cos 2d, sin 4d, cos 4d, sin 8d, cos 8d]
-// -> 16 ReLU -> 16 ReLU -> 3 (App. B: three layers, 16 hidden units, 4 frequencies).
+// -> 16 ReLU -> 16 ReLU -> 3 (App. B: three layers, 16 hidden units, 4 frequencies).  The 16-wide
+// layers run as packed FP32 pairs over the outputs (each lane rounds as fmaf does), with the
+// weights read 4 at a time from shared memory (w 16-byte aligned).
 __device__ __forceinline__ void mlp_f32(const float *w, const float cd[3], const float f[4],
                                         const float d[3], float out[3])
 {
-    float x[34];
-    x[0] = cd[0]; x[1] = cd[1]; x[2] = cd[2];
-    x[3] = f[0]; x[4] = f[1]; x[5] = f[2]; x[6] = f[3];
-    x[7] = d[0]; x[8] = d[1]; x[9] = d[2];
+    const float4 *W0 = reinterpret_cast<const float4 *>(w), *b0 = reinterpret_cast<const float4 *>(w + 544);
+    const float4 *W1 = reinterpret_cast<const float4 *>(w + 560), *b1 = reinterpret_cast<const float4 *>(w + 816);
+    const float *W2 = w + 832, *b2 = w + 880;
+    float2 h1[8], h2[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 b = b0[q];
+        h1[2 * q] = make_float2(b.x, b.y);
+        h1[2 * q + 1] = make_float2(b.z, b.w);
+    }
+    // layer 1, input row i of W0 times x_i; the encoding is produced level by level (as posenc
+    // does, same values, same row order) so that only one level's sines and cosines are live
+    auto row = [&](int i, float xi) {
+        const float2 x2 = make_float2(xi, xi);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 wq = W0[i * 4 + q];
+            h1[2 * q] = __ffma2_rn(x2, make_float2(wq.x, wq.y), h1[2 * q]);
+            h1[2 * q + 1] = __ffma2_rn(x2, make_float2(wq.z, wq.w), h1[2 * q + 1]);
+        }
+    };
+    row(0, cd[0]); row(1, cd[1]); row(2, cd[2]);
+    row(3, f[0]); row(4, f[1]); row(5, f[2]); row(6, f[3]);
+    row(7, d[0]); row(8, d[1]); row(9, d[2]);
+    float sn[3], cs[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sincosf(d[k], &sn[k], &cs[k]);
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
-        const float fr = (float)(1 << l);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            float s, c;
-            sincosf(fr * d[k], &s, &c);
-            x[10 + 6 * l + k] = s;
-            x[13 + 6 * l + k] = c;
+        for (int k = 0; k < 3; ++k) row(10 + 6 * l + k, sn[k]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) row(13 + 6 * l + k, cs[k]);
+        if (l < 3) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float s2 = 2.0f * sn[k], c = cs[k];
+                cs[k] = fmaf(-s2, sn[k], 1.0f);      // cos 2a = 1 - (2 sin a) sin a
+                sn[k] = s2 * c;                      // sin 2a = (2 sin a) cos a
+            }
         }
     }
-    const float *W0 = w, *b0 = w + 544, *W1 = w + 560, *b1 = w + 816, *W2 = w + 832, *b2 = w + 880;
-    float h1[16], h2[16];
 #pragma unroll
-    for (int o = 0; o < 16; ++o) h1[o] = b0[o];
+    for (int q = 0; q < 8; ++q) h1[q] = make_float2(fmaxf(h1[q].x, 0.0f), fmaxf(h1[q].y, 0.0f));
 #pragma unroll
-    for (int i = 0; i < 34; ++i)
+    for (int q = 0; q < 4; ++q) {
+        const float4 b = b1[q];
+        h2[2 * q] = make_float2(b.x, b.y);
+        h2[2 * q + 1] = make_float2(b.z, b.w);
+    }
 #pragma unroll
-        for (int o = 0; o < 16; ++o) h1[o] = fmaf(x[i], W0[i * 16 + o], h1[o]);
+    for (int i = 0; i < 16; ++i) {
+        const float a = (i & 1) ? h1[i >> 1].y : h1[i >> 1].x;
+        const float2 hi = make_float2(a, a);
 #pragma unroll
-    for (int o = 0; o < 16; ++o) { h1[o] = fmaxf(h1[o], 0.0f); h2[o] = b1[o]; }
-#pragma unroll
-    for (int i = 0; i < 16; ++i)
-#pragma unroll
-        for (int o = 0; o < 16; ++o) h2[o] = fmaf(h1[i], W1[i * 16 + o], h2[o]);
+        for (int q = 0; q < 4; ++q) {
+            const float4 wq = W1[i * 4 + q];
+            h2[2 * q] = __ffma2_rn(hi, make_float2(wq.x, wq.y), h2[2 * q]);
+            h2[2 * q + 1] = __ffma2_rn(hi, make_float2(wq.z, wq.w), h2[2 * q + 1]);
+        }
+    }
 #pragma unroll
     for (int o = 0; o < 3; ++o) out[o] = b2[o];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-        const float h = fmaxf(h2[i], 0.0f);
+        const float h = fmaxf((i & 1) ? h2[i >> 1].y : h2[i >> 1].x, 0.0f);
 #pragma unroll
         for (int o = 0; o < 3; ++o) out[o] = fmaf(h, W2[i * 3 + o], out[o]);
     }
@@ -399,17 +451,7 @@ __device__ __forceinline__ void mlp_umma(MlpUmma<kPrec> &ms, uint32_t &phase, co
     x[0] = cd[0]; x[1] = cd[1]; x[2] = cd[2];
     x[3] = f[0]; x[4] = f[1]; x[5] = f[2]; x[6] = f[3];
     x[7] = d[0]; x[8] = d[1]; x[9] = d[2];
-#pragma unroll
-    for (int l = 0; l < 4; ++l) {
-        const float fr = (float)(1 << l);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            float sn, cs;
-            sincosf(fr * d[k], &sn, &cs);
-            x[10 + 6 * l + k] = sn;
-            x[13 + 6 * l + k] = cs;
-        }
-    }
+    posenc(d, x);
 #pragma unroll
     for (int k = 34; k < 48; ++k) x[k] = 0.0f;
     // layer 1 (BF16: hi*hi + hi*lo, then the low parts replace the high ones for lo*hi)
@@ -574,7 +616,7 @@ template <int kPrec>
 struct MlpSmem;
 template <>
 struct MlpSmem<0> {
-    float w[kMlpParams];
+    alignas(16) float w[kMlpParams];
     __device__ __forceinline__ void init() {}
     __device__ __forceinline__ void load(const float *mlp)
     {
