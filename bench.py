@@ -566,7 +566,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_precision:
         precision = _precision_form(gs, prec_ref)
     differentiation = None
-    if rank == 0 and world == 1 and not args.no_precision:
+    if rank == 0 and world == 1 and not args.no_diff:
         differentiation = _differentiation()
     serving = None
     if rank == 0 and world == 1 and args.serve_requests > 0:
@@ -650,6 +650,7 @@ def main():
     ap.add_argument("--cams", type=int, default=N_CAMS, help="cameras per step (profiling cases)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-output measurement (profiling)")
     ap.add_argument("--no-precision", action="store_true", help="skip the FP16/BF16 comparison (profiling)")
+    ap.add_argument("--no-diff", action="store_true", help="skip the differentiation form (profiling)")
     ap.add_argument("--serve-requests", type=int, default=10000, help="requests of the serving run (0 = skip)")
     ap.add_argument("--no-variants", action="store_true", help="skip the grid-only comparison (profiling)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"],
