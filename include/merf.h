@@ -170,7 +170,9 @@ merf_status merf_scene_load(const char *path, void *stream, merf_scene **out);
 
 /* Render n_cams images of W x H pixels into `out` (device float32 [n_cams][H][W][3],
  * written, never read): C = C_d + h(C_d, F, d) per pixel (Sec. 2).  `cams` is a host array
- * of n_cams cameras.  Asynchronous on `stream`. */
+ * of n_cams cameras.  Asynchronous on `stream`, with no allocation and no synchronisation, so it
+ * can be captured into a CUDA graph; the cameras travel by value in the kernel parameters, so a
+ * captured graph replays the cameras it was captured with. */
 merf_status merf_render(const merf_scene *scene, const merf_camera *cams, int n_cams, int W,
                         int H, float *out, const merf_render_opts *opts, void *stream);
 

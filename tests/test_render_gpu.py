@@ -270,3 +270,26 @@ def test_traversal_bit_exact_dense_scene_and_random_orbits():
         m_o, _, n_o = oracle.trace(osc, cams, W, H, sc.cfg.step, words=40, decide_f32=True)
         np.testing.assert_array_equal(nlat.cpu().numpy(), n_o)
         np.testing.assert_array_equal(mask.cpu().numpy().view(np.uint32), m_o)
+
+
+@pytest.mark.parametrize("prec", [merf.PREC_FP32, merf.PREC_FP16])
+def test_render_is_graph_capturable(tiny, prec):
+    """merf_render allocates nothing and does not synchronise: it captures into a CUDA graph, and
+    a replay writes the same image as an eager call (the FP16 form includes the tcgen05 MLP)."""
+    gs, _ = tiny
+    cams = synth.config_cameras("tiny", W=40, H=24, n=3)
+    ref = merf.render(gs, cams, 40, 24, 1 / 64, precision=prec)
+    out = torch.zeros_like(ref)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        merf.render(gs, cams, 40, 24, 1 / 64, out=out, precision=prec)
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        merf.render(gs, cams, 40, 24, 1 / 64, out=out, precision=prec)
+    out.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    merf.check_device()
