@@ -293,3 +293,23 @@ def test_render_is_graph_capturable(tiny, prec):
     torch.cuda.synchronize()
     assert torch.equal(out, ref)
     merf.check_device()
+
+
+@pytest.mark.parametrize("n,W,H", [(1, 16384, 16), (1, 16, 16384), (32, 8192, 7629)])
+def test_maximum_sizes(tiny, n, W, H):
+    """The largest accepted images (16384 pixels on a side) and one call close to the 2e9-ray limit
+    (32 cameras x 8192 x 7629 = 1.9999e9 rays, a 24 GB output): sampled pixels, including the
+    corners of the last camera, against the oracle."""
+    gs, osc = tiny
+    cams = synth.sphere_cameras(n, W, H, radius=2.5, seed=71)
+    out = merf.render(gs, cams, W, H, 1 / 64)
+    torch.cuda.synchronize()
+    pix, lin = parity.pick_pixels(n, W, H, 400, seed=72)
+    last = np.array([[n - 1, 0, 0], [n - 1, W - 1, 0], [n - 1, 0, H - 1], [n - 1, W - 1, H - 1]], np.int32)
+    pix = np.concatenate([pix, last]).astype(np.int32)
+    lin = (pix[:, 0].astype(np.int64) * H + pix[:, 2]) * W + pix[:, 1]
+    rgb = out.reshape(-1, 3)[torch.from_numpy(lin).cuda()].double().cpu().numpy()
+    del out
+    torch.cuda.empty_cache()
+    lo, hi = parity.oracle_rgb(osc, cams, W, H, 1 / 64, pix=pix)
+    assert parity.max_err(rgb, lo, hi).max() <= parity.RGB_TOL
