@@ -37,10 +37,28 @@ struct BackwardParams {
     CamBlock cams;
 };
 
-__device__ __forceinline__ void atomic_add8(float *dst, const float g[8], float w)
+// Add w g at texel `key` of `base` (8 floats per texel; key < 0: nothing), merging with the
+// horizontally adjacent pixel (lane ^ 1) when both add to the same texel: the even lane adds the
+// pair's sum and the odd lane skips its atomics.  m: the lanes executing this call together.
+__device__ __forceinline__ void atomic_add8_pair(float *base, long long key, const float g[8], float w, unsigned m)
 {
-    atomicAdd(reinterpret_cast<float4 *>(dst), make_float4(w * g[0], w * g[1], w * g[2], w * g[3]));
-    atomicAdd(reinterpret_cast<float4 *>(dst + 4), make_float4(w * g[4], w * g[5], w * g[6], w * g[7]));
+    const int lane = threadIdx.x & 31;
+    const long long pk = __shfl_xor_sync(m, key, 1);
+    const bool merge = key >= 0 && pk == key && ((m >> (lane ^ 1)) & 1u);
+    float v[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) v[c] = w * g[c];
+    if (__any_sync(m, merge)) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float o = __shfl_xor_sync(m, v[c], 1);
+            if (merge) v[c] += o;
+        }
+    }
+    if (key < 0 || (merge && (lane & 1))) return;
+    float *dst = base + key * 8;
+    atomicAdd(reinterpret_cast<float4 *>(dst), make_float4(v[0], v[1], v[2], v[3]));
+    atomicAdd(reinterpret_cast<float4 *>(dst + 4), make_float4(v[4], v[5], v[6], v[7]));
 }
 
 // Add g (per channel) times the interpolation weights of p to the dense grid and plane gradients.
@@ -54,12 +72,14 @@ __device__ __forceinline__ void scatter_f32(const FieldView &fv, float *g_grid, 
     texel_coord(p0, sL, hL, L, x0, fx);
     texel_coord(p1, sL, hL, L, y0, fy);
     texel_coord(p2, sL, hL, L, z0, fz);
+    const unsigned m = __activemask();
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
         const float w = (cx ? fx : 1.0f - fx) * (cy ? fy : 1.0f - fy) * (cz ? fz : 1.0f - fz);
         const size_t gi = ((size_t)(z0 + cz) * L + (y0 + cy)) * L + (x0 + cx);
-        if (w != 0.0f && MERF_IN_RANGE(gi, (long long)L * L * L, kBadDense)) atomic_add8(g_grid + gi * 8, g, w);
+        const bool ok = w != 0.0f && MERF_IN_RANGE(gi, (long long)L * L * L, kBadDense);
+        atomic_add8_pair(g_grid, ok ? (long long)gi : -1LL, g, w, m);
     }
     const float sR = (float)fv.R * 0.25f;
     const int hR = fv.R >> 1, R = fv.R;
@@ -76,7 +96,8 @@ __device__ __forceinline__ void scatter_f32(const FieldView &fv, float *g_grid, 
             const int cu = c & 1, cv = c >> 1;
             const float w = (cu ? fu[ca] : 1.0f - fu[ca]) * (cv ? fu[ra] : 1.0f - fu[ra]);
             const size_t pi = ((size_t)q * R + u0[ra] + cv) * R + u0[ca] + cu;
-            if (w != 0.0f && MERF_IN_RANGE(pi, 3LL * R * R, kBadDense)) atomic_add8(g_planes + pi * 8, g, w);
+            const bool ok = w != 0.0f && MERF_IN_RANGE(pi, 3LL * R * R, kBadDense);
+            atomic_add8_pair(g_planes, ok ? (long long)pi : -1LL, g, w, m);
         }
     }
 }
