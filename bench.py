@@ -605,7 +605,10 @@ def run_ours(args):
                                          and args.precision == "fp32" else None),
                              "kernel": f"render_kernel<0,{prec},1,0> ({args.precision.upper()})",
                              "kernel_ms": mean_kern_ms,
-                             "peak_source": peak_src},
+                             "peak_source": peak_src,
+                             "note": "algorithmic gather bytes (no reuse) over the measured HBM copy peak, as "
+                                     "the metric defines its roofline; L1/L2 serve all but 0.3 % of the "
+                                     "gather, and the binding limit is instruction issue (roofline_issue)"},
                 "gpu_launches": args.steps,
                 "e2e": e2e, "clocks": ck}
         if cpu is not None:
