@@ -118,6 +118,8 @@ typedef struct merf_scene merf_scene;  /* opaque; owns device memory */
  *                                          (NULL allowed when plane_res is 0: grid only)
  *   occ_levels  n_occ_levels pointers to uint8 [N][N][N], non-zero = occupied
  *   mlp_weights float32 [883]: W0[34][16], b0[16], W1[16][16], b1[16], W2[16][3], b2[3]
+ * On the device the weights become one 11,776-byte block: the FP32 weights, then the FP16 and
+ * BF16 forms packed as the tensor cores read them (built by a kernel on `stream`).
  * The layout is validated (ids in range, every coarse occupancy cell that is empty has
  * only empty children) before anything is allocated.  Returns MERF_ERR_OOM without
  * touching the device if the scene exceeds the budget set by merf_set_device_budget.
@@ -138,7 +140,7 @@ merf_status merf_scene_upload_dense(const merf_scene_desc *desc, const float *gr
 /* Release a scene (NULL is ignored).  Synchronises the device first. */
 void merf_scene_free(merf_scene *scene);
 
-/* Device bytes held by a scene. */
+/* Device bytes held by a scene (its arrays plus the 11,776-byte MLP block). */
 size_t merf_scene_device_bytes(const merf_scene *scene);
 
 /* Scene files: one baked scene as a raw binary file -- the arrays merf_scene_upload(_dense) takes,
@@ -224,7 +226,8 @@ merf_status merf_trace(const merf_scene *scene, const merf_camera *cams, int n_c
 
 /* Replace the parameters of a dense float scene (storage MERF_STORAGE_F32_DENSE) with new values
  * from device memory: grid float32 [L][L][L][8], planes float32 [3][R][R][8], mlp float32 [883]
- * (device-to-device copies on `stream`; no allocation).  Used between optimisation steps. */
+ * (device-to-device copies on `stream`, and the MLP's 16-bit forms rebuilt by a kernel there; no
+ * allocation).  Used between optimisation steps. */
 merf_status merf_scene_set_dense(merf_scene *scene, const float *d_grid, const float *d_planes,
                                  const float *d_mlp, void *stream);
 

@@ -106,6 +106,27 @@ merf_status check_occupancy(const merf_scene_desc *d, const uint8_t *const *occ)
     return MERF_OK;
 }
 
+static_assert(merf::kMlpBlockBytes == 11776, "the MLP block size merf.h states");
+
+// Fill the FP16 and BF16 forms of a scene's MLP block from its FP32 weights (one CTA).
+__global__ void __launch_bounds__(merf::kThreads) mlp_pack_kernel(uint8_t *block)
+{
+    const float *w = reinterpret_cast<const float *>(block);
+    merf::mlp_pack16<1>(*reinterpret_cast<merf::MlpWeights16<1> *>(block + merf::kMlpOffF16), w);
+    merf::mlp_pack16<2>(*reinterpret_cast<merf::MlpWeights16<2> *>(block + merf::kMlpOffBf16), w);
+}
+
+// The MLP block from n FP32 weights at src (host or device memory, `kind`): zero it, copy the
+// weights in, pack the 16-bit forms; all on `st`.
+cudaError_t put_mlp_block(void *block, const float *src, cudaMemcpyKind kind, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(block, 0, merf::kMlpBlockBytes, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(block, src, sizeof(float) * MERF_MLP_PARAMS, kind, st);
+    if (e != cudaSuccess) return e;
+    mlp_pack_kernel<<<1, merf::kThreads, 0, st>>>((uint8_t *)block);
+    return cudaGetLastError();
+}
+
 void free_scene_memory(merf_scene *s)
 {
     cudaFree(s->index_grid);
@@ -121,7 +142,7 @@ merf_status upload_common(const merf_scene_desc *desc, const void *grid, size_t 
                           void *stream, merf_scene **out)
 {
     size_t occ_bytes[MERF_MAX_OCC_LEVELS] = {};
-    size_t total = grid_bytes + plane_bytes + index_bytes + sizeof(float) * MERF_MLP_PARAMS;
+    size_t total = grid_bytes + plane_bytes + index_bytes + merf::kMlpBlockBytes;
     for (int l = 0; l < desc->n_occ_levels; ++l) {
         occ_bytes[l] = (size_t)desc->occ_res[l] * desc->occ_res[l] * desc->occ_res[l];
         total += occ_bytes[l];
@@ -136,7 +157,7 @@ merf_status upload_common(const merf_scene_desc *desc, const void *grid, size_t 
     std::vector<Item> items = {{&s->atlas, grid, grid_bytes},
                                {&s->planes, planes, plane_bytes},
                                {&s->index_grid, index_grid, index_bytes},
-                               {&s->mlp, mlp, sizeof(float) * MERF_MLP_PARAMS}};
+                               {&s->mlp, nullptr, merf::kMlpBlockBytes}};
     for (int l = 0; l < desc->n_occ_levels; ++l) items.push_back({&s->occ[l], occ[l], occ_bytes[l]});
     for (auto &it : items) {
         if (it.n == 0) continue;
@@ -148,7 +169,8 @@ merf_status upload_common(const merf_scene_desc *desc, const void *grid, size_t 
             return fail(e == cudaErrorMemoryAllocation ? MERF_ERR_OOM : MERF_ERR_CUDA,
                         "cudaMalloc(%zu): %s", it.n, cudaGetErrorString(e));
         }
-        e = cudaMemcpyAsync(*it.dst, it.src, it.n, cudaMemcpyHostToDevice, st);
+        e = it.dst == &s->mlp ? put_mlp_block(s->mlp, mlp, cudaMemcpyHostToDevice, st)
+                              : cudaMemcpyAsync(*it.dst, it.src, it.n, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) {
             free_scene_memory(s);
             delete s;
@@ -680,7 +702,7 @@ merf_status merf_scene_set_dense(merf_scene *scene, const float *d_grid, const f
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(scene->planes, d_planes, 3 * R * R * 8 * sizeof(float), cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(scene->mlp, d_mlp, MERF_MLP_PARAMS * sizeof(float), cudaMemcpyDeviceToDevice, s);
+        e = put_mlp_block(scene->mlp, d_mlp, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return fail(MERF_ERR_CUDA, "set_dense: %s", cudaGetErrorString(e));
     return ok();
 }

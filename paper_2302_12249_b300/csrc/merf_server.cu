@@ -6,7 +6,8 @@
 // serve_kernel.  The kernel keeps one CTA per resident slot (SMs x CTAs per SM) and pulls tiles
 // from the work list with an atomic counter, so long and short requests balance across SMs.  Each
 // CTA renders its tile with the same march and deferred MLP as render_kernel; the MLP weights in
-// shared memory are reloaded when a tile belongs to another scene.  There is no device-side wait.
+// shared memory are fetched again (one bulk copy) when a tile belongs to another scene.  The only
+// device-side waits are the CTA's own bounded waits on its copies and MMAs.
 // The scheduler's two iteration slots are two work buffers and two graphs on one compute stream;
 // a finished request's image is copied to host memory on a second stream, and the copy's event
 // completes the request.
@@ -48,7 +49,7 @@ __global__ void __launch_bounds__(kThreads, (kMinBlocks<0, kPrec>)) serve_kernel
     ms.init();                          // the first barrier below publishes it
     const int n_tiles = P.work->n_tiles;
     int cur_scene = -1;
-    uint32_t phase = 0;
+    uint32_t phase = 0, wphase = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(P.counter, 1);
@@ -58,9 +59,11 @@ __global__ void __launch_bounds__(kThreads, (kMinBlocks<0, kPrec>)) serve_kernel
         const uint32_t code = P.work->tiles[tile];
         const ServeReq &R = P.work->req[code >> 20];
         const int sc = R.scene;
-        if (sc != cur_scene) {          // uniform across the CTA
-            ms.load(P.scenes[sc].mlp);
-            __syncthreads();
+        // Uniform across the CTA.  The barriers since the last tile's MLP ordered every read of
+        // the old weights before this copy.
+        const bool fetched = sc != cur_scene;
+        if (fetched) {
+            ms.fetch(P.scenes[sc].mlp);     // lands while the rays march
             cur_scene = sc;
         }
         const int tl = (int)(code & 0xfffffu);
@@ -73,6 +76,7 @@ __global__ void __launch_bounds__(kThreads, (kMinBlocks<0, kPrec>)) serve_kernel
         if (inside)
             march_ray<0, kPrec, kGeo>(P.scenes[sc].fv, P.scenes[sc].occ, R.cam, i, j, P.step, P.t_term, P.early_term, r);
         float h[3];
+        if (fetched) ms.wait(wphase);
         deferred_mlp<kPrec>(ms, phase, r, inside, h);
         if (inside) {
             float *o = P.pool + R.out_off + ((size_t)j * R.W + i) * 3;

@@ -5,11 +5,11 @@
 // texels of each evaluated sample, all eight channels interpolated in one tap-major pass (the
 // appearance values enter the result only when the sample's opacity is non-zero, Sec. 5),
 // front-to-back compositing of C_d and F with early termination (Eq. 1, Eq. 2, Sec. 5), and
-// finally the deferred MLP h(C_d, F, d) (Sec. 2, App. B), whose 883 weights are staged once per
-// CTA in shared memory (FP32: per pixel on the CUDA cores; FP16 / BF16: the CTA's 128 pixels as
-// one M = 128 tcgen05.mma tile, accumulated in tensor memory).  A warp covers an 8 x 4 pixel
-// tile and a CTA a 16 x 8 tile, so neighbouring rays walk
-// neighbouring texels together and share L1 lines.  Template parameters select the storage
+// finally the deferred MLP h(C_d, F, d) (Sec. 2, App. B), whose 883 weights reach each CTA's
+// shared memory by one bulk (TMA) copy that overlaps the march (FP32: per pixel on the CUDA
+// cores; FP16 / BF16: the CTA's 128 pixels as one M = 128 tcgen05.mma tile, accumulated in
+// tensor memory).  A warp covers an 8 x 4 pixel tile and a CTA a 16 x 8 tile, so neighbouring
+// rays walk neighbouring texels together and share L1 lines.  Template parameters select the storage
 // (uint8 block-sparse / dense float), the precision (FP32 / FP16 / BF16 appearance arithmetic
 // and MLP), the gather geometry (the paper's / grid-only / run-time strides) and the contraction
 // (contract_pi, or the spherical ablation's dense march).
@@ -262,20 +262,47 @@ __device__ __forceinline__ void mlp_f32(const float *w, const float cd[3], const
 constexpr int kTmemCols = 32;               // the smallest TMEM allocation; N = 16 uses 16
 constexpr int kWaitPolls = 1 << 22;         // bounded wait for an MMA group (microseconds in practice)
 
+// The weights of one 16-bit form as the MMAs read them, built once per scene in device memory and
+// brought to shared memory by one bulk copy: the B operands W0^T, W1^T, W2^T as K-major 16-bit
+// tiles (each with its BF16 low part in [1]), then the FP32 biases.
+template <int kPrec>
+struct alignas(128) MlpWeights16 {
+    static constexpr int kParts = kPrec == 2 ? 2 : 1;     // [1]: BF16 low parts
+    uint8_t w0[kParts][16 * 48 * 2];                       // W0^T [n][k], k >= 34 zero
+    uint8_t w1[kParts][16 * 16 * 2];                       // W1^T
+    uint8_t w2[kParts][16 * 16 * 2];                       // W2^T, rows n >= 3 zero
+    float b0[16], b1[16], b2[4];                           // b2[3] zero
+};
+
 template <int kPrec>
 struct MlpUmma {
-    static constexpr int kParts = kPrec == 2 ? 2 : 1;     // [1]: BF16 low parts
+    static constexpr int kParts = MlpWeights16<kPrec>::kParts;
     // A operand.  Layer 1: the 128 x 48 rows (BF16: the high parts, then the low parts in a
     // second round).  Layers 2 and 3: the 128 x 16 rows at 0, BF16 low parts at kLoOffset.
     alignas(128) uint8_t x[128 * 48 * 2];
-    alignas(128) uint8_t w0[kParts][16 * 48 * 2];          // B: W0^T [n][k], K-major
-    alignas(128) uint8_t w1[kParts][16 * 16 * 2];          // W1^T
-    alignas(128) uint8_t w2[kParts][16 * 16 * 2];          // W2^T, rows n >= 3 zero
-    float b0[16], b1[16], b2[4];
-    alignas(8) uint64_t mbar;
+    MlpWeights16<kPrec> wt;
+    alignas(8) uint64_t mbar;                              // MMA completion
     uint32_t tmem;                                         // the CTA's accumulator columns
 };
 constexpr int kLoOffset = 128 * 16 * 2;
+
+// A scene's MLP block in device memory: the 883 FP32 weights padded to 884 (16 bytes), then the
+// FP16 and the BF16 forms, each at a 128-byte boundary.  Each form is one bulk copy: 16-byte
+// aligned at both ends and a multiple of 16 bytes long.
+constexpr int kMlpF32Floats = 884;
+constexpr size_t kMlpOffF16 = 3584;
+constexpr size_t kMlpOffBf16 = kMlpOffF16 + sizeof(MlpWeights16<1>);
+constexpr size_t kMlpBlockBytes = kMlpOffBf16 + sizeof(MlpWeights16<2>);
+static_assert(kMlpF32Floats >= kMlpParams && kMlpF32Floats * 4 % 16 == 0 && kMlpF32Floats * 4 <= kMlpOffF16,
+              "FP32 form: one 16-byte multiple before the FP16 form");
+static_assert(kMlpOffF16 % 128 == 0 && kMlpOffBf16 % 128 == 0, "forms at 128-byte boundaries");
+static_assert(sizeof(MlpWeights16<1>) % 16 == 0 && sizeof(MlpWeights16<2>) % 16 == 0, "bulk-copy sizes");
+
+template <int kPrec>
+__host__ __device__ constexpr size_t mlp_form_offset()
+{
+    return kPrec == 0 ? 0 : kPrec == 1 ? kMlpOffF16 : kMlpOffBf16;
+}
 
 template <int kPrec>
 __device__ __forceinline__ uint32_t pack16(float lo, float hi)
@@ -305,7 +332,7 @@ __device__ __forceinline__ uint32_t pack16_lo(float lo, float hi)
 
 // One 16-bit element pair (k, k + 1) of row n of a K-major B tile, with its BF16 low part.
 template <int kPrec, int K, int kBytes>
-__device__ __forceinline__ void put_w(uint8_t (&w)[MlpUmma<kPrec>::kParts][kBytes], int n, int k, float a, float b)
+__device__ __forceinline__ void put_w(uint8_t (&w)[MlpWeights16<kPrec>::kParts][kBytes], int n, int k, float a, float b)
 {
     const int off = kmajor_offset(n, k, K);
     *reinterpret_cast<uint32_t *>(&w[0][off]) = pack16<kPrec>(a, b);
@@ -335,27 +362,28 @@ __device__ __forceinline__ void mlp_umma_fini(MlpUmma<kPrec> &ms)
     }
 }
 
-// Stage the scene's FP32 weights as K-major 16-bit B tiles (whole CTA, before a barrier).
+// Pack the FP32 weights w (layout of App. B: W0 [34][16], b0, W1 [16][16], b1, W2 [16][3], b2)
+// into one 16-bit form (the threads of one CTA).
 template <int kPrec>
-__device__ __forceinline__ void mlp_umma_load(MlpUmma<kPrec> &ms, const float *w)
+__device__ __forceinline__ void mlp_pack16(MlpWeights16<kPrec> &o, const float *w)
 {
     const float *W0 = w, *B0 = w + 544, *W1 = w + 560, *B1 = w + 816, *W2 = w + 832, *B2 = w + 880;
     for (int e = threadIdx.x; e < 16 * 24; e += kThreads) {
         const int n = e / 24, k = 2 * (e % 24);
         const float a = k < 34 ? __ldg(W0 + k * 16 + n) : 0.0f;
         const float b = k + 1 < 34 ? __ldg(W0 + (k + 1) * 16 + n) : 0.0f;
-        put_w<kPrec, 48>(ms.w0, n, k, a, b);
+        put_w<kPrec, 48>(o.w0, n, k, a, b);
     }
     for (int e = threadIdx.x; e < 16 * 8; e += kThreads) {
         const int n = e / 8, k = 2 * (e % 8);
-        put_w<kPrec, 16>(ms.w1, n, k, __ldg(W1 + k * 16 + n), __ldg(W1 + (k + 1) * 16 + n));
+        put_w<kPrec, 16>(o.w1, n, k, __ldg(W1 + k * 16 + n), __ldg(W1 + (k + 1) * 16 + n));
         const float a = n < 3 ? __ldg(W2 + k * 3 + n) : 0.0f, b = n < 3 ? __ldg(W2 + (k + 1) * 3 + n) : 0.0f;
-        put_w<kPrec, 16>(ms.w2, n, k, a, b);
+        put_w<kPrec, 16>(o.w2, n, k, a, b);
     }
     for (int e = threadIdx.x; e < 16; e += kThreads) {
-        ms.b0[e] = __ldg(B0 + e);
-        ms.b1[e] = __ldg(B1 + e);
-        if (e < 4) ms.b2[e] = e < 3 ? __ldg(B2 + e) : 0.0f;
+        o.b0[e] = __ldg(B0 + e);
+        o.b1[e] = __ldg(B1 + e);
+        if (e < 4) o.b2[e] = e < 3 ? __ldg(B2 + e) : 0.0f;
     }
 }
 
@@ -424,7 +452,7 @@ __device__ __forceinline__ void acc_row(uint32_t tmem, bool ok, float *acc)
 
 // A 16-input layer (2 or 3): D = H W, BF16 as hi*hi + lo*hi + hi*lo in one round.
 template <int kPrec, int nc>
-__device__ __forceinline__ void layer16(MlpUmma<kPrec> &ms, uint32_t &phase, uint8_t (&w)[MlpUmma<kPrec>::kParts][512],
+__device__ __forceinline__ void layer16(MlpUmma<kPrec> &ms, uint32_t &phase, uint8_t (&w)[MlpWeights16<kPrec>::kParts][512],
                                         const float h[16], float *acc)
 {
     put_row<kPrec, 16, false>(ms.x, h);
@@ -455,7 +483,7 @@ __device__ __forceinline__ void mlp_umma(MlpUmma<kPrec> &ms, uint32_t &phase, co
 #pragma unroll
     for (int k = 34; k < 48; ++k) x[k] = 0.0f;
     // layer 1 (BF16: hi*hi + hi*lo, then the low parts replace the high ones for lo*hi)
-    const uint32_t xa = smem_addr(ms.x), wh = smem_addr(ms.w0[0]), wl = smem_addr(ms.w0[MlpUmma<kPrec>::kParts - 1]);
+    const uint32_t xa = smem_addr(ms.x), wh = smem_addr(ms.wt.w0[0]), wl = smem_addr(ms.wt.w0[MlpUmma<kPrec>::kParts - 1]);
     const uint32_t tm = ms.tmem;
     put_row<kPrec, 48, false>(ms.x, x);
     bool ok = umma_round(ms, phase, [&] {
@@ -469,16 +497,16 @@ __device__ __forceinline__ void mlp_umma(MlpUmma<kPrec> &ms, uint32_t &phase, co
     float h[16];
     acc_row<16>(tm, ok, h);
 #pragma unroll
-    for (int o = 0; o < 16; ++o) h[o] = fmaxf(h[o] + ms.b0[o], 0.0f);
+    for (int o = 0; o < 16; ++o) h[o] = fmaxf(h[o] + ms.wt.b0[o], 0.0f);
     float h2[16];
-    layer16<kPrec, 16>(ms, phase, ms.w1, h, h2);
+    layer16<kPrec, 16>(ms, phase, ms.wt.w1, h, h2);
 #pragma unroll
-    for (int o = 0; o < 16; ++o) h2[o] = fmaxf(h2[o] + ms.b1[o], 0.0f);
+    for (int o = 0; o < 16; ++o) h2[o] = fmaxf(h2[o] + ms.wt.b1[o], 0.0f);
     float y[4];
-    layer16<kPrec, 4>(ms, phase, ms.w2, h2, y);
-    out[0] = y[0] + ms.b2[0];
-    out[1] = y[1] + ms.b2[1];
-    out[2] = y[2] + ms.b2[2];
+    layer16<kPrec, 4>(ms, phase, ms.wt.w2, h2, y);
+    out[0] = y[0] + ms.wt.b2[0];
+    out[1] = y[1] + ms.wt.b2[1];
+    out[2] = y[2] + ms.wt.b2[2];
 }
 
 __device__ __forceinline__ void pixel_of_thread(int &i, int &j)
@@ -611,24 +639,54 @@ __device__ __forceinline__ void ray_state_init(RayState &r)
     r.nlat = r.neval = r.napp = r.term = 0;
 }
 
-// Shared-memory weights of the deferred MLP for one precision.
+// Shared-memory weights of the deferred MLP for one precision, staged by one bulk (TMA) copy of
+// the form from the scene's MLP block.  Thread 0 issues the copy (fetch) when the CTA starts or
+// changes scene; it lands while the rays march, and every thread waits for it (wait) just before
+// the MLP.  Each fetch completes one phase of `wbar`.
+template <int kPrec>
+struct MlpStage {
+    alignas(8) uint64_t wbar;
+    __device__ __forceinline__ void init_bar()
+    {
+        if (threadIdx.x == 0) {
+            mbar_init(&wbar, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+    }
+    // Thread 0; every thread's earlier reads of the destination are ordered before it by a barrier.
+    __device__ __forceinline__ void copy(void *dst, const float *mlp, uint32_t bytes)
+    {
+        if (threadIdx.x == 0) {
+            fence_async_smem();
+            bulk_g2s(dst, reinterpret_cast<const char *>(mlp) + mlp_form_offset<kPrec>(), bytes, &wbar);
+        }
+    }
+    // All threads; a wait that gives up is recorded in the device status word.
+    __device__ __forceinline__ void wait(uint32_t &wphase)
+    {
+        if (!mbar_wait(&wbar, wphase, kWaitPolls)) set_status(kWaitTimeout);
+        wphase ^= 1u;
+    }
+};
+
 template <int kPrec>
 struct MlpSmem;
 template <>
-struct MlpSmem<0> {
-    alignas(16) float w[kMlpParams];
-    __device__ __forceinline__ void init() {}
-    __device__ __forceinline__ void load(const float *mlp)
-    {
-        for (int t = threadIdx.x; t < kMlpParams; t += kThreads) w[t] = __ldg(mlp + t);
-    }
+struct MlpSmem<0> : MlpStage<0> {
+    alignas(16) float w[kMlpF32Floats];
+    __device__ __forceinline__ void init() { init_bar(); }                       // before a barrier
+    __device__ __forceinline__ void fetch(const float *mlp) { copy(w, mlp, sizeof w); }
     __device__ __forceinline__ void fini() {}
 };
 template <int kPrec>
-struct MlpSmem {
+struct MlpSmem : MlpStage<kPrec> {
     MlpUmma<kPrec> tc;
-    __device__ __forceinline__ void init() { mlp_umma_init<kPrec>(tc); }      // before the first barrier
-    __device__ __forceinline__ void load(const float *mlp) { mlp_umma_load<kPrec>(tc, mlp); }
+    __device__ __forceinline__ void init()                                       // before a barrier
+    {
+        this->init_bar();
+        mlp_umma_init<kPrec>(tc);
+    }
+    __device__ __forceinline__ void fetch(const float *mlp) { this->copy(&tc.wt, mlp, sizeof tc.wt); }
     __device__ __forceinline__ void fini() { mlp_umma_fini<kPrec>(tc); }      // all threads, at the end
 };
 
@@ -658,8 +716,8 @@ __global__ void __launch_bounds__(kThreads, (kMinBlocks<kStorage, kPrec>)) rende
 {
     __shared__ MlpSmem<kPrec> ms;
     ms.init();
-    ms.load(P.mlp);
     __syncthreads();
+    ms.fetch(P.mlp);                   // lands while the rays march
 
     int i, j;
     pixel_of_thread(i, j);
@@ -674,7 +732,8 @@ __global__ void __launch_bounds__(kThreads, (kMinBlocks<kStorage, kPrec>)) rende
             march_ray_sph<kStorage, kGeo>(P.fv, P.occ, P.cams.m[cl], i, j, P.step, P.t_term, P.early_term, r);
     }
     float h[3];
-    uint32_t phase = 0;
+    uint32_t phase = 0, wphase = 0;
+    ms.wait(wphase);
     deferred_mlp<kPrec>(ms, phase, r, inside, h);
     if (inside) {
         const size_t pix = ((size_t)(P.cam0 + cl) * P.H + j) * P.W + i;

@@ -55,7 +55,8 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr)
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-// Generic-proxy shared-memory writes become visible to the tensor cores' (async proxy) reads.
+// Orders this thread's generic-proxy shared-memory accesses before later async-proxy ones: operand
+// writes before the tensor cores read them, earlier reads before a bulk copy overwrites them.
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // D (TMEM) = A B (+ D if accumulate); one thread issues it for the CTA.
@@ -91,6 +92,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, int l
                      : "r"(smem_addr(mbar)), "r"(parity)
                      : "memory");
     return done != 0;
+}
+
+// One bulk (TMA, untiled) copy of `bytes` from global to shared memory, completing on `mbar`
+// (count 1: this thread's arrival plus the bytes).  Both addresses 16-byte aligned, bytes a
+// multiple of 16.  One thread calls it.
+__device__ __forceinline__ void bulk_g2s(void *smem_dst, const void *gsrc, uint32_t bytes, uint64_t *mbar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(smem_dst)),
+                 "l"(gsrc), "r"(bytes), "r"(smem_addr(mbar))
+                 : "memory");
 }
 
 // Columns col .. col + 15 of this thread's TMEM lane (warp w: lanes 32 w + lane).
