@@ -150,10 +150,18 @@ template <int kGeo>
 constexpr int kPlaneSources = kGeo == kGeoGridOnly ? 0 : 3;     // planes that add to the grid
 template <int kGeo>
 constexpr int kTaps = 8 + 4 * kPlaneSources<kGeo>;               // texels per sample
+// Offset type of the gather and occupancy indices.  The paper's geometry is chosen only for
+// scenes whose atlas holds at most 2^32 / 17^3 blocks and whose finest occupancy level is at
+// most 1024^3 cells, so every offset fits 32 bits there; other geometries use 64.
+template <int kGeo>
+struct GatherIndex { using T = size_t; };
+template <>
+struct GatherIndex<kGeoPaper> { using T = uint32_t; };
 
 template <int kGeo>
 __device__ __forceinline__ void gather_u8(const FieldView &fv, float p0, float p1, float p2, Taps &t)
 {
+    using Idx = typename GatherIndex<kGeo>::T;
     const int L = kGeo == kGeoPaper ? 512 : fv.L;
     const int sh = kGeo == kGeoPaper ? 4 : fv.log2B;
     const int nb = kGeo == kGeoPaper ? 32 : fv.nb;
@@ -169,7 +177,7 @@ __device__ __forceinline__ void gather_u8(const FieldView &fv, float p0, float p
     const int ent = MERF_IN_RANGE(gi, nb * nb * nb, kBadIndexGrid) ? __ldg(fv.index_grid + gi) : -1;
     if (ent >= 0) {
         const int lx = x0 & msk, ly = y0 & msk, lz = z0 & msk;
-        const size_t ai = ((size_t)(ent & 0xffffff) * B1 + lz) * B1 * B1 + ly * B1 + lx;
+        const Idx ai = ((Idx)(ent & 0xffffff) * B1 + lz) * B1 * B1 + ly * B1 + lx;
         // bounds-checked build: the farthest corner is ai + B1^2 + B1 + 1
         if (!MERF_IN_RANGE(ai + B1 * B1 + B1 + 1, (long long)fv.n_blocks * B1 * B1 * B1, kBadAtlas)) {
 #pragma unroll
@@ -215,7 +223,7 @@ grid_done:;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         const int ca = q == 0 ? 1 : 0, ra = q == 2 ? 1 : 2;
-        const size_t pi = ((size_t)q * Rp + u0[ra]) * Rp + u0[ca];
+        const Idx pi = ((Idx)q * Rp + u0[ra]) * Rp + u0[ca];
         if (!MERF_IN_RANGE(pi + Rp + 1, 3LL * Rp * Rp, kBadPlane)) {
             t.v[8 + 4 * q + 0] = t.v[8 + 4 * q + 1] = t.v[8 + 4 * q + 2] = t.v[8 + 4 * q + 3] = make_uint2(0u, 0u);
             continue;

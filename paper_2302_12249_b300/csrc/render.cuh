@@ -562,7 +562,7 @@ __device__ __forceinline__ void march_ray(const FieldView &fv, const OccView &oc
     acc.c12 = acc.f01 = acc.f23 = make_float2(0.0f, 0.0f);
     for (;;) {
         float p0, p1, p2;
-        if (!wk.next_sample(occ, p0, p1, p2)) break;
+        if (!wk.next_sample<typename GatherIndex<kGeo>::T>(occ, p0, p1, p2)) break;
         float dens;
         AppArg ya;
         eval_field<kStorage, kPrec, kGeo>(fv, p0, p1, p2, dens, ya);

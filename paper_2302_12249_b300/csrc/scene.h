@@ -52,10 +52,14 @@ inline void scene_views(const merf_scene *s, FieldView &fv, OccView &occ)
     }
 }
 
-// True when the gather may use the kernels compiled for the paper's geometry (kGeoPaper).
+// True when the gather may use the kernels compiled for the paper's geometry (kGeoPaper), whose
+// atlas and occupancy offsets are 32-bit: at most 2^32 / 17^3 atlas blocks and a finest
+// occupancy level of at most 1024^3 cells.
 inline bool paper_geometry(const merf_scene_desc &d)
 {
-    return d.storage == MERF_STORAGE_U8_SPARSE && d.grid_res == 512 && d.block_size == 16 && d.plane_res == 2048;
+    return d.storage == MERF_STORAGE_U8_SPARSE && d.grid_res == 512 && d.block_size == 16 && d.plane_res == 2048 &&
+           (unsigned long long)d.n_blocks * 17 * 17 * 17 <= 0xffffffffull && d.n_occ_levels >= 1 &&
+           d.occ_res[0] <= 1024;
 }
 
 // The gather variant of a uint8 scene: the paper's geometry, a grid-only scene (no planes), or

@@ -368,7 +368,9 @@ struct Walker {
     // Advance k to the next lattice sample whose own finest occupancy cell is set and return
     // its position.  A sample in an empty finest cell starts a skip out of the largest empty
     // cell that contains it (coarse-to-fine: the first empty level from the coarsest), through
-    // cell_exit's verified jump.  False when the ray has no further occupied sample.
+    // cell_exit's verified jump.  False when the ray has no further occupied sample.  Idx: the
+    // offset type of the occupancy indices (32 bits only when the finest level fits).
+    template <typename Idx = size_t>
     __device__ __forceinline__ bool next_sample(const OccView &occ, float &p0, float &p1, float &p2)
     {
         const int N0 = occ.res[0];
@@ -379,12 +381,12 @@ struct Walker {
             position(k, p0, p1, p2);
             const int c0 = cell_of(p0, sc0, h0, N0), c1 = cell_of(p1, sc0, h0, N0),
                       c2 = cell_of(p2, sc0, h0, N0);
-            const size_t oi = ((size_t)c2 * N0 + c1) * N0 + c0;
+            const Idx oi = ((Idx)c2 * N0 + c1) * N0 + c0;
             if (MERF_IN_RANGE(oi, (long long)N0 * N0 * N0, kBadOcc) && __ldg(occ.level[0] + oi) != 0) return true;
             int sh = 0;
             for (int l = occ.n - 1; l > 0; --l) {
                 const int s = occ.shift[l], Nl = occ.res[l];
-                const size_t li = ((size_t)(c2 >> s) * Nl + (c1 >> s)) * Nl + (c0 >> s);
+                const Idx li = ((Idx)(c2 >> s) * Nl + (c1 >> s)) * Nl + (c0 >> s);
                 if (!MERF_IN_RANGE(li, (long long)Nl * Nl * Nl, kBadOcc) || __ldg(occ.level[l] + li) == 0) {
                     sh = s;
                     break;
