@@ -44,14 +44,14 @@ B_DENSITY, B_INDEX, B_APPEAR, B_OUT = 20, 4, 140, 12
 # launch from an ncu capture of this workload; reported as roofline.traffic only while the
 # render kernel's sources (device code, launch and scene layout) hash to the value they were
 # measured with (otherwise null).
-TRAFFIC_BYTES_PER_LAUNCH = (400.07 + 646.84) * 1e6
+TRAFFIC_BYTES_PER_LAUNCH = (400.60 + 647.24) * 1e6
 TRAFFIC_SOURCES = ("debug.cuh", "field.cuh", "merf_api.cu", "render.cuh", "scene.h", "traverse.cuh", "umma.cuh")
 # Warp-level instructions (smsp__inst_executed.sum) of the same timed launch from an ncu capture
 # (1 pass, full size), for the issue-rate roofline: the kernel is bound by instruction issue, and
 # an SM's four schedulers issue at most one warp instruction per clock each.
-INST_PER_LAUNCH = 43.847545862e9
+INST_PER_LAUNCH = 43.215163516e9
 SMS, SCHEDULERS_PER_SM = 148, 4
-TRAFFIC_SOURCES_SHA256 = "2df59d4ba4550c798b6d19d9b2eed23d510570cfdbee49afc1855a1babbbbd73"
+TRAFFIC_SOURCES_SHA256 = "518cdfcc0afbeb54df0ff526a5d0eeb9d03d8cc3edb4961728a3c8bd517e3f9c"
 
 
 def _sources_sha256() -> str:
