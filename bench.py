@@ -51,7 +51,7 @@ TRAFFIC_SOURCES = ("debug.cuh", "field.cuh", "merf_api.cu", "render.cuh", "scene
 # an SM's four schedulers issue at most one warp instruction per clock each.
 INST_PER_LAUNCH = 43.215163516e9
 SMS, SCHEDULERS_PER_SM = 148, 4
-TRAFFIC_SOURCES_SHA256 = "518cdfcc0afbeb54df0ff526a5d0eeb9d03d8cc3edb4961728a3c8bd517e3f9c"
+TRAFFIC_SOURCES_SHA256 = "d02c3180d335a56f56d092aea184b9f80baca6d1caa41c03845a3e898fa11d17"
 
 
 def _sources_sha256() -> str:

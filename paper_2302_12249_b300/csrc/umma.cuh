@@ -1,6 +1,7 @@
-// umma.cuh -- the sm_100-family tensor-core primitives used by the deferred MLP: tcgen05.mma
-// (one elected thread issues a CTA-wide M = 128 MMA), its accumulator in tensor memory (TMEM),
-// tcgen05.ld back to registers, and the mbarrier that tcgen05.commit signals when the MMAs are done.
+// umma.cuh -- the sm_100-family primitives used by the deferred MLP: tcgen05.mma (one elected
+// thread issues a CTA-wide M = 128 MMA), its accumulator in tensor memory (TMEM), tcgen05.ld back
+// to registers, the mbarrier that tcgen05.commit signals when the MMAs are done, and the bulk
+// (TMA) copy that brings the weights into shared memory.
 //
 // Operands live in shared memory in the canonical K-major layout without swizzle: an R x K tile of
 // 16-bit elements is made of 8-row x 16-byte "core matrices"; element (r, k) sits at
