@@ -372,7 +372,7 @@ def _spherical_ablation(gs, merf_ref, steps=5, warmup=3):
 SERVE_RES = [(256, 256), (640, 360), (1280, 720), (1920, 1080)]
 
 
-def _serving(gs_first, n_requests: int, rate: float = 200.0, seed_arrivals: int = 4000):
+def _serving(gs_first, n_requests: int, rate: float = 200.0, seed_arrivals: int = 4000, max_tiles: int = 16384):
     """Serving form: four resident paper-scale scenes, Poisson arrivals, random scene and orbit
     camera, resolution uniform over SERVE_RES, FP16 continuous batching.  Latency is measured by the
     library from submission to the image being in host memory."""
@@ -383,7 +383,7 @@ def _serving(gs_first, n_requests: int, rate: float = 200.0, seed_arrivals: int 
     scenes = [gs_first] + [merf.Scene(synth.make_scene("paper", seed=synth.SEED_SCENE + k)) for k in (1, 2, 3)]
     free_b, total_b = torch.cuda.mem_get_info()
     pool = int(min(4 << 30, free_b // 4))
-    srv = merf.Server(scenes, pool_bytes=pool, step=STEP, max_tiles_per_iter=16384, precision=merf.PREC_FP16)
+    srv = merf.Server(scenes, pool_bytes=pool, step=STEP, max_tiles_per_iter=max_tiles, precision=merf.PREC_FP16)
     rng = np.random.default_rng(seed_arrivals)
     gaps = rng.exponential(1.0 / rate, size=n_requests)
     which = rng.integers(0, len(scenes), size=n_requests)
@@ -437,7 +437,7 @@ def _serving(gs_first, n_requests: int, rate: float = 200.0, seed_arrivals: int 
     rays = sum(SERVE_RES[int(r)][0] * SERVE_RES[int(r)][1] for r in res)
     for sc in scenes[1:]:
         sc.close()
-    return {"requests": n_requests, "arrival_rate_per_s": rate, "precision": "fp16",
+    return {"requests": n_requests, "arrival_rate_per_s": rate, "precision": "fp16", "max_tiles_per_iter": max_tiles,
             "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
             "mean_ms": float(lat.mean() * 1e3), "max_ms": float(lat.max() * 1e3),
             "aggregate_mrays_per_s": rays / (t_end - t0) / 1e6, "offered_mrays_per_s": rays / gaps.sum() / 1e6,
