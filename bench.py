@@ -45,7 +45,8 @@ B_DENSITY, B_INDEX, B_APPEAR, B_OUT = 20, 4, 140, 12
 # render kernel's sources (device code, launch and scene layout) hash to the value they were
 # measured with (otherwise null).
 TRAFFIC_BYTES_PER_LAUNCH = (400.60 + 647.24) * 1e6
-TRAFFIC_SOURCES = ("debug.cuh", "field.cuh", "merf_api.cu", "render.cuh", "scene.h", "traverse.cuh", "umma.cuh")
+TRAFFIC_SOURCES = ("debug.cuh", "field.cuh", "geometry.h", "merf_api.cu", "render.cuh", "scene.h", "traverse.cuh",
+                   "umma.cuh")
 # Warp-level instructions (smsp__inst_executed.sum) of the same timed launch from an ncu capture
 # (1 pass, full size), for the issue-rate roofline: the kernel is bound by instruction issue, and
 # an SM's four schedulers issue at most one warp instruction per clock each.

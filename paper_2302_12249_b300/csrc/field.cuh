@@ -30,6 +30,7 @@
 #include <stdint.h>
 
 #include "debug.cuh"
+#include "geometry.h"
 
 namespace merf {
 
@@ -140,19 +141,15 @@ __device__ __forceinline__ void gather_grid_slow(const FieldView &fv, int x0, in
     t.wv = stored_weight(t, gmask);
 }
 
-// Scene geometry a gather is compiled for.  kGeoRuntime reads L, B and R from the FieldView;
-// kGeoPaper is the paper's configuration (L = 512 stored in 16^3 blocks, planes R = 2048;
-// Sec. 4), for which every stride, shift and scale below is a compile-time constant;
-// kGeoGridOnly is a scene with no planes (R = 0, t~ = V: the SNeRG++-style baseline the paper
-// compares against in Sec. 6), L and B read at run time.
-constexpr int kGeoRuntime = 0, kGeoPaper = 1, kGeoGridOnly = 2;
+// The gather variants (kGeoRuntime, kGeoPaper, kGeoGridOnly) and the host's choice among them are
+// in geometry.h.
 template <int kGeo>
 constexpr int kPlaneSources = kGeo == kGeoGridOnly ? 0 : 3;     // planes that add to the grid
 template <int kGeo>
 constexpr int kTaps = 8 + 4 * kPlaneSources<kGeo>;               // texels per sample
 // Offset type of the gather and occupancy indices.  The paper's geometry is chosen only for
-// scenes whose atlas holds at most 2^32 / 17^3 blocks and whose finest occupancy level is at
-// most 1024^3 cells, so every offset fits 32 bits there; other geometries use 64.
+// scenes whose atlas holds at most kPaperMaxBlocks blocks and whose finest occupancy level is at
+// most kPaperMaxOccRes^3 cells, so every offset fits 32 bits there; other geometries use 64.
 template <int kGeo>
 struct GatherIndex { using T = size_t; };
 template <>

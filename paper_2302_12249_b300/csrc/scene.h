@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include "geometry.h"
 #include "merf.h"
 #include "render.cuh"
 
@@ -50,25 +51,6 @@ inline void scene_views(const merf_scene *s, FieldView &fv, OccView &occ)
         occ.res[l] = d.occ_res[l];
         occ.shift[l] = log2_int(d.occ_res[0] / d.occ_res[l]);
     }
-}
-
-// True when the gather may use the kernels compiled for the paper's geometry (kGeoPaper), whose
-// atlas and occupancy offsets are 32-bit: at most 2^32 / 17^3 atlas blocks and a finest
-// occupancy level of at most 1024^3 cells.
-inline bool paper_geometry(const merf_scene_desc &d)
-{
-    return d.storage == MERF_STORAGE_U8_SPARSE && d.grid_res == 512 && d.block_size == 16 && d.plane_res == 2048 &&
-           (unsigned long long)d.n_blocks * 17 * 17 * 17 <= 0xffffffffull && d.n_occ_levels >= 1 &&
-           d.occ_res[0] <= 1024;
-}
-
-// The gather variant of a uint8 scene: the paper's geometry, a grid-only scene (no planes), or
-// run-time strides.
-inline int gather_geometry(const merf_scene_desc &d)
-{
-    if (paper_geometry(d)) return kGeoPaper;
-    if (d.storage == MERF_STORAGE_U8_SPARSE && d.plane_res == 0) return kGeoGridOnly;
-    return kGeoRuntime;
 }
 
 // Bounds-checked build: read and clear the server translation unit's device status word (0 in

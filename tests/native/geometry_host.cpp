@@ -1,0 +1,5 @@
+// Host-side entry to the gather-variant choice (geometry.h), for the CPU tests: no device code.
+#include "geometry.h"
+
+extern "C" int host_gather_geometry(const merf_scene_desc *d) { return merf::gather_geometry(*d); }
+extern "C" unsigned long long host_paper_max_blocks() { return merf::kPaperMaxBlocks; }
