@@ -44,7 +44,7 @@ B_DENSITY, B_INDEX, B_APPEAR, B_OUT = 20, 4, 140, 12
 # launch from an ncu capture of this workload; reported as roofline.traffic only while the
 # render kernel's sources (device code, launch and scene layout) hash to the value they were
 # measured with (otherwise null).
-TRAFFIC_BYTES_PER_LAUNCH = (400.60 + 647.24) * 1e6
+TRAFFIC_BYTES_PER_LAUNCH = (402.50 + 646.58) * 1e6
 TRAFFIC_SOURCES = ("debug.cuh", "field.cuh", "geometry.h", "merf_api.cu", "render.cuh", "scene.h", "traverse.cuh",
                    "umma.cuh")
 # Warp-level instructions (smsp__inst_executed.sum) of the same timed launch from an ncu capture
@@ -52,7 +52,7 @@ TRAFFIC_SOURCES = ("debug.cuh", "field.cuh", "geometry.h", "merf_api.cu", "rende
 # an SM's four schedulers issue at most one warp instruction per clock each.
 INST_PER_LAUNCH = 43.215163516e9
 SMS, SCHEDULERS_PER_SM = 148, 4
-TRAFFIC_SOURCES_SHA256 = "d02c3180d335a56f56d092aea184b9f80baca6d1caa41c03845a3e898fa11d17"
+TRAFFIC_SOURCES_SHA256 = "1193b3e303d5533ec634eb5ade54564b7f23eceb07daf9490986726a61271b38"
 
 
 def _sources_sha256() -> str:
