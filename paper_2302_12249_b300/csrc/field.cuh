@@ -141,19 +141,20 @@ __device__ __forceinline__ void gather_grid_slow(const FieldView &fv, int x0, in
     t.wv = stored_weight(t, gmask);
 }
 
-// The gather variants (kGeoRuntime, kGeoPaper, kGeoGridOnly) and the host's choice among them are
+// The gather variants (kGeoRuntime, kGeoPaper, kGeoGridOnly, kGeoGridOnlyWide) and the host's choice among them are
 // in geometry.h.
 template <int kGeo>
-constexpr int kPlaneSources = kGeo == kGeoGridOnly ? 0 : 3;     // planes that add to the grid
+constexpr int kPlaneSources = kGridOnly<kGeo> ? 0 : 3;          // planes that add to the grid
 template <int kGeo>
 constexpr int kTaps = 8 + 4 * kPlaneSources<kGeo>;               // texels per sample
-// Offset type of the gather and occupancy indices.  The paper's geometry is chosen only for
-// scenes whose atlas holds at most kPaperMaxBlocks blocks and whose finest occupancy level is at
-// most kPaperMaxOccRes^3 cells, so every offset fits 32 bits there; other geometries use 64.
+// Offset type of the gather and occupancy indices: 32-bit for the variants the host picks only when
+// offsets_fit_32 holds (kGeoPaper, kGeoGridOnly), 64-bit for the others.
 template <int kGeo>
 struct GatherIndex { using T = size_t; };
 template <>
 struct GatherIndex<kGeoPaper> { using T = uint32_t; };
+template <>
+struct GatherIndex<kGeoGridOnly> { using T = uint32_t; };
 
 template <int kGeo>
 __device__ __forceinline__ void gather_u8(const FieldView &fv, float p0, float p1, float p2, Taps &t)
@@ -209,7 +210,7 @@ __device__ __forceinline__ void gather_u8(const FieldView &fv, float p0, float p
         gather_grid_slow(fv, x0, y0, z0, t);
     }
 grid_done:;
-    if constexpr (kGeo == kGeoGridOnly) return;
+    if constexpr (kGridOnly<kGeo>) return;
     const float sR = (float)Rg * 0.25f;
     const int hR = Rg >> 1, R = Rg, Rp = Rg + 2;
     int u0[3];

@@ -5,36 +5,47 @@
 // stored in 16^3 blocks, planes R = 2048; Sec. 4), for which every stride, shift and scale of the
 // gather is a compile-time constant and every atlas, plane and occupancy offset is 32-bit.
 // kGeoGridOnly is a scene with no planes (R = 0, t~ = V: the SNeRG++-style baseline the paper
-// compares against in Sec. 6), L and B read at run time.
+// compares against in Sec. 6), L and B read at run time, offsets 32-bit; kGeoGridOnlyWide is the
+// same gather with 64-bit offsets, for grid-only scenes whose offsets do not fit 32 bits.
 #pragma once
 
 #include "merf.h"
 
 namespace merf {
 
-constexpr int kGeoRuntime = 0, kGeoPaper = 1, kGeoGridOnly = 2;
+constexpr int kGeoRuntime = 0, kGeoPaper = 1, kGeoGridOnly = 2, kGeoGridOnlyWide = 3;
+template <int kGeo>
+constexpr bool kGridOnly = kGeo == kGeoGridOnly || kGeo == kGeoGridOnlyWide;
 
-// Largest atlas, in blocks of 17^3 voxels (16^3 plus the apron), whose voxel offsets fit 32 bits.
-constexpr unsigned long long kPaperMaxBlocks = 0xffffffffull / (17ull * 17ull * 17ull);
-// Largest finest occupancy level of a paper-geometry scene: 1024^3 cells, offsets below 2^30.
-constexpr int kPaperMaxOccRes = 1024;
+// Largest finest occupancy level whose cell offsets the 32-bit variants take: 1024^3 cells.
+constexpr int kMaxOccRes32 = 1024;
+
+// True when every offset of a uint8 scene fits 32 bits: the largest atlas voxel offset,
+// n_blocks (B + 1)^3 - 1 (blocks carry a one-voxel apron), and the largest finest occupancy cell
+// offset, N^3 - 1 with N <= kMaxOccRes32.  (The paper geometry's plane offsets stay below
+// 3 * 2050^2; grid-only scenes have no planes.)
+inline bool offsets_fit_32(const merf_scene_desc &d)
+{
+    const unsigned long long b1 = (unsigned long long)d.block_size + 1;
+    return d.n_blocks >= 0 && (unsigned long long)d.n_blocks * b1 * b1 * b1 <= 0xffffffffull &&
+           d.n_occ_levels >= 1 && d.occ_res[0] <= kMaxOccRes32;
+}
 
 // True when the gather may use the kernels compiled for the paper's geometry (kGeoPaper): its
-// sizes, at most kPaperMaxBlocks atlas blocks and a finest occupancy level of at most
-// kPaperMaxOccRes^3 cells, so that every offset fits 32 bits.
+// sizes, and offsets that fit 32 bits.
 inline bool paper_geometry(const merf_scene_desc &d)
 {
     return d.storage == MERF_STORAGE_U8_SPARSE && d.grid_res == 512 && d.block_size == 16 && d.plane_res == 2048 &&
-           d.n_blocks >= 0 && (unsigned long long)d.n_blocks <= kPaperMaxBlocks && d.n_occ_levels >= 1 &&
-           d.occ_res[0] <= kPaperMaxOccRes;
+           offsets_fit_32(d);
 }
 
-// The gather variant of a scene: the paper's geometry, a grid-only uint8 scene (no planes), or
-// run-time strides.
+// The gather variant of a scene: the paper's geometry, a grid-only uint8 scene (no planes; 32- or
+// 64-bit offsets), or run-time strides.
 inline int gather_geometry(const merf_scene_desc &d)
 {
     if (paper_geometry(d)) return kGeoPaper;
-    if (d.storage == MERF_STORAGE_U8_SPARSE && d.plane_res == 0) return kGeoGridOnly;
+    if (d.storage == MERF_STORAGE_U8_SPARSE && d.plane_res == 0)
+        return offsets_fit_32(d) ? kGeoGridOnly : kGeoGridOnlyWide;
     return kGeoRuntime;
 }
 

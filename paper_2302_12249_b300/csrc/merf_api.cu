@@ -260,6 +260,8 @@ void launch_u8(int geo, dim3 grid, dim3 block, cudaStream_t st, const merf::Rend
         merf::render_kernel<0, kPrec, merf::kGeoPaper><<<grid, block, 0, st>>>(P);
     else if (geo == merf::kGeoGridOnly)
         merf::render_kernel<0, kPrec, merf::kGeoGridOnly><<<grid, block, 0, st>>>(P);
+    else if (geo == merf::kGeoGridOnlyWide)
+        merf::render_kernel<0, kPrec, merf::kGeoGridOnlyWide><<<grid, block, 0, st>>>(P);
     else
         merf::render_kernel<0, kPrec, merf::kGeoRuntime><<<grid, block, 0, st>>>(P);
 }
@@ -288,6 +290,8 @@ merf_status launch_render(const merf_scene *s, const merf_camera *cams, int n, i
                 merf::render_kernel<0, 0, merf::kGeoPaper, 1><<<grid, block, 0, st>>>(P);
             else if (geo == merf::kGeoGridOnly)
                 merf::render_kernel<0, 0, merf::kGeoGridOnly, 1><<<grid, block, 0, st>>>(P);
+            else if (geo == merf::kGeoGridOnlyWide)
+                merf::render_kernel<0, 0, merf::kGeoGridOnlyWide, 1><<<grid, block, 0, st>>>(P);
             else
                 merf::render_kernel<0, 0, merf::kGeoRuntime, 1><<<grid, block, 0, st>>>(P);
         } else if (s->desc.storage == MERF_STORAGE_F32_DENSE)

@@ -2,4 +2,4 @@
 #include "geometry.h"
 
 extern "C" int host_gather_geometry(const merf_scene_desc *d) { return merf::gather_geometry(*d); }
-extern "C" unsigned long long host_paper_max_blocks() { return merf::kPaperMaxBlocks; }
+extern "C" int host_offsets_fit_32(const merf_scene_desc *d) { return merf::offsets_fit_32(*d) ? 1 : 0; }

@@ -1,7 +1,8 @@
-"""CPU tests of the host's choice of gather variant (geometry.h).  The paper-geometry kernels index
-the atlas, the planes and the occupancy levels with 32-bit offsets, so the choice must exclude every
-scene whose offsets could exceed 2^32: the largest voxel offset is n_blocks * 17^3 - 1 (16^3 blocks
-plus the one-voxel apron) and the largest finest-level cell offset is N^3 - 1.  No GPU."""
+"""CPU tests of the host's choice of gather variant (geometry.h).  The paper-geometry and grid-only
+kernels index the atlas, the planes and the occupancy levels with 32-bit offsets, so the choice must
+send every scene whose offsets could exceed 2^32 elsewhere: the largest voxel offset is
+n_blocks * (B + 1)^3 - 1 (B^3 blocks plus the one-voxel apron) and the largest finest-level cell
+offset is N^3 - 1.  No GPU."""
 import ctypes as ct
 import os
 import subprocess
@@ -12,7 +13,7 @@ from paper_2302_12249_b300 import merf
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-GEO_RUNTIME, GEO_PAPER, GEO_GRID_ONLY = 0, 1, 2
+GEO_RUNTIME, GEO_PAPER, GEO_GRID_ONLY, GEO_GRID_ONLY_WIDE = 0, 1, 2, 3
 
 
 @pytest.fixture(scope="module")
@@ -24,7 +25,8 @@ def geolib(tmp_path_factory):
     L = ct.CDLL(out)
     L.host_gather_geometry.argtypes = [ct.POINTER(merf.Desc)]
     L.host_gather_geometry.restype = ct.c_int
-    L.host_paper_max_blocks.restype = ct.c_ulonglong
+    L.host_offsets_fit_32.argtypes = [ct.POINTER(merf.Desc)]
+    L.host_offsets_fit_32.restype = ct.c_int
     return L
 
 
@@ -43,9 +45,32 @@ def test_paper_scene_takes_the_paper_kernels(geolib):
     assert geolib.host_gather_geometry(ct.byref(paper_desc())) == GEO_PAPER
 
 
-def test_block_limit_is_the_largest_32_bit_atlas(geolib):
-    n = geolib.host_paper_max_blocks()
-    assert n * 17 ** 3 - 1 <= 2 ** 32 - 1 < (n + 1) * 17 ** 3 - 1
+def largest_32_bit_atlas(B):
+    """Most blocks of (B + 1)^3 voxels whose every voxel offset is below 2^32 (by search, not by the
+    formula the header uses)."""
+    lo, hi = 0, 2 ** 31
+    while lo < hi:
+        mid = (lo + hi + 1) // 2
+        if mid * (B + 1) ** 3 - 1 <= 2 ** 32 - 1:
+            lo = mid
+        else:
+            hi = mid - 1
+    return lo
+
+
+@pytest.mark.parametrize("B", [8, 16, 32])
+def test_offsets_fit_32_at_the_block_limit(geolib, B):
+    n = largest_32_bit_atlas(B)
+    d = paper_desc(n_blocks=n)
+    d.block_size = B
+    assert geolib.host_offsets_fit_32(ct.byref(d)) == 1
+    d.n_blocks = n + 1
+    assert geolib.host_offsets_fit_32(ct.byref(d)) == 0
+
+
+def test_block_limit_of_the_paper_geometry(geolib):
+    n = largest_32_bit_atlas(16)
+    assert n == 874204
     assert geolib.host_gather_geometry(ct.byref(paper_desc(n_blocks=n))) == GEO_PAPER
     assert geolib.host_gather_geometry(ct.byref(paper_desc(n_blocks=n + 1))) == GEO_RUNTIME
 
@@ -69,3 +94,14 @@ def test_other_geometries(geolib):
     d = paper_desc()
     d.storage = merf.STORAGE_F32_DENSE
     assert geolib.host_gather_geometry(ct.byref(d)) == GEO_RUNTIME
+
+
+def test_grid_only_scenes_take_32_bit_offsets_only_when_they_fit(geolib):
+    d = paper_desc(occ=(256, 64, 16))
+    d.grid_res, d.plane_res = 2048, 0
+    assert geolib.host_gather_geometry(ct.byref(d)) == GEO_GRID_ONLY
+    d.n_blocks = largest_32_bit_atlas(16) + 1
+    assert geolib.host_gather_geometry(ct.byref(d)) == GEO_GRID_ONLY_WIDE
+    d = paper_desc(occ=(2048, 64, 16))
+    d.plane_res = 0
+    assert geolib.host_gather_geometry(ct.byref(d)) == GEO_GRID_ONLY_WIDE
