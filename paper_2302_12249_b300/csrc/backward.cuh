@@ -18,6 +18,8 @@
 //      (float4 atomics).
 #pragma once
 
+#include <type_traits>
+
 #include "render.cuh"
 
 namespace merf {
@@ -40,10 +42,12 @@ struct BackwardParams {
 // Add w g at texel `key` of `base` (8 floats per texel; key < 0: nothing), merging with the
 // horizontally adjacent pixel (lane ^ 1) when both add to the same texel: the even lane adds the
 // pair's sum and the odd lane skips its atomics.  m: the lanes executing this call together.
-__device__ __forceinline__ void atomic_add8_pair(float *base, long long key, const float g[8], float w, unsigned m)
+// Key: int when every texel index fits (the 32-bit variant), else long long.
+template <typename Key>
+__device__ __forceinline__ void atomic_add8_pair(float *base, Key key, const float g[8], float w, unsigned m)
 {
     const int lane = threadIdx.x & 31;
-    const long long pk = __shfl_xor_sync(m, key, 1);
+    const Key pk = __shfl_xor_sync(m, key, 1);
     const bool merge = key >= 0 && pk == key && ((m >> (lane ^ 1)) & 1u);
     float v[8];
 #pragma unroll
@@ -62,9 +66,12 @@ __device__ __forceinline__ void atomic_add8_pair(float *base, long long key, con
 }
 
 // Add g (per channel) times the interpolation weights of p to the dense grid and plane gradients.
+template <int kGeo>
 __device__ __forceinline__ void scatter_f32(const FieldView &fv, float *g_grid, float *g_planes, float p0, float p1,
                                             float p2, const float g[8])
 {
+    using Idx = typename GatherIndex<kGeo>::T;
+    using Key = typename std::conditional<sizeof(Idx) == 4, int, long long>::type;   // signed: -1 = none
     const float sL = (float)fv.L * 0.25f;
     const int hL = fv.L >> 1, L = fv.L;
     int x0, y0, z0;
@@ -77,9 +84,9 @@ __device__ __forceinline__ void scatter_f32(const FieldView &fv, float *g_grid, 
     for (int c = 0; c < 8; ++c) {
         const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
         const float w = (cx ? fx : 1.0f - fx) * (cy ? fy : 1.0f - fy) * (cz ? fz : 1.0f - fz);
-        const size_t gi = ((size_t)(z0 + cz) * L + (y0 + cy)) * L + (x0 + cx);
+        const Idx gi = ((Idx)(z0 + cz) * L + (y0 + cy)) * L + (x0 + cx);
         const bool ok = w != 0.0f && MERF_IN_RANGE(gi, (long long)L * L * L, kBadDense);
-        atomic_add8_pair(g_grid, ok ? (long long)gi : -1LL, g, w, m);
+        atomic_add8_pair<Key>(g_grid, ok ? (Key)gi : (Key)-1, g, w, m);
     }
     const float sR = (float)fv.R * 0.25f;
     const int hR = fv.R >> 1, R = fv.R;
@@ -95,9 +102,9 @@ __device__ __forceinline__ void scatter_f32(const FieldView &fv, float *g_grid, 
         for (int c = 0; c < 4; ++c) {
             const int cu = c & 1, cv = c >> 1;
             const float w = (cu ? fu[ca] : 1.0f - fu[ca]) * (cv ? fu[ra] : 1.0f - fu[ra]);
-            const size_t pi = ((size_t)q * R + u0[ra] + cv) * R + u0[ca] + cu;
+            const Idx pi = ((Idx)q * R + u0[ra] + cv) * R + u0[ca] + cu;
             const bool ok = w != 0.0f && MERF_IN_RANGE(pi, 3LL * R * R, kBadDense);
-            atomic_add8_pair(g_planes, ok ? (long long)pi : -1LL, g, w, m);
+            atomic_add8_pair<Key>(g_planes, ok ? (Key)pi : (Key)-1, g, w, m);
         }
     }
 }
@@ -238,7 +245,9 @@ __device__ __forceinline__ void mlp_weight_grads_warp(float *gw, float *st, cons
     __syncwarp();
 }
 
-static __global__ void __launch_bounds__(kThreads, 4) backward_kernel(const __grid_constant__ BackwardParams P)
+// kGeo: kGeoDense32 (32-bit offsets) or kGeoRuntime (64-bit), as the host chose for the scene.
+template <int kGeo>
+__global__ void __launch_bounds__(kThreads, 4) backward_kernel(const __grid_constant__ BackwardParams P)
 {
     __shared__ float wsm[kMlpParams];
     __shared__ float gsm[kMlpParams];
@@ -268,7 +277,7 @@ static __global__ void __launch_bounds__(kThreads, 4) backward_kernel(const __gr
             float o[3];
             ray_f32(cam, i, j, o, r.d);
         } else {
-            march_ray<1, 0>(P.fv, P.occ, cam, i, j, P.step, P.t_term, P.early_term, r);
+            march_ray<1, 0, kGeo>(P.fv, P.occ, cam, i, j, P.step, P.t_term, P.early_term, r);
         }
     }
     // the whole warp: MLP backward per lane, weight gradients reduced across the warp
@@ -293,9 +302,9 @@ static __global__ void __launch_bounds__(kThreads, 4) backward_kernel(const __gr
         float T = 1.0f, A = 0.0f;
         for (;;) {
             float p0, p1, p2;
-            if (!wk.next_sample(P.occ, p0, p1, p2)) break;
+            if (!wk.next_sample<typename GatherIndex<kGeo>::T>(P.occ, p0, p1, p2)) break;
             float t8[8];
-            field_f32(P.fv, p0, p1, p2, t8);
+            field_f32<kGeo>(P.fv, p0, p1, p2, t8);
             const float tau = __expf(t8[0]);
             const float dw = wk.delta_world(wk.k);
             const float alpha = 1.0f - __expf(-tau * dw);
@@ -322,7 +331,7 @@ static __global__ void __launch_bounds__(kThreads, 4) backward_kernel(const __gr
                 for (int k = 0; k < 3; ++k) g[1 + k] = w * Gc[k] * c[k] * (1.0f - c[k]);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) g[4 + k] = w * Gf[k] * f[k] * (1.0f - f[k]);
-                scatter_f32(P.fv, P.g_grid, P.g_planes, p0, p1, p2, g);
+                scatter_f32<kGeo>(P.fv, P.g_grid, P.g_planes, p0, p1, p2, g);
                 T = T * om;
                 if (P.early_term && T < P.t_term) break;
             }

@@ -141,20 +141,23 @@ __device__ __forceinline__ void gather_grid_slow(const FieldView &fv, int x0, in
     t.wv = stored_weight(t, gmask);
 }
 
-// The gather variants (kGeoRuntime, kGeoPaper, kGeoGridOnly, kGeoGridOnlyWide) and the host's choice among them are
+// The gather variants (kGeoRuntime, kGeoPaper, kGeoGridOnly, kGeoGridOnlyWide, kGeoDense32) and the host's choice among them are
 // in geometry.h.
 template <int kGeo>
 constexpr int kPlaneSources = kGridOnly<kGeo> ? 0 : 3;          // planes that add to the grid
 template <int kGeo>
 constexpr int kTaps = 8 + 4 * kPlaneSources<kGeo>;               // texels per sample
 // Offset type of the gather and occupancy indices: 32-bit for the variants the host picks only when
-// offsets_fit_32 holds (kGeoPaper, kGeoGridOnly), 64-bit for the others.
+// offsets_fit_32 holds (kGeoPaper, kGeoGridOnly) or dense_offsets_fit_32 (kGeoDense32), 64-bit for
+// the others.
 template <int kGeo>
 struct GatherIndex { using T = size_t; };
 template <>
 struct GatherIndex<kGeoPaper> { using T = uint32_t; };
 template <>
 struct GatherIndex<kGeoGridOnly> { using T = uint32_t; };
+template <>
+struct GatherIndex<kGeoDense32> { using T = uint32_t; };
 
 template <int kGeo>
 __device__ __forceinline__ void gather_u8(const FieldView &fv, float p0, float p1, float p2, Taps &t)
@@ -405,8 +408,10 @@ __device__ __forceinline__ void byte_sums_lp(const Taps &t, float2 k[4])
 }
 
 // Dense float storage: all eight channels of all 20 taps, summed.
+template <int kGeo = kGeoRuntime>
 __device__ __forceinline__ void field_f32(const FieldView &fv, float p0, float p1, float p2, float out[8])
 {
+    using Idx = typename GatherIndex<kGeo>::T;
     const float sL = (float)fv.L * 0.25f;
     const int hL = fv.L >> 1, L = fv.L;
     int x0, y0, z0;
@@ -418,14 +423,14 @@ __device__ __forceinline__ void field_f32(const FieldView &fv, float p0, float p
     float2 acc[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[j] = make_float2(0.0f, 0.0f);
-    const size_t gidx = ((size_t)z0 * L + y0) * L + x0;
-    const bool g_ok = MERF_IN_RANGE(gidx + (size_t)L * L + L + 1, (long long)L * L * L, kBadDense);
+    const Idx gidx = ((Idx)z0 * L + y0) * L + x0;
+    const bool g_ok = MERF_IN_RANGE(gidx + (Idx)L * L + L + 1, (long long)L * L * L, kBadDense);
     const float4 *g0 = fv.grid_f32 + gidx * 2;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
         const float w = (cx ? fx : 1.0f - fx) * (cy ? fy : 1.0f - fy) * (cz ? fz : 1.0f - fz);
-        const float4 *q = g0 + ((size_t)(cz * L + cy) * L + cx) * 2;
+        const float4 *q = g0 + ((Idx)(cz * L + cy) * L + cx) * 2;
         if (!g_ok) continue;
         const float4 a = __ldg(q), b = __ldg(q + 1);
         const float2 ww = make_float2(w, w);
@@ -444,14 +449,14 @@ __device__ __forceinline__ void field_f32(const FieldView &fv, float p0, float p
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         const int ca = q == 0 ? 1 : 0, ra = q == 2 ? 1 : 2;
-        const size_t pidx = ((size_t)q * R + u0[ra]) * R + u0[ca];
+        const Idx pidx = ((Idx)q * R + u0[ra]) * R + u0[ca];
         if (!MERF_IN_RANGE(pidx + R + 1, 3LL * R * R, kBadDense)) continue;
         const float4 *t0 = fv.planes_f32 + pidx * 2;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int cu = c & 1, cv = c >> 1;
             const float w = (cu ? fu[ca] : 1.0f - fu[ca]) * (cv ? fu[ra] : 1.0f - fu[ra]);
-            const float4 *t = t0 + ((size_t)cv * R + cu) * 2;
+            const float4 *t = t0 + ((Idx)cv * R + cu) * 2;
             const float4 a = __ldg(t), b = __ldg(t + 1);
             const float2 ww = make_float2(w, w);
             acc[0] = __ffma2_rn(ww, make_float2(a.x, a.y), acc[0]);

@@ -6,14 +6,16 @@
 // gather is a compile-time constant and every atlas, plane and occupancy offset is 32-bit.
 // kGeoGridOnly is a scene with no planes (R = 0, t~ = V: the SNeRG++-style baseline the paper
 // compares against in Sec. 6), L and B read at run time, offsets 32-bit; kGeoGridOnlyWide is the
-// same gather with 64-bit offsets, for grid-only scenes whose offsets do not fit 32 bits.
+// same gather with 64-bit offsets, for grid-only scenes whose offsets do not fit 32 bits.  Dense
+// float scenes (the differentiable storage) take kGeoDense32, 32-bit offsets, when theirs fit, and
+// kGeoRuntime (64-bit) otherwise.
 #pragma once
 
 #include "merf.h"
 
 namespace merf {
 
-constexpr int kGeoRuntime = 0, kGeoPaper = 1, kGeoGridOnly = 2, kGeoGridOnlyWide = 3;
+constexpr int kGeoRuntime = 0, kGeoPaper = 1, kGeoGridOnly = 2, kGeoGridOnlyWide = 3, kGeoDense32 = 4;
 template <int kGeo>
 constexpr bool kGridOnly = kGeo == kGeoGridOnly || kGeo == kGeoGridOnlyWide;
 
@@ -31,6 +33,16 @@ inline bool offsets_fit_32(const merf_scene_desc &d)
            d.n_occ_levels >= 1 && d.occ_res[0] <= kMaxOccRes32;
 }
 
+// True when every offset of a dense float scene fits 32 bits as a signed value: the grid holds
+// L^3 texels of two float4 (2 L^3 float4 offsets), the planes 3 R^2 texels (6 R^2), and the finest
+// occupancy level at most kMaxOccRes32^3 cells.
+inline bool dense_offsets_fit_32(const merf_scene_desc &d)
+{
+    const unsigned long long L = (unsigned long long)d.grid_res, R = (unsigned long long)d.plane_res;
+    return d.grid_res >= 0 && d.plane_res >= 0 && 2ull * L * L * L <= 0x7fffffffull && 6ull * R * R <= 0x7fffffffull &&
+           d.n_occ_levels >= 1 && d.occ_res[0] <= kMaxOccRes32;
+}
+
 // True when the gather may use the kernels compiled for the paper's geometry (kGeoPaper): its
 // sizes, and offsets that fit 32 bits.
 inline bool paper_geometry(const merf_scene_desc &d)
@@ -40,9 +52,10 @@ inline bool paper_geometry(const merf_scene_desc &d)
 }
 
 // The gather variant of a scene: the paper's geometry, a grid-only uint8 scene (no planes; 32- or
-// 64-bit offsets), or run-time strides.
+// 64-bit offsets), a dense float scene with 32-bit offsets, or run-time strides.
 inline int gather_geometry(const merf_scene_desc &d)
 {
+    if (d.storage == MERF_STORAGE_F32_DENSE) return dense_offsets_fit_32(d) ? kGeoDense32 : kGeoRuntime;
     if (paper_geometry(d)) return kGeoPaper;
     if (d.storage == MERF_STORAGE_U8_SPARSE && d.plane_res == 0)
         return offsets_fit_32(d) ? kGeoGridOnly : kGeoGridOnlyWide;

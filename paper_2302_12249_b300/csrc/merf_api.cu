@@ -284,7 +284,9 @@ merf_status launch_render(const merf_scene *s, const merf_camera *cams, int n, i
         const dim3 grid((W + merf::kTileW - 1) / merf::kTileW, (H + merf::kTileH - 1) / merf::kTileH, nc);
         const int geo = merf::gather_geometry(s->desc);
         if (o->contraction == 1) {          // spherical-contraction ablation (FP32, dense march)
-            if (s->desc.storage == MERF_STORAGE_F32_DENSE)
+            if (geo == merf::kGeoDense32)
+                merf::render_kernel<1, 0, merf::kGeoDense32, 1><<<grid, block, 0, st>>>(P);
+            else if (s->desc.storage == MERF_STORAGE_F32_DENSE)
                 merf::render_kernel<1, 0, merf::kGeoRuntime, 1><<<grid, block, 0, st>>>(P);
             else if (geo == merf::kGeoPaper)
                 merf::render_kernel<0, 0, merf::kGeoPaper, 1><<<grid, block, 0, st>>>(P);
@@ -294,7 +296,9 @@ merf_status launch_render(const merf_scene *s, const merf_camera *cams, int n, i
                 merf::render_kernel<0, 0, merf::kGeoGridOnlyWide, 1><<<grid, block, 0, st>>>(P);
             else
                 merf::render_kernel<0, 0, merf::kGeoRuntime, 1><<<grid, block, 0, st>>>(P);
-        } else if (s->desc.storage == MERF_STORAGE_F32_DENSE)
+        } else if (geo == merf::kGeoDense32)
+            merf::render_kernel<1, 0, merf::kGeoDense32><<<grid, block, 0, st>>>(P);
+        else if (s->desc.storage == MERF_STORAGE_F32_DENSE)
             merf::render_kernel<1, 0, merf::kGeoRuntime><<<grid, block, 0, st>>>(P);
         else if (o->precision == MERF_PREC_FP16)
             launch_u8<1>(geo, grid, block, st, P);
@@ -754,7 +758,10 @@ merf_status merf_render_backward_aux(const merf_scene *scene, const merf_camera 
         P.cam0 = c0;
         for (int c = 0; c < nc; ++c) memcpy(P.cams.m[c], &cams[c0 + c], sizeof(merf_camera));
         const dim3 grid((W + merf::kTileW - 1) / merf::kTileW, (H + merf::kTileH - 1) / merf::kTileH, nc);
-        merf::backward_kernel<<<grid, merf::kThreads, 0, s>>>(P);
+        if (merf::gather_geometry(scene->desc) == merf::kGeoDense32)
+            merf::backward_kernel<merf::kGeoDense32><<<grid, merf::kThreads, 0, s>>>(P);
+        else
+            merf::backward_kernel<merf::kGeoRuntime><<<grid, merf::kThreads, 0, s>>>(P);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return fail(MERF_ERR_CUDA, "backward launch: %s", cudaGetErrorString(e));
     }

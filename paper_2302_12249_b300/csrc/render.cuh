@@ -541,7 +541,7 @@ __device__ __forceinline__ void eval_field(const FieldView &fv, float p0, float 
         else ya = app_arg_u8_half(k, wsum);
     } else {
         float all[8];
-        field_f32(fv, p0, p1, p2, all);
+        field_f32<kGeo>(fv, p0, p1, p2, all);
         dens = all[0];
         ya = app_arg(all + 1);
     }

@@ -13,7 +13,7 @@ from paper_2302_12249_b300 import merf
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-GEO_RUNTIME, GEO_PAPER, GEO_GRID_ONLY, GEO_GRID_ONLY_WIDE = 0, 1, 2, 3
+GEO_RUNTIME, GEO_PAPER, GEO_GRID_ONLY, GEO_GRID_ONLY_WIDE, GEO_DENSE_32 = 0, 1, 2, 3, 4
 
 
 @pytest.fixture(scope="module")
@@ -93,7 +93,7 @@ def test_other_geometries(geolib):
     assert geolib.host_gather_geometry(ct.byref(d)) == GEO_RUNTIME
     d = paper_desc()
     d.storage = merf.STORAGE_F32_DENSE
-    assert geolib.host_gather_geometry(ct.byref(d)) == GEO_RUNTIME
+    assert geolib.host_gather_geometry(ct.byref(d)) == GEO_DENSE_32
 
 
 def test_grid_only_scenes_take_32_bit_offsets_only_when_they_fit(geolib):
@@ -105,3 +105,21 @@ def test_grid_only_scenes_take_32_bit_offsets_only_when_they_fit(geolib):
     d = paper_desc(occ=(2048, 64, 16))
     d.plane_res = 0
     assert geolib.host_gather_geometry(ct.byref(d)) == GEO_GRID_ONLY_WIDE
+
+
+def test_dense_scenes_take_32_bit_offsets_only_when_they_fit(geolib):
+    """Dense float scenes hold two float4 per grid texel and per plane texel; the adjoint keys texel
+    indices as signed 32-bit values, so 2 L^3 and 6 R^2 must stay below 2^31."""
+    def dense(L, R, occ=(128, 64, 32, 16)):
+        d = paper_desc(occ=occ)
+        d.storage, d.grid_res, d.plane_res = merf.STORAGE_F32_DENSE, L, R
+        return d
+    assert geolib.host_gather_geometry(ct.byref(dense(128, 512))) == GEO_DENSE_32
+    L = max(l for l in range(1, 2000) if 2 * l ** 3 <= 2 ** 31 - 1)
+    assert L == 1023
+    assert geolib.host_gather_geometry(ct.byref(dense(L, 512))) == GEO_DENSE_32
+    assert geolib.host_gather_geometry(ct.byref(dense(L + 1, 512))) == GEO_RUNTIME
+    R = max(r for r in range(1, 30000) if 6 * r * r <= 2 ** 31 - 1)
+    assert geolib.host_gather_geometry(ct.byref(dense(128, R))) == GEO_DENSE_32
+    assert geolib.host_gather_geometry(ct.byref(dense(128, R + 1))) == GEO_RUNTIME
+    assert geolib.host_gather_geometry(ct.byref(dense(128, 512, occ=(2048, 64)))) == GEO_RUNTIME
