@@ -52,7 +52,7 @@ TRAFFIC_SOURCES = ("debug.cuh", "field.cuh", "geometry.h", "merf_api.cu", "rende
 # an SM's four schedulers issue at most one warp instruction per clock each.
 INST_PER_LAUNCH = 43.215163516e9
 SMS, SCHEDULERS_PER_SM = 148, 4
-TRAFFIC_SOURCES_SHA256 = "c84b3e73bf748311c75d6af5d4adb057371b280d309822af12ca9de1f9159257"
+TRAFFIC_SOURCES_SHA256 = "639c665e37d3e418ddcb026727eacb7fe501a338a8dd5623b2c0546932018088"
 
 
 def _sources_sha256() -> str:

@@ -329,9 +329,11 @@ void merf_set_device_budget(size_t bytes);
  * index into the index grid, atlas, planes, occupancy levels and dense arrays; an index out of
  * range is skipped (the texel reads as zero, the cell as empty) and recorded, never trapped.
  * Returns MERF_ERR_DEVICE_BOUNDS (merf_last_error names what was out of range) if anything was
- * recorded since the last call, and clears the word.  In every build the FP16/BF16 kernels wait
- * for their tensor-core MMAs on a barrier with a bounded number of polls; a wait that gives up
- * (its pixels' MLP term then reads as zero) is recorded too, and reported as MERF_ERR_TIMEOUT.
+ * recorded since the last call, and clears the word.  In every build the render and serving
+ * kernels wait for the bulk copy of the MLP weights, and the FP16/BF16 kernels for their
+ * tensor-core MMAs, on barriers with a bounded number of polls; a wait that gives up (the MLP term
+ * of its pixels is then unreliable; after an MMA wait it reads as zero) is recorded too, and
+ * reported as MERF_ERR_TIMEOUT.
  * self_test exercises the reporting paths first: 1 (bounds-checked build only, else
  * MERF_ERR_UNSUPPORTED) records a self-test bit from a one-thread kernel (the call returns
  * MERF_ERR_DEVICE_BOUNDS); 2 (any build) runs the MLP's bounded barrier wait on a barrier that

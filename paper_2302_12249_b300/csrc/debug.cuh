@@ -5,9 +5,9 @@
 // occupancy levels and the dense float arrays is checked before the access.  An index out of
 // range sets a bit of the translation unit's device status word and the access is skipped (the
 // texel reads as zero, the cell as empty); nothing traps.  In the release build MERF_IN_RANGE is
-// the constant true and the checks compile to nothing.  A wait on the tensor cores' completion
-// barrier that runs out of polls sets kWaitTimeout in both builds.  The host reads and clears the
-// word with merf_check_device.
+// the constant true and the checks compile to nothing.  A wait on the MLP weights' bulk copy or on
+// the tensor cores' completion barrier that runs out of polls sets kWaitTimeout in both builds.
+// The host reads and clears the word with merf_check_device.
 #pragma once
 
 #include <cuda_runtime.h>
