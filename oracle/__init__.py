@@ -95,6 +95,8 @@ def lib():
                                 ct.c_void_p, ct.c_int, ct.c_double, ct.c_int, ct.c_double,
                                 ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_int, ct.c_int]
         L.orc_trace.restype = ct.c_int
+        L.orc_trace_flagged.argtypes = L.orc_trace.argtypes + [ct.c_int]
+        L.orc_trace_flagged.restype = ct.c_int
         L.orc_footprint.argtypes = [ct.POINTER(_Scene), ct.c_void_p, ct.c_int, ct.c_int, ct.c_int,
                                     ct.c_void_p, ct.c_int, ct.POINTER(_Opts), ct.c_void_p, ct.c_int]
         L.orc_footprint.restype = ct.c_int
@@ -339,8 +341,10 @@ def footprint(oscene: OracleScene, cams: np.ndarray, W: int, H: int, step: float
 
 def trace(oscene: OracleScene, cams: np.ndarray, W: int, H: int, step: float, words: int,
           pix: Optional[np.ndarray] = None, decide_f32: bool = True, eps: float = 2e-6,
-          threads: Optional[int] = None, contraction: int = 0):
-    """Evaluated lattice-sample sets (termination off) as bit masks [n, words] + FP64 face flags."""
+          threads: Optional[int] = None, contraction: int = 0, decisive: bool = False):
+    """Evaluated lattice-sample sets (termination off) as bit masks [n, words] + FP64 flags: every
+    sample within eps of a cell face, or (decisive) only the samples whose outcome a move of eps
+    can change (orc_trace_flagged)."""
     cams = np.ascontiguousarray(cams, dtype=np.float32).reshape(-1, 16)
     if pix is not None:
         pix = np.ascontiguousarray(pix, dtype=np.int32).reshape(-1, 3)
@@ -350,9 +354,10 @@ def trace(oscene: OracleScene, cams: np.ndarray, W: int, H: int, step: float, wo
     mask = np.zeros((n, words), dtype=np.uint32)
     flags = np.zeros((n, words), dtype=np.uint32)
     nlat = np.zeros(n, dtype=np.int32)
-    lib().orc_trace(ct.byref(oscene.s), _ptr(cams), cams.shape[0], W, H, _ptr(pix),
-                    0 if pix is None else n, float(step), int(decide_f32), float(eps),
-                    _ptr(mask), _ptr(flags), words, _ptr(nlat), threads or default_threads(), int(contraction))
+    lib().orc_trace_flagged(ct.byref(oscene.s), _ptr(cams), cams.shape[0], W, H, _ptr(pix),
+                            0 if pix is None else n, float(step), int(decide_f32), float(eps),
+                            _ptr(mask), _ptr(flags), words, _ptr(nlat), threads or default_threads(),
+                            int(contraction), int(decisive))
     return mask, flags, nlat
 
 

@@ -934,6 +934,7 @@ typedef struct {
     /* trace */
     double step, eps;
     int decide_f32, words, contraction;
+    int decisive;          /* trace flags: 0 near any cell face, 1 only where a decision can change */
     uint32_t *mask, *flags;
     int32_t *nlat;
     orc_marks *marks;      /* footprint: NULL when only rendering */
@@ -1024,6 +1025,39 @@ int orc_footprint(const orc_scene *sc, const float *cams, int n_cams, int W, int
     return 0;
 }
 
+/* Reading 14 of the FP32-vs-FP64 comparison: an integer outcome of a lattice sample can differ
+ * between two precisions only where a rounding-sized move of its position or arc length changes
+ * it.  Position: some finest cell within eps of p (across a face, an edge or a corner, inside the
+ * grid) holds an occupancy value other than p's own cell's.  Arc length: s lies within eps of an
+ * interior segment boundary (the contracted ray may jump there, Sec. 3.2) or (k + 1) step lies
+ * within eps of the total arc length (whether sample k exists at all). */
+static int occ_decision_ambiguous(const orc_scene *sc, const double p[3], const int cell[3], double eps)
+{
+    int N = sc->occ_res[0], lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        double u = (p[a] + 2.0) * (double)N / 4.0, f = floor(u);
+        double d_lo = (u - f) * 4.0 / (double)N, d_hi = (f + 1.0 - u) * 4.0 / (double)N;
+        lo[a] = (d_lo < eps && cell[a] > 0) ? cell[a] - 1 : cell[a];
+        hi[a] = (d_hi < eps && cell[a] < N - 1) ? cell[a] + 1 : cell[a];
+    }
+    int own = occ_at(sc, cell);
+    for (int z = lo[2]; z <= hi[2]; ++z)
+        for (int y = lo[1]; y <= hi[1]; ++y)
+            for (int x = lo[0]; x <= hi[0]; ++x) {
+                int c[3] = {x, y, z};
+                if (occ_at(sc, c) != own) return 1;
+            }
+    return 0;
+}
+
+static int arc_decision_ambiguous(const orc_seg *segs, int ns, double step, int k, double eps)
+{
+    double s = ((double)k + 0.5) * step, total = segs[ns - 1].s0 + segs[ns - 1].len;
+    for (int m = 1; m < ns; ++m)
+        if (fabs(s - segs[m].s0) < eps) return 1;
+    return fabs(((double)k + 1.0) * step - total) < eps;
+}
+
 static void *trace_worker(void *arg)
 {
     job *jb = (job *)arg;
@@ -1052,13 +1086,14 @@ static void *trace_worker(void *arg)
                 orc_contract_sph(x, p);
                 int cell[3];
                 cell64(p, N, cell, &fd);
+                int amb = jb->decisive ? occ_decision_ambiguous(sc, p, cell, jb->eps) : fd < jb->eps;
+                if (fl && amb) fl[k >> 5] |= 1u << (k & 31);
                 if (jb->decide_f32) {
                     float p32[3];
                     orc32_sph_point(o32, d32, (float)jb->step, k, p32);
                     cell32(p32, N, cell);
                 }
                 if (occ_at(sc, cell)) m[k >> 5] |= 1u << (k & 31);
-                if (fl && fd < jb->eps) fl[k >> 5] |= 1u << (k & 31);
             }
             continue;
         }
@@ -1084,10 +1119,18 @@ static void *trace_worker(void *arg)
             int cell[3];
             orc_point_at(segs, ns, ((double)k + 0.5) * jb->step, p);
             cell64(p, N, cell, &fd);
+            int amb = fd < jb->eps;
+            if (jb->decisive)      /* from the FP64 position, before any FP32 decision replaces cell */
+                amb = occ_decision_ambiguous(sc, p, cell, jb->eps) ||
+                      arc_decision_ambiguous(segs, ns, jb->step, k, jb->eps);
+            if (fl && amb) fl[k >> 5] |= 1u << (k & 31);
             if (jb->decide_f32 && !orc32_sample_cell(&sg, (float)jb->step, k, N, cell)) continue;
             if (occ_at(sc, cell)) m[k >> 5] |= 1u << (k & 31);
-            if (fl && fd < jb->eps) fl[k >> 5] |= 1u << (k & 31);
         }
+        /* the first lattice index past the end may exist in another precision */
+        if (fl && jb->decisive && nlat < 32 * jb->words &&
+            arc_decision_ambiguous(segs, ns, jb->step, nlat, jb->eps))
+            fl[nlat >> 5] |= 1u << (nlat & 31);
     }
     return NULL;
 }
@@ -1097,9 +1140,19 @@ int orc_trace(const orc_scene *sc, const float *cams, int n_cams, int W, int H,
               uint32_t *mask, uint32_t *flags, int words, int32_t *n_lattice, int n_threads,
               int contraction)
 {
+    return orc_trace_flagged(sc, cams, n_cams, W, H, pix, n_pix, step, decide_f32, eps, mask, flags, words,
+                             n_lattice, n_threads, contraction, 0);
+}
+
+int orc_trace_flagged(const orc_scene *sc, const float *cams, int n_cams, int W, int H,
+                      const int32_t *pix, int n_pix, double step, int decide_f32, double eps,
+                      uint32_t *mask, uint32_t *flags, int words, int32_t *n_lattice, int n_threads,
+                      int contraction, int decisive)
+{
     job jb;
     memset(&jb, 0, sizeof jb);
     jb.contraction = contraction;
+    jb.decisive = decisive;
     jb.sc = sc; jb.cams = cams; jb.n_cams = n_cams; jb.W = W; jb.H = H;
     jb.pix = pix; jb.n_pix = n_pix; jb.step = step; jb.decide_f32 = decide_f32; jb.eps = eps;
     jb.mask = mask; jb.flags = flags; jb.words = words; jb.nlat = n_lattice;

@@ -101,6 +101,17 @@ int orc_trace(const orc_scene *sc, const float *cams, int n_cams, int W, int H,
               uint32_t *mask, uint32_t *flags, int words, int32_t *n_lattice, int n_threads,
               int contraction);
 
+/* orc_trace with a choice of flags: decisive 0 flags every sample within eps of a cell face (as
+ * orc_trace); decisive 1 flags, from the FP64 position and arc length, only the samples whose
+ * outcome a move of eps can change: a finest cell of other occupancy within eps, an interior
+ * segment boundary within eps (the contracted ray may jump there), or (k + 1) step within eps
+ * of the total arc length.  Rows also flag lattice index n_lattice when that sample is within eps
+ * of existing. */
+int orc_trace_flagged(const orc_scene *sc, const float *cams, int n_cams, int W, int H,
+                      const int32_t *pix, int n_pix, double step, int decide_f32, double eps,
+                      uint32_t *mask, uint32_t *flags, int words, int32_t *n_lattice, int n_threads,
+                      int contraction, int decisive);
+
 /* Distinct data a set of rays reads (the reuse beside the bandwidth roofline): the render's own
  * evaluated samples (opts as in orc_render) each mark the eight grid voxels of their trilinear
  * interpolation that lie in stored blocks, the index-grid entry of their lowest corner's block,

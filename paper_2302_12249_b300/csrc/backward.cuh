@@ -42,7 +42,8 @@ struct BackwardParams {
 // Add w g at texel `key` of `base` (8 floats per texel; key < 0: nothing), merging with the
 // horizontally adjacent pixel (lane ^ 1) when both add to the same texel: the even lane adds the
 // pair's sum and the odd lane skips its atomics.  m: the lanes executing this call together.
-// Key: int when every texel index fits (the 32-bit variant), else long long.
+// Key: int when every texel index fits (the 32-bit variant), else long long.  The float offset
+// key * 8 is formed in 64 bits, so it cannot wrap whatever the key's type.
 template <typename Key>
 __device__ __forceinline__ void atomic_add8_pair(float *base, Key key, const float g[8], float w, unsigned m)
 {
@@ -60,7 +61,7 @@ __device__ __forceinline__ void atomic_add8_pair(float *base, Key key, const flo
         }
     }
     if (key < 0 || (merge && (lane & 1))) return;
-    float *dst = base + key * 8;
+    float *dst = base + (long long)key * 8;
     atomicAdd(reinterpret_cast<float4 *>(dst), make_float4(v[0], v[1], v[2], v[3]));
     atomicAdd(reinterpret_cast<float4 *>(dst + 4), make_float4(v[4], v[5], v[6], v[7]));
 }

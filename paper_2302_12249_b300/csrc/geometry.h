@@ -33,14 +33,16 @@ inline bool offsets_fit_32(const merf_scene_desc &d)
            d.n_occ_levels >= 1 && d.occ_res[0] <= kMaxOccRes32;
 }
 
-// True when every offset of a dense float scene fits 32 bits as a signed value: the grid holds
-// L^3 texels of two float4 (2 L^3 float4 offsets), the planes 3 R^2 texels (6 R^2), and the finest
-// occupancy level at most kMaxOccRes32^3 cells.
+// True when every offset of a dense float scene fits 32 bits as a signed value, counted in floats:
+// the grid holds L^3 texels of 8 floats (8 L^3 float offsets; the forward pass addresses them as
+// 2 L^3 float4, the adjoint's gradient scatter as 8 floats per texel), the planes 3 R^2 texels
+// (24 R^2 floats), and the finest occupancy level at most kMaxOccRes32^3 cells.  So L <= 645 and
+// R <= 9459.
 inline bool dense_offsets_fit_32(const merf_scene_desc &d)
 {
     const unsigned long long L = (unsigned long long)d.grid_res, R = (unsigned long long)d.plane_res;
-    return d.grid_res >= 0 && d.plane_res >= 0 && 2ull * L * L * L <= 0x7fffffffull && 6ull * R * R <= 0x7fffffffull &&
-           d.n_occ_levels >= 1 && d.occ_res[0] <= kMaxOccRes32;
+    return d.grid_res >= 0 && d.plane_res >= 0 && 8ull * L * L * L <= 0x7fffffffull &&
+           24ull * R * R <= 0x7fffffffull && d.n_occ_levels >= 1 && d.occ_res[0] <= kMaxOccRes32;
 }
 
 // True when the gather may use the kernels compiled for the paper's geometry (kGeoPaper): its

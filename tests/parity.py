@@ -14,14 +14,15 @@ RGB_TOL = 1e-4          # max |dRGB| per channel against the FP64 oracle (FP32 p
 TERM_BAND = 1e-3
 
 
-def oracle_rgb(osc, cams, W, H, step, pix=None, early_term=True, t_term=2e-4, threads=None):
-    """Two oracle renders (threshold moved down / up by TERM_BAND): [n, ORC_OUT] each."""
+def oracle_rgb(osc, cams, W, H, step, pix=None, early_term=True, t_term=2e-4, threads=None, decide_f32=True):
+    """Two oracle renders (threshold moved down / up by TERM_BAND): [n, ORC_OUT] each.  decide_f32
+    False: lattice and occupancy decisions of the FP64 definition itself."""
     lo = oracle.render(osc, cams, W, H, step, pix=pix, t_term=t_term * (1 - TERM_BAND), early_term=early_term,
-                       decide_f32=True, threads=threads)
+                       decide_f32=decide_f32, threads=threads)
     if not early_term:
         return lo, lo
     hi = oracle.render(osc, cams, W, H, step, pix=pix, t_term=t_term * (1 + TERM_BAND), early_term=early_term,
-                       decide_f32=True, threads=threads)
+                       decide_f32=decide_f32, threads=threads)
     return lo, hi
 
 

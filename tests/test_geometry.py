@@ -108,18 +108,34 @@ def test_grid_only_scenes_take_32_bit_offsets_only_when_they_fit(geolib):
 
 
 def test_dense_scenes_take_32_bit_offsets_only_when_they_fit(geolib):
-    """Dense float scenes hold two float4 per grid texel and per plane texel; the adjoint keys texel
-    indices as signed 32-bit values, so 2 L^3 and 6 R^2 must stay below 2^31."""
+    """Dense float scenes hold 8 floats per grid texel and per plane texel.  The 32-bit variant forms
+    float4 offsets in the forward pass and float offsets (8 per texel) in the adjoint's gradient
+    scatter, so the bound is on floats: 8 L^3 and 24 R^2 must stay below 2^31, which admits
+    L <= 645 and R <= 9459.  (An earlier bound of 2 L^3 admitted L up to 1023, where texel key * 8
+    wrapped a signed 32-bit value.)"""
     def dense(L, R, occ=(128, 64, 32, 16)):
         d = paper_desc(occ=occ)
         d.storage, d.grid_res, d.plane_res = merf.STORAGE_F32_DENSE, L, R
         return d
     assert geolib.host_gather_geometry(ct.byref(dense(128, 512))) == GEO_DENSE_32
-    L = max(l for l in range(1, 2000) if 2 * l ** 3 <= 2 ** 31 - 1)
-    assert L == 1023
+    L = max(l for l in range(1, 2000) if 8 * l ** 3 <= 2 ** 31 - 1)
+    assert L == 645
+    # the largest float offset of the adjoint's grid scatter: last texel's last float
+    assert (L ** 3 - 1) * 8 + 7 <= 2 ** 31 - 1 < ((L + 1) ** 3 - 1) * 8 + 7
     assert geolib.host_gather_geometry(ct.byref(dense(L, 512))) == GEO_DENSE_32
     assert geolib.host_gather_geometry(ct.byref(dense(L + 1, 512))) == GEO_RUNTIME
-    R = max(r for r in range(1, 30000) if 6 * r * r <= 2 ** 31 - 1)
+    assert geolib.host_gather_geometry(ct.byref(dense(1023, 512))) == GEO_RUNTIME
+    R = max(r for r in range(1, 30000) if 24 * r * r <= 2 ** 31 - 1)
+    assert R == 9459
+    assert (3 * R * R - 1) * 8 + 7 <= 2 ** 31 - 1 < (3 * (R + 1) ** 2 - 1) * 8 + 7
     assert geolib.host_gather_geometry(ct.byref(dense(128, R))) == GEO_DENSE_32
     assert geolib.host_gather_geometry(ct.byref(dense(128, R + 1))) == GEO_RUNTIME
     assert geolib.host_gather_geometry(ct.byref(dense(128, 512, occ=(2048, 64)))) == GEO_RUNTIME
+
+
+def test_adjoint_scatter_widens_the_float_offset():
+    """The gradient scatter forms its float offset in 64 bits (key * 8 with a 32-bit key could wrap
+    if the bound above were ever loosened); the source states it."""
+    src = open(os.path.join(ROOT, "paper_2302_12249_b300", "csrc", "backward.cuh")).read()
+    assert "base + (long long)key * 8" in src
+    assert "base + key * 8" not in src
