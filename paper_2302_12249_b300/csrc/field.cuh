@@ -4,7 +4,7 @@
 // low-resolution 3D grid plus bilinear interpolation in three high-resolution planes, each
 // texel dequantised as 2 m k / 255 - m (m = 14 for density, 7 otherwise).  Because the
 // dequantisation is affine and interpolation weights sum to one, the kernel interpolates raw
-// byte values and dequantises the sum once per channel:
+// byte values (exactly, in integers: dot_sums below) and dequantises the sum once per channel:
 //     t~_c = (2 m_c / 255) * sum_w w k_c  -  m_c * (W_V + 3),
 // with W_V the weight of the 3D-grid corners that are stored (a voxel of a block that is not
 // stored contributes nothing).  A grid-only scene (no planes, R = 0: the SNeRG++-style baseline
@@ -74,20 +74,6 @@ __device__ __forceinline__ void plane_coord(float p, float scale, int half, int 
     f = __fadd_rn(__fsub_rn(a, n), 0.5f);
 }
 
-// Byte b of a 32-bit word as a float: the byte is placed in the low mantissa bits of 2^23
-// (one byte permute) and 2^23 is subtracted; both steps are exact.
-template <int b>
-__device__ __forceinline__ float byte_f(uint32_t w)
-{
-    return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u | b)) - 8388608.0f;
-}
-
-template <int c>
-__device__ __forceinline__ float byte_of(uint2 v)
-{
-    return c < 4 ? byte_f<c & 3>(v.x) : byte_f<c & 3>(v.y);
-}
-
 // The 20 texels of one sample (8 grid corners, 4 texels in each plane) and their weights.
 struct Taps {
     uint2 v[20];
@@ -111,12 +97,6 @@ __device__ __forceinline__ float stored_weight(const Taps &t, uint32_t mask)
 #pragma unroll
     for (int c = 0; c < 8; ++c) wv += ((mask >> c) & 1u) ? grid_w(t, c) : 0.0f;
     return wv;
-}
-
-__device__ __forceinline__ float plane_w(const Taps &t, int q, int c)
-{
-    const int ca = q == 0 ? 1 : 0, ra = q == 2 ? 1 : 2;
-    return ((c & 1) ? t.fu[ca] : 1.0f - t.fu[ca]) * ((c & 2) ? t.fu[ra] : 1.0f - t.fu[ra]);
 }
 
 // Lowest corner in a block that is not stored: every corner is looked up on its own.
@@ -247,164 +227,153 @@ __device__ __forceinline__ float dequant_density(float k, float wsum)
 }
 
 
-// Bytes b and b + 1 of a 32-bit word as two floats (byte_f on both, the subtraction packed).
-template <int b>
-__device__ __forceinline__ float2 byte_pair_f(uint32_t w)
-{
-    const float2 m = make_float2(__uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u | b)),
-                                 __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u | (b + 1))));
-    return __fadd2_rn(m, make_float2(-8388608.0f, -8388608.0f));
-}
-
-// All eight pre-activations in one pass over the taps (tap-major): each tap's weight is formed
-// once and its eight bytes are accumulated into four running float2 sums with packed FP32
-// arithmetic (each lane rounds exactly as the scalar fmaf does).
-template <int i>
-__device__ __forceinline__ void accumulate_tap(const Taps &t, float2 acc[4])
-{
-    const float w = i < 8 ? grid_w(t, i) : plane_w(t, (i - 8) >> 2, (i - 8) & 3);
-    const float2 ww = make_float2(w, w);
-    acc[0] = __ffma2_rn(ww, byte_pair_f<0>(t.v[i].x), acc[0]);
-    acc[1] = __ffma2_rn(ww, byte_pair_f<2>(t.v[i].x), acc[1]);
-    acc[2] = __ffma2_rn(ww, byte_pair_f<0>(t.v[i].y), acc[2]);
-    acc[3] = __ffma2_rn(ww, byte_pair_f<2>(t.v[i].y), acc[3]);
-}
-
-// Weighted byte sums of all eight channels, as the pairs (0, 1), (2, 3), (4, 5), (6, 7), over
-// the first nt taps (20: grid and planes; 8: grid only).
-template <int nt = 20>
-__device__ __forceinline__ void byte_sums_u8(const Taps &t, float2 acc[4])
-{
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[j] = make_float2(0.0f, 0.0f);
-    accumulate_tap<0>(t, acc);  accumulate_tap<1>(t, acc);  accumulate_tap<2>(t, acc);
-    accumulate_tap<3>(t, acc);  accumulate_tap<4>(t, acc);  accumulate_tap<5>(t, acc);
-    accumulate_tap<6>(t, acc);  accumulate_tap<7>(t, acc);
-    if constexpr (nt > 8) {
-        accumulate_tap<8>(t, acc);  accumulate_tap<9>(t, acc);  accumulate_tap<10>(t, acc);
-        accumulate_tap<11>(t, acc); accumulate_tap<12>(t, acc); accumulate_tap<13>(t, acc);
-        accumulate_tap<14>(t, acc); accumulate_tap<15>(t, acc); accumulate_tap<16>(t, acc);
-        accumulate_tap<17>(t, acc); accumulate_tap<18>(t, acc); accumulate_tap<19>(t, acc);
-    }
-}
-
 // ---------------------------------------------------------------------------------------------
-// Reduced-precision byte sums (the precision form).  Density and channel 1 keep the FP32 packed
-// pair of the FP32 path (so density, opacity and transmittance are those of the FP32 path bit
-// for bit); channels (2, 3), (4, 5), (6, 7) go through 16-bit pairs.  Within each source (grid,
-// P_x, P_y, P_z) every tap is taken relative to the source's first tap: the difference of two
-// bytes is an exact integer in [-255, 255] (exact in half and in bfloat16), so the 16-bit
-// arithmetic only carries the interpolation corrections sum_i w_i (b_i - b_first), with weights
-// rounded to that type.  A grid corner that is not stored holds zero bytes, so with the
-// unmasked trilinear weights summing to one the first taps enter with weight one; their sum is
-// an integer <= 1020, exact in either form:
-//     K_c = b_first,V + b_first,Px + b_first,Py + b_first,Pz + sum of corrections.
-// FP16: one byte permute gives a half2 of 1024 + byte for two channels (the half 0x64XX is
-// 1024 + XX), and the difference of two such halves is the exact byte difference.  BF16 (7
-// stored mantissa bits cannot hold 1024 + byte) takes the differences in FP32 from the packed
-// 2^23 + byte floats; their high halves are their exact bfloat16 values.
+// Weighted byte sums by integer dot products.  The interpolated value of channel c is
+// K_c = sum_i w_i b_ic over the taps i (8 grid corners, then 4 texels per plane), and bytes are
+// exact integers, so the sum is formed in integer arithmetic from fixed-point weights: the taps
+// are taken in pairs (i, j); one byte permute interleaves two channels of the pair's texels as
+// (b_ic, b_jc, b_ic', b_jc'), and dp2a multiplies a byte pair by a pair of 16-bit weights
+// (w_i, w_j) and adds to a 32-bit accumulator, exactly.  A pair of taps and two channels cost one
+// permute and two dot products, where float arithmetic needs a permute per byte, a subtraction and
+// a multiply-add per two bytes.
+//
+// Weights.  One fused multiply-add forms each weight's last product and rounds it to the integer
+// round(w S) in the low mantissa bits of 2^23 + w S (S <= 2^22, so the exponent stays that of
+// 2^23 and bit 23 stays zero).
+// * Two-level (the FP32 form, and density in every form): S = 2^22, the weight split into its low
+//   16 bits and its bits 16..22 (<= 64), two dot products per byte pair, and
+//   K_c = (H_c 2^16 + L_c) / 2^22.  The weight's rounding (2^-23) bounds the error of K_c by
+//   20 * 255 * 2^-23 < 6.1e-4 byte units, the same as float accumulation of the sum to 1020
+//   (half an ulp of 1020 per step); L_c < 20 * 65535 * 255 < 2^32 cannot overflow.
+// * One-level (appearance channels 1..7 of the 16-bit forms): S = 65535, one dot product,
+//   K_c = L_c / 65535, error at most 20 * 255 / 131070 < 0.039 byte units (typically 1e-3),
+//   within the 16-bit forms' tolerance and more accurate than half-precision weights (2^-11).
+// A grid corner that is not stored holds zero bytes, so it adds nothing whatever its weight.
 
-__device__ __forceinline__ __half2 magic_h2(uint32_t w, uint32_t sel)
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel)
 {
-    const uint32_t u = __byte_perm(w, 0x64646464u, sel);
-    __half2 h;
-    memcpy(&h, &u, 4);
-    return h;
+    // PTX prmt, default mode: a selector nibble with its high bit set replicates the selected
+    // byte's sign bit (here always zero) over the output byte
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
 }
 
-// 2^23 + byte for bytes b and b + 1 of a word (no subtraction).
-template <int b>
-__device__ __forceinline__ float2 byte_pair_magic(uint32_t w)
+// c + a.h0 * b.b0 + a.h1 * b.b1 (lo) or c + a.h0 * b.b2 + a.h1 * b.b3 (hi), unsigned
+__device__ __forceinline__ uint32_t dp2a_lo(uint32_t a, uint32_t b, uint32_t c)
 {
-    return make_float2(__uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u | b)),
-                       __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u | (b + 1))));
+    uint32_t d;
+    asm("dp2a.lo.u32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ uint32_t dp2a_hi(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("dp2a.hi.u32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
 }
 
-template <int kPrec>
-struct LpAcc;
-template <>
-struct LpAcc<1> {                        // FP16
-    __half2 first[3], fsum[3], corr[3];
-};
-template <>
-struct LpAcc<2> {                        // BF16
-    float2 nfirst[3], fsum[3];           // nfirst: -(2^23 + first byte)
-    __nv_bfloat162 corr[3];
-};
+constexpr float kW22 = 4194304.0f;            // two-level weight scale 2^22
+constexpr float kW16 = 65535.0f;              // one-level weight scale
+constexpr float kWMagic = 8388608.0f;         // 2^23
 
-template <int kPrec, int i>
-__device__ __forceinline__ void lp_tap(const Taps &t, float2 &k01, LpAcc<kPrec> &a)
+// 2^23 + round(a b): a weight's last product, rounded to an integer in the low mantissa bits.
+__device__ __forceinline__ uint32_t weight_word(float a, float b)
 {
-    constexpr bool first = i == 0 || i == 8 || i == 12 || i == 16;
-    const float w = i < 8 ? grid_w(t, i) : plane_w(t, (i - 8) >> 2, (i - 8) & 3);
-    k01 = __ffma2_rn(make_float2(w, w), byte_pair_f<0>(t.v[i].x), k01);
-    if constexpr (kPrec == 1) {
-        const __half2 m[3] = {magic_h2(t.v[i].x, 0x4342u), magic_h2(t.v[i].y, 0x4140u),
-                              magic_h2(t.v[i].y, 0x4342u)};
-        if constexpr (first) {
-            const __half2 mag = __float2half2_rn(1024.0f);
-#pragma unroll
-            for (int p = 0; p < 3; ++p) {
-                a.first[p] = m[p];
-                a.fsum[p] = i == 0 ? __hsub2(m[p], mag) : __hadd2(a.fsum[p], __hsub2(m[p], mag));
-            }
-        } else {
-            const __half2 w2 = __float2half2_rn(w);
-#pragma unroll
-            for (int p = 0; p < 3; ++p) a.corr[p] = __hfma2(w2, __hsub2(m[p], a.first[p]), a.corr[p]);
-        }
-    } else {
-        const float2 m[3] = {byte_pair_magic<2>(t.v[i].x), byte_pair_magic<0>(t.v[i].y),
-                             byte_pair_magic<2>(t.v[i].y)};
-        if constexpr (first) {
-            const float2 nmag = make_float2(-8388608.0f, -8388608.0f);
-#pragma unroll
-            for (int p = 0; p < 3; ++p) {
-                a.nfirst[p] = make_float2(-m[p].x, -m[p].y);
-                a.fsum[p] = i == 0 ? __fadd2_rn(m[p], nmag) : __fadd2_rn(a.fsum[p], __fadd2_rn(m[p], nmag));
-            }
-        } else {
-            const __nv_bfloat162 w2 = __float2bfloat162_rn(w);
-#pragma unroll
-            for (int p = 0; p < 3; ++p) {
-                // d holds exact integers |d| <= 255, which bfloat16 keeps exactly; a bfloat16 is
-                // the high half of the FP32 word, so one byte permute packs the pair
-                const float2 d = __fadd2_rn(m[p], a.nfirst[p]);
-                const uint32_t u = __byte_perm(__float_as_uint(d.x), __float_as_uint(d.y), 0x7632u);
-                __nv_bfloat162 db;
-                memcpy(&db, &u, 4);
-                a.corr[p] = __hfma2(w2, db, a.corr[p]);
-            }
-        }
-    }
+    return __float_as_uint(fmaf(a, b, kWMagic));
 }
 
-// Weighted byte sums in the layout of byte_sums_u8: k[0] = channels (0, 1) in FP32, k[1..3] =
-// channels (2, 3), (4, 5), (6, 7) from their 16-bit corrections.
-template <int kPrec, int nt = 20>
-__device__ __forceinline__ void byte_sums_lp(const Taps &t, float2 k[4])
+// Weight words of the first nt taps at scale S (grid corners: trilinear; plane q: bilinear in
+// its column axis (1, 0, 0)[q] and row axis (2, 2, 1)[q]).
+template <int nt>
+__device__ __forceinline__ void weight_words(const Taps &t, float S, uint32_t w[nt])
 {
-    LpAcc<kPrec> a;
+    const float gx = 1.0f - t.fx, gy = 1.0f - t.fy;
+    const float xy[4] = {gx * gy, t.fx * gy, gx * t.fy, t.fx * t.fy};
+    const float z1 = t.fz * S, z0 = (1.0f - t.fz) * S;
 #pragma unroll
-    for (int p = 0; p < 3; ++p) {
-        if constexpr (kPrec == 1) a.corr[p] = __float2half2_rn(0.0f);
-        else a.corr[p] = __float2bfloat162_rn(0.0f);
-    }
-    k[0] = make_float2(0.0f, 0.0f);
-    lp_tap<kPrec, 0>(t, k[0], a);  lp_tap<kPrec, 1>(t, k[0], a);  lp_tap<kPrec, 2>(t, k[0], a);
-    lp_tap<kPrec, 3>(t, k[0], a);  lp_tap<kPrec, 4>(t, k[0], a);  lp_tap<kPrec, 5>(t, k[0], a);
-    lp_tap<kPrec, 6>(t, k[0], a);  lp_tap<kPrec, 7>(t, k[0], a);
+    for (int c = 0; c < 8; ++c) w[c] = weight_word(xy[c & 3], (c & 4) ? z1 : z0);
     if constexpr (nt > 8) {
-        lp_tap<kPrec, 8>(t, k[0], a);  lp_tap<kPrec, 9>(t, k[0], a);  lp_tap<kPrec, 10>(t, k[0], a);
-        lp_tap<kPrec, 11>(t, k[0], a); lp_tap<kPrec, 12>(t, k[0], a); lp_tap<kPrec, 13>(t, k[0], a);
-        lp_tap<kPrec, 14>(t, k[0], a); lp_tap<kPrec, 15>(t, k[0], a); lp_tap<kPrec, 16>(t, k[0], a);
-        lp_tap<kPrec, 17>(t, k[0], a); lp_tap<kPrec, 18>(t, k[0], a); lp_tap<kPrec, 19>(t, k[0], a);
-    }
+        const float u1[3] = {t.fu[0], t.fu[1], t.fu[2]};
+        const float u0[3] = {1.0f - t.fu[0], 1.0f - t.fu[1], 1.0f - t.fu[2]};
+        const float r1[3] = {0.0f, t.fu[1] * S, t.fu[2] * S};       // rows run along y or z
+        const float r0[3] = {0.0f, u0[1] * S, u0[2] * S};
 #pragma unroll
-    for (int p = 0; p < 3; ++p) {
-        if constexpr (kPrec == 1) k[1 + p] = __fadd2_rn(__half22float2(a.fsum[p]), __half22float2(a.corr[p]));
-        else k[1 + p] = __fadd2_rn(a.fsum[p], __bfloat1622float2(a.corr[p]));
+        for (int q = 0; q < 3; ++q) {
+            const int ca = q == 0 ? 1 : 0, ra = q == 2 ? 1 : 2;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                w[8 + 4 * q + c] = weight_word((c & 1) ? u1[ca] : u0[ca], (c & 2) ? r1[ra] : r0[ra]);
+        }
     }
+}
+
+// The byte pairs of taps a and b: channels (0, 1), (2, 3), (4, 5), (6, 7), each as
+// (a.c, b.c, a.c', b.c').
+__device__ __forceinline__ void pair_bytes(uint2 a, uint2 b, uint32_t B[4])
+{
+    B[0] = prmt(a.x, b.x, 0x5140u);
+    B[1] = prmt(a.x, b.x, 0x7362u);
+    B[2] = prmt(a.y, b.y, 0x5140u);
+    B[3] = prmt(a.y, b.y, 0x7362u);
+}
+
+// Integer weighted byte sums of one sample over the first nt taps.  kPrec 0 (FP32): every
+// channel two-level, K_c = (hi[c] 2^16 + lo[c]) / 2^22.  kPrec 1, 2 (the 16-bit forms): density
+// two-level as in FP32 (so density, opacity and transmittance equal the FP32 form's bit for bit),
+// channels 1..7 one-level, K_c = lo[c] / 65535 (hi[1..7] unused).
+template <int kPrec>
+struct DotSums {
+    uint32_t lo[8], hi[kPrec == 0 ? 8 : 1];
+};
+
+template <int kPrec, int nt>
+__device__ __forceinline__ void dot_sums(const Taps &t, DotSums<kPrec> &s)
+{
+    uint32_t w[nt];
+    weight_words<nt>(t, kW22, w);
+    uint32_t w16[kPrec == 0 ? 1 : nt];
+    if constexpr (kPrec != 0) weight_words<nt>(t, kW16, w16);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s.lo[c] = 0u;
+#pragma unroll
+    for (int c = 0; c < (kPrec == 0 ? 8 : 1); ++c) s.hi[c] = 0u;
+#pragma unroll
+    for (int p = 0; p < nt / 2; ++p) {
+        const uint32_t wl = prmt(w[2 * p], w[2 * p + 1], 0x5410u);     // low 16 bits of both
+        const uint32_t wh = prmt(w[2 * p], w[2 * p + 1], 0xE6A2u);     // bits 16..22, zero-extended
+        uint32_t B[4];
+        pair_bytes(t.v[2 * p], t.v[2 * p + 1], B);
+        if constexpr (kPrec == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                s.lo[2 * q] = dp2a_lo(wl, B[q], s.lo[2 * q]);
+                s.lo[2 * q + 1] = dp2a_hi(wl, B[q], s.lo[2 * q + 1]);
+                s.hi[2 * q] = dp2a_lo(wh, B[q], s.hi[2 * q]);
+                s.hi[2 * q + 1] = dp2a_hi(wh, B[q], s.hi[2 * q + 1]);
+            }
+        } else {
+            const uint32_t ws = prmt(w16[2 * p], w16[2 * p + 1], 0x5410u);
+            s.lo[0] = dp2a_lo(wl, B[0], s.lo[0]);
+            s.hi[0] = dp2a_lo(wh, B[0], s.hi[0]);
+            s.lo[1] = dp2a_hi(ws, B[0], s.lo[1]);
+#pragma unroll
+            for (int q = 1; q < 4; ++q) {
+                s.lo[2 * q] = dp2a_lo(ws, B[q], s.lo[2 * q]);
+                s.lo[2 * q + 1] = dp2a_hi(ws, B[q], s.lo[2 * q + 1]);
+            }
+        }
+    }
+}
+
+// Density pre-activation from its two-level sums: (28 / 255) K_0 - 14 W, where W = W_V + 3 is
+// the total interpolation weight of the sources (the planes' weights sum to one each; W = W_V for
+// a grid-only scene).  Every path that evaluates a uint8 scene's density calls this one
+// expression, so their opacities agree bit for bit.
+__device__ __forceinline__ float dequant_density(uint32_t lo, uint32_t hi, float wsum)
+{
+    constexpr float A = 28.0f / 255.0f;
+    return fmaf(__uint2float_rn(lo), A * (1.0f / kW22), fmaf(__uint2float_rn(hi), A * (65536.0f / kW22), -14.0f * wsum));
 }
 
 // Dense float storage: all eight channels of all 20 taps, summed.

@@ -83,18 +83,25 @@ __device__ __forceinline__ AppArg app_arg(const float app[7])
     return a;
 }
 
-// From the weighted byte sums of the uint8 path: x = (14 / 255) k - 7 W (W the sources' total
-// weight, as in dequant_density), so y = k (-14 log2(e) / 255) + 7 log2(e) W, one fused
-// multiply-add per channel.
-__device__ __forceinline__ AppArg app_arg_u8(const float2 k[4], float wsum)
+// From the two-level integer sums of the FP32 uint8 path: x = (14 / 255) K - 7 W (W the sources'
+// total weight, as in dequant_density) with K = (H 2^16 + L) / 2^22, so
+// y = -x log2(e) = L A / 2^22 + (H A / 2^6 + 7 log2(e) W), A = -14 log2(e) / 255: two fused
+// multiply-adds per channel, in pairs.
+__device__ __forceinline__ float2 u2f2(uint32_t a, uint32_t b)
+{
+    return make_float2(__uint2float_rn(a), __uint2float_rn(b));
+}
+
+__device__ __forceinline__ AppArg app_arg_u8(const DotSums<0> &k, float wsum)
 {
     const float A = -kLog2e * 14.0f / 255.0f, b = (7.0f * kLog2e) * wsum;
-    const float2 A2 = make_float2(A, A), b2 = make_float2(b, b);
+    const float Al = A * (1.0f / kW22), Ah = A * (65536.0f / kW22);
+    const float2 Al2 = make_float2(Al, Al), Ah2 = make_float2(Ah, Ah), b2 = make_float2(b, b);
     AppArg a;
-    a.y1 = fmaf(k[0].y, A, b);
-    a.y23 = __ffma2_rn(k[1], A2, b2);
-    a.y45 = __ffma2_rn(k[2], A2, b2);
-    a.y67 = __ffma2_rn(k[3], A2, b2);
+    a.y1 = fmaf(__uint2float_rn(k.lo[1]), Al, fmaf(__uint2float_rn(k.hi[1]), Ah, b));
+    a.y23 = __ffma2_rn(u2f2(k.lo[2], k.lo[3]), Al2, __ffma2_rn(u2f2(k.hi[2], k.hi[3]), Ah2, b2));
+    a.y45 = __ffma2_rn(u2f2(k.lo[4], k.lo[5]), Al2, __ffma2_rn(u2f2(k.hi[4], k.hi[5]), Ah2, b2));
+    a.y67 = __ffma2_rn(u2f2(k.lo[6], k.lo[7]), Al2, __ffma2_rn(u2f2(k.hi[6], k.hi[7]), Ah2, b2));
     return a;
 }
 
@@ -128,17 +135,19 @@ __device__ __forceinline__ float tanh_approx(float x)
 }
 
 // 16-bit forms: sigmoid(x) = (1 + tanh(x / 2)) / 2, so AppArg holds t = x / 2 =
-// (7 / 255) k - 3.5 W, and compositing accumulates only (w / 2) tanh(t); the constant halves
-// sum to (1 - T) / 2 per ray (the weights alpha_i T_i sum to 1 - T), added once at the end.
-__device__ __forceinline__ AppArg app_arg_u8_half(const float2 k[4], float wsum)
+// (7 / 255) K - 3.5 W with the one-level sums K = L / 65535, and compositing accumulates only
+// (w / 2) tanh(t); the constant halves sum to (1 - T) / 2 per ray (the weights alpha_i T_i sum
+// to 1 - T), added once at the end.
+template <int kPrec>
+__device__ __forceinline__ AppArg app_arg_u8_half(const DotSums<kPrec> &k, float wsum)
 {
-    const float A = 7.0f / 255.0f, b = -3.5f * wsum;
+    const float A = 7.0f / 255.0f / kW16, b = -3.5f * wsum;
     const float2 A2 = make_float2(A, A), b2 = make_float2(b, b);
     AppArg a;
-    a.y1 = fmaf(k[0].y, A, b);
-    a.y23 = __ffma2_rn(k[1], A2, b2);
-    a.y45 = __ffma2_rn(k[2], A2, b2);
-    a.y67 = __ffma2_rn(k[3], A2, b2);
+    a.y1 = fmaf(__uint2float_rn(k.lo[1]), A, b);
+    a.y23 = __ffma2_rn(u2f2(k.lo[2], k.lo[3]), A2, b2);
+    a.y45 = __ffma2_rn(u2f2(k.lo[4], k.lo[5]), A2, b2);
+    a.y67 = __ffma2_rn(u2f2(k.lo[6], k.lo[7]), A2, b2);
     return a;
 }
 
@@ -532,13 +541,12 @@ __device__ __forceinline__ void eval_field(const FieldView &fv, float p0, float 
     if constexpr (kStorage == 0) {
         Taps tp;
         gather_u8<kGeo>(fv, p0, p1, p2, tp);
-        float2 k[4];
-        if constexpr (kPrec == 0) byte_sums_u8<kTaps<kGeo>>(tp, k);
-        else byte_sums_lp<kPrec, kTaps<kGeo>>(tp, k);   // FP16 / BF16 appearance; density FP32
+        DotSums<kPrec> k;
+        dot_sums<kPrec, kTaps<kGeo>>(tp, k);      // 16-bit forms: one-level appearance weights
         const float wsum = tp.wv + (float)kPlaneSources<kGeo>;
-        dens = dequant_density(k[0].x, wsum);
+        dens = dequant_density(k.lo[0], k.hi[0], wsum);
         if constexpr (kPrec == 0) ya = app_arg_u8(k, wsum);
-        else ya = app_arg_u8_half(k, wsum);
+        else ya = app_arg_u8_half<kPrec>(k, wsum);
     } else {
         float all[8];
         field_f32<kGeo>(fv, p0, p1, p2, all);
