@@ -373,44 +373,35 @@ def _spherical_ablation(gs, merf_ref, steps=5, warmup=3):
 SERVE_RES = [(256, 256), (640, 360), (1280, 720), (1920, 1080)]
 
 
-def _serving(gs_first, n_requests: int, rate: float = 200.0, seed_arrivals: int = 4000, max_tiles: int = 16384):
-    """Serving form: four resident paper-scale scenes, Poisson arrivals, random scene and orbit
-    camera, resolution uniform over SERVE_RES, FP16 continuous batching.  Latency is measured by the
-    library from submission to the image being in host memory."""
+def _serving_stream(srv, n_scenes: int, n_requests: int, rate, seed_arrivals: int, bufs) -> dict:
+    """One request stream through a running server.  rate: Poisson arrivals per second, or None for
+    saturation (every request offered at once; in flight as many as the host buffers allow).
+    Returns latency percentiles overall and per resolution, and where the latency went
+    (merf_request_timing: admission, queue, render, copy-back), for all requests and for the
+    slowest 1 %."""
     import queue
     import threading
-    import torch
-    from paper_2302_12249_b300 import merf, synth
-    scenes = [gs_first] + [merf.Scene(synth.make_scene("paper", seed=synth.SEED_SCENE + k)) for k in (1, 2, 3)]
-    free_b, total_b = torch.cuda.mem_get_info()
-    pool = int(min(4 << 30, free_b // 4))
-    srv = merf.Server(scenes, pool_bytes=pool, step=STEP, max_tiles_per_iter=max_tiles, precision=merf.PREC_FP16)
+    from paper_2302_12249_b300 import synth
     rng = np.random.default_rng(seed_arrivals)
-    gaps = rng.exponential(1.0 / rate, size=n_requests)
-    which = rng.integers(0, len(scenes), size=n_requests)
+    gaps = rng.exponential(1.0 / rate, size=n_requests) if rate else np.zeros(n_requests)
+    which = rng.integers(0, n_scenes, size=n_requests)
     res = rng.integers(0, len(SERVE_RES), size=n_requests)
     radius = rng.uniform(1.2, 3.0, size=n_requests)
     az = rng.uniform(0, 2 * math.pi, size=n_requests)
     el = np.radians(rng.uniform(-30, 30, size=n_requests))
-    bufs = {r: queue.Queue() for r in range(len(SERVE_RES))}
-    for r, (W, H) in enumerate(SERVE_RES):
-        for _ in range(48):
-            bufs[r].put(torch.empty((H, W, 3), dtype=torch.float32, pin_memory=True))
-    # warm-up: one request per resolution
-    for r, (W, H) in enumerate(SERVE_RES):
-        b = bufs[r].get()
-        cam = synth.camera_record(synth.look_at([2.0, 0.0, 0.3]), W, H)
-        srv.wait(srv.submit(0, cam, W, H, b))
-        bufs[r].put(b)
     submitted = queue.Queue()
+    phases = ("admit_s", "queue_s", "render_s", "copy_s")
     lat = np.zeros(n_requests)
+    part = np.zeros((n_requests, len(phases)))
     lags = np.zeros(n_requests)
     blocked = [0]
 
     def collector():
         for k in range(n_requests):
             rid, r, b = submitted.get()
-            lat[k] = srv.wait(rid, timeout=600.0)
+            t = srv.wait_timed(rid, timeout=600.0)
+            lat[k] = t["total_s"]
+            part[k] = [t[p] for p in phases]
             bufs[r].put(b)
 
     th = threading.Thread(target=collector)
@@ -433,21 +424,73 @@ def _serving(gs_first, n_requests: int, rate: float = 200.0, seed_arrivals: int 
         submitted.put((srv.submit(int(which[k]), cam, W, H, b), r, b))
     th.join()
     t_end = time.perf_counter()
-    st = srv.stats()
-    srv.close()
     rays = sum(SERVE_RES[int(r)][0] * SERVE_RES[int(r)][1] for r in res)
+    ms = lambda v: float(v * 1e3)
+    per_res = {}
+    for r, (W, H) in enumerate(SERVE_RES):
+        sel = res == r
+        if sel.any():
+            per_res[f"{W}x{H}"] = {"count": int(sel.sum()), "p50_ms": ms(np.percentile(lat[sel], 50)),
+                                   "p99_ms": ms(np.percentile(lat[sel], 99)),
+                                   "mean_render_ms": ms(part[sel, 2].mean())}
+    tail = lat >= np.percentile(lat, 99)
+    out = {"requests": n_requests, "arrival_rate_per_s": rate if rate else "saturation",
+           "p50_ms": ms(np.percentile(lat, 50)), "p99_ms": ms(np.percentile(lat, 99)),
+           "mean_ms": ms(lat.mean()), "max_ms": ms(lat.max()),
+           "aggregate_mrays_per_s": rays / (t_end - t0) / 1e6,
+           "offered_mrays_per_s": (rays / gaps.sum() / 1e6) if rate else None,
+           "wall_s": t_end - t0, "per_resolution": per_res,
+           "phases_mean_ms": {p[:-2]: ms(part[:, i].mean()) for i, p in enumerate(phases)},
+           "phases_p99_ms": {p[:-2]: ms(np.percentile(part[:, i], 99)) for i, p in enumerate(phases)},
+           "slowest_1pct_phases_mean_ms": {p[:-2]: ms(part[tail, i].mean()) for i, p in enumerate(phases)},
+           "slowest_1pct_resolutions": {f"{W}x{H}": int((res[tail] == r).sum()) for r, (W, H) in enumerate(SERVE_RES)},
+           "submit_lag_p99_ms": ms(np.percentile(lags, 99)), "host_buffer_waits": blocked[0]}
+    return out
+
+
+def _serving(gs_first, n_requests: int, rate: float = 200.0, seed_arrivals: int = 4000, max_tiles: int = 16384,
+             sweep=((300.0, 4000), (400.0, 4000), (None, 2000))):
+    """Serving form: four resident paper-scale scenes, Poisson arrivals, random scene and orbit
+    camera, resolution uniform over SERVE_RES, FP16 continuous batching.  Latency is measured by the
+    library from submission to the image being in host memory.  The configured stream (200
+    requests/s) first, then a sweep of higher rates and saturation on the same server."""
+    import queue
+    import torch
+    from paper_2302_12249_b300 import merf, synth
+    scenes = [gs_first] + [merf.Scene(synth.make_scene("paper", seed=synth.SEED_SCENE + k)) for k in (1, 2, 3)]
+    free_b, total_b = torch.cuda.mem_get_info()
+    pool = int(min(4 << 30, free_b // 4))
+    srv = merf.Server(scenes, pool_bytes=pool, step=STEP, max_tiles_per_iter=max_tiles, precision=merf.PREC_FP16)
+    bufs = {r: queue.Queue() for r in range(len(SERVE_RES))}
+    for r, (W, H) in enumerate(SERVE_RES):
+        for _ in range(48):
+            bufs[r].put(torch.empty((H, W, 3), dtype=torch.float32, pin_memory=True))
+    # warm-up: one request per resolution
+    for r, (W, H) in enumerate(SERVE_RES):
+        b = bufs[r].get()
+        cam = synth.camera_record(synth.look_at([2.0, 0.0, 0.3]), W, H)
+        srv.wait(srv.submit(0, cam, W, H, b))
+        bufs[r].put(b)
+    it0 = srv.stats()["iterations"]
+    main = _serving_stream(srv, len(scenes), n_requests, rate, seed_arrivals, bufs)
+    st = srv.stats()
+    runs = []
+    for k, (r, n) in enumerate(sweep):
+        runs.append(_serving_stream(srv, len(scenes), n, r, seed_arrivals + 1 + k, bufs))
+    srv.close()
     for sc in scenes[1:]:
         sc.close()
-    return {"requests": n_requests, "arrival_rate_per_s": rate, "precision": "fp16", "max_tiles_per_iter": max_tiles,
-            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-            "mean_ms": float(lat.mean() * 1e3), "max_ms": float(lat.max() * 1e3),
-            "aggregate_mrays_per_s": rays / (t_end - t0) / 1e6, "offered_mrays_per_s": rays / gaps.sum() / 1e6,
-            "wall_s": t_end - t0, "iterations": st["iterations"], "peak_admitted": st["peak_admitted"],
-            "pool_mb": st["pool_bytes"] / 1e6, "peak_pool_mb": st["peak_pool_bytes"] / 1e6,
-            "submit_lag_p99_ms": float(np.percentile(lags, 99) * 1e3), "host_buffer_waits": blocked[0],
-            "workload": "4 resident paper-scale scenes (seeds 1000-1003), Poisson arrivals, random scene and "
-                        "orbit (radius U(1.2,3), elevation U(-30,30) deg), resolution uniform over "
-                        "256x256/640x360/1280x720/1920x1080; latency = submit to image in host memory"}
+    main.update({"precision": "fp16", "max_tiles_per_iter": max_tiles, "iterations": st["iterations"] - it0,
+                 "peak_admitted": st["peak_admitted"], "pool_mb": st["pool_bytes"] / 1e6,
+                 "peak_pool_mb": st["peak_pool_bytes"] / 1e6,
+                 "sweep": runs,
+                 "workload": "4 resident paper-scale scenes (seeds 1000-1003), Poisson arrivals, random scene and "
+                             "orbit (radius U(1.2,3), elevation U(-30,30) deg), resolution uniform over "
+                             "256x256/640x360/1280x720/1920x1080; latency = submit to image in host memory, split "
+                             "into admission (pool memory), queue (to the first launch of its tiles), render (to "
+                             "the end of its last iteration) and copy-back; sweep: 300 and 400 requests/s and "
+                             "saturation (every request offered at once, at most 48 in flight per resolution)"})
+    return main
 
 
 def run_reference(args):

@@ -231,6 +231,14 @@ merf_status merf_trace(const merf_scene *scene, const merf_camera *cams, int n_c
 merf_status merf_scene_set_dense(merf_scene *scene, const float *d_grid, const float *d_planes,
                                  const float *d_mlp, void *stream);
 
+/* How many times merf_scene_set_dense has replaced this scene's parameters (0 after upload; 0 for a
+ * NULL scene).  The adjoint differentiates at the parameters the scene holds when it runs, so a
+ * caller that keeps a forward pass for a later backward records this count at the forward and,
+ * if it has changed, installs that forward's parameters again before the adjoint (the Python
+ * autograd wrapper does so).  Host only, no synchronisation: the count changes when the copies
+ * are queued. */
+unsigned long long merf_scene_param_version(const merf_scene *scene);
+
 /* Adjoint of merf_render for dense float scenes in FP32 (Eq. 1, Eq. 2, Sec. 3.1, App. B): given
  * d_out = dL/dC (device float32 [n_cams][H][W][3]), accumulate dL/dgrid, dL/dplanes and dL/dmlp
  * into g_grid, g_planes, g_mlp (device, shapes of merf_scene_set_dense's arguments; the caller
@@ -307,6 +315,19 @@ merf_status merf_server_submit(merf_server *srv, int scene, const merf_camera *c
  * once per request.  A cancelled request returns MERF_ERR_CANCELLED (latency: to its release), one
  * that failed on the device MERF_ERR_CUDA. */
 merf_status merf_server_wait(merf_server *srv, uint64_t req_id, double timeout_s, double *latency_s);
+
+/* Where a request's latency went, in seconds (host clock, sampled by the server thread, which
+ * polls every 50 us at most): admit_s from submission to admission by pool memory, queue_s from
+ * admission to the launch of the first iteration carrying its tiles, render_s from there to the
+ * completion of the last iteration carrying its tiles, copy_s from there to the image in host
+ * memory.  The four add up to total_s, the latency merf_server_wait reports. */
+typedef struct merf_request_timing {
+    double total_s, admit_s, queue_s, render_s, copy_s;
+} merf_request_timing;
+
+/* merf_server_wait that also fills *timing (may be NULL) on completion. */
+merf_status merf_server_wait_timed(merf_server *srv, uint64_t req_id, double timeout_s, double *latency_s,
+                                   merf_request_timing *timing);
 
 /* Withdraw request req_id.  *cancelled = 1 if it was still waiting for admission or rendering
  * (its tiles may still be running): from this call on, its h_out is never written, and

@@ -712,7 +712,13 @@ merf_status merf_scene_set_dense(merf_scene *scene, const float *d_grid, const f
     if (e == cudaSuccess)
         e = put_mlp_block(scene->mlp, d_mlp, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return fail(MERF_ERR_CUDA, "set_dense: %s", cudaGetErrorString(e));
+    ++scene->param_version;
     return ok();
+}
+
+unsigned long long merf_scene_param_version(const merf_scene *scene)
+{
+    return scene ? scene->param_version : 0ull;
 }
 
 merf_status merf_render_backward(const merf_scene *scene, const merf_camera *cams, int n_cams, int W, int H,

@@ -336,6 +336,13 @@ merf_status merf_server_wait(merf_server *srv, uint64_t req_id, double timeout_s
     return srv->sched->wait(req_id, timeout_s, latency_s);
 }
 
+merf_status merf_server_wait_timed(merf_server *srv, uint64_t req_id, double timeout_s, double *latency_s,
+                                   merf_request_timing *timing)
+{
+    if (!srv) return merf::set_error(MERF_ERR_INVALID_ARG, "srv is NULL");
+    return srv->sched->wait_timed(req_id, timeout_s, latency_s, timing);
+}
+
 merf_status merf_server_cancel(merf_server *srv, uint64_t req_id, int *cancelled)
 {
     if (!srv) return merf::set_error(MERF_ERR_INVALID_ARG, "srv is NULL");

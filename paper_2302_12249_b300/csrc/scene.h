@@ -14,6 +14,7 @@ struct merf_scene {
     void *index_grid = nullptr, *atlas = nullptr, *planes = nullptr, *mlp = nullptr;
     void *occ[MERF_MAX_OCC_LEVELS] = {};
     size_t bytes = 0;
+    unsigned long long param_version = 0;   // parameter installs: upload 0, +1 per merf_scene_set_dense
 };
 
 namespace merf {

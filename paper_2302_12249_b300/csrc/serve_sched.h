@@ -116,6 +116,7 @@ struct ServeRequest {
     float *h_out = nullptr;
     size_t floats = 0, pool_off = 0;
     double t_submit = 0, t_done = 0;
+    double t_admit = 0, t_launch = 0, t_rendered = 0;   // pool admission, first tiles launched, last tiles done
     ServeState state = kPending;
     merf_status status = MERF_OK;
     void *dev = nullptr;                   // the backend's per-request handle
@@ -222,6 +223,12 @@ public:
 
     merf_status wait(uint64_t req_id, double timeout_s, double *latency_s)
     {
+        return wait_timed(req_id, timeout_s, latency_s, nullptr);
+    }
+
+    // wait, and on completion the request's phases (merf_request_timing; may be NULL)
+    merf_status wait_timed(uint64_t req_id, double timeout_s, double *latency_s, merf_request_timing *timing)
+    {
         std::unique_lock<std::mutex> lk(mu_);
         auto it = reqs_.find(req_id);
         if (it == reqs_.end()) return fail(MERF_ERR_INVALID_ARG, "unknown request %llu", (unsigned long long)req_id);
@@ -232,6 +239,16 @@ public:
             return fail(MERF_ERR_TIMEOUT, "request %llu not complete after %.3f s", (unsigned long long)req_id, timeout_s);
         const merf_status st = r->state == kDone ? MERF_OK : r->status;
         if (latency_s) *latency_s = r->t_done - r->t_submit;
+        if (timing) {
+            // phases end where the next begins; a request cancelled early has no later phases
+            const double a = r->t_admit > 0 ? r->t_admit : r->t_done, l = r->t_launch > 0 ? r->t_launch : a,
+                         e = r->t_rendered > 0 ? r->t_rendered : l;
+            timing->total_s = r->t_done - r->t_submit;
+            timing->admit_s = a - r->t_submit;
+            timing->queue_s = l - a;
+            timing->render_s = e - l;
+            timing->copy_s = r->t_done - e;
+        }
         reqs_.erase(it);
         be_.req_free(*r);
         delete r;
@@ -341,6 +358,7 @@ private:
             q.out_off = r->pool_off;
             memcpy(q.cam, r->cam, sizeof q.cam);
             const int take = std::min(max_tiles_ - nt, r->tiles_total - r->tiles_next);
+            if (r->tiles_next == 0) r->t_launch = now_s();          // its first tiles: this iteration
             for (int t = 0; t < take; ++t) w.tiles[nt + t] = ((uint32_t)nr << 20) | (uint32_t)(r->tiles_next + t);
             nt += take;
             r->tiles_next += take;
@@ -375,6 +393,7 @@ private:
                     if (r->state == kCancelling) {
                         retire_cancelled(r, true);
                     } else if (r->state == kScheduled) {
+                        r->t_rendered = now_s();
                         if (!be_.copy_out(*r)) { fail_all(MERF_ERR_CUDA); return; }
                         r->state = kCopying;
                         copying_.push_back(r);
@@ -405,6 +424,7 @@ private:
                 ServeRequest *r = pending_.front();
                 if (!pool_.alloc(r->floats, r->pool_off)) break;
                 r->state = kActive;
+                r->t_admit = now_s();
                 active_.push_back(r);
                 pending_.pop_front();
                 ++admitted_;

@@ -27,9 +27,11 @@ CNT_RAYS, CNT_LATTICE, CNT_EVAL, CNT_APPEAR = 0, 1, 2, 3
 
 EXPORTS = ("merf_scene_upload", "merf_scene_upload_dense", "merf_scene_load", "merf_scene_free",
            "merf_scene_device_bytes", "merf_render", "merf_render_aux", "merf_render_host", "merf_render_host_noalloc",
-           "merf_trace", "merf_set_device_budget", "merf_scene_set_dense", "merf_render_backward",
+           "merf_trace", "merf_set_device_budget", "merf_scene_set_dense", "merf_scene_param_version",
+           "merf_render_backward",
            "merf_render_backward_aux", "merf_server_create", "merf_server_submit", "merf_server_wait",
-           "merf_server_cancel", "merf_server_get_stats", "merf_server_destroy", "merf_check_device",
+           "merf_server_wait_timed", "merf_server_cancel", "merf_server_get_stats", "merf_server_destroy",
+           "merf_check_device",
            "merf_last_error", "merf_version")
 
 
@@ -62,6 +64,11 @@ class ServerStats(ct.Structure):
                 ("pool_bytes", ct.c_size_t), ("peak_pool_bytes", ct.c_size_t), ("pool_used_bytes", ct.c_size_t),
                 ("peak_admitted", ct.c_int32), ("admitted", ct.c_int32), ("queued", ct.c_int32),
                 ("reserved", ct.c_int32)]
+
+
+class RequestTiming(ct.Structure):
+    _fields_ = [("total_s", ct.c_double), ("admit_s", ct.c_double), ("queue_s", ct.c_double),
+                ("render_s", ct.c_double), ("copy_s", ct.c_double)]
 
 
 _lib = None
@@ -98,6 +105,8 @@ def lib():
         L.merf_set_device_budget.argtypes = [ct.c_size_t]
         L.merf_set_device_budget.restype = None
         L.merf_scene_set_dense.argtypes = [vp, vp, vp, vp, vp]
+        L.merf_scene_param_version.argtypes = [vp]
+        L.merf_scene_param_version.restype = ct.c_ulonglong
         L.merf_render_backward.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp, ct.POINTER(Opts), vp]
         L.merf_render_backward_aux.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp, vp, ct.POINTER(Opts), vp]
         L.merf_render_backward_aux.restype = ct.c_int
@@ -108,13 +117,16 @@ def lib():
         L.merf_server_create.argtypes = [vp, i32, ct.POINTER(ServerOpts), ct.POINTER(vp)]
         L.merf_server_submit.argtypes = [vp, i32, vp, i32, i32, vp, ct.POINTER(ct.c_uint64)]
         L.merf_server_wait.argtypes = [vp, ct.c_uint64, ct.c_double, ct.POINTER(ct.c_double)]
+        L.merf_server_wait_timed.argtypes = [vp, ct.c_uint64, ct.c_double, ct.POINTER(ct.c_double),
+                                             ct.POINTER(RequestTiming)]
         L.merf_server_get_stats.argtypes = [vp, ct.POINTER(ServerStats)]
         L.merf_server_cancel.argtypes = [vp, ct.c_uint64, ct.POINTER(ct.c_int)]
         L.merf_scene_load.argtypes = [ct.c_char_p, vp, ct.POINTER(vp)]
         L.merf_scene_load.restype = ct.c_int
         L.merf_server_destroy.argtypes = [vp]
         L.merf_server_destroy.restype = None
-        for name in ("merf_server_create", "merf_server_submit", "merf_server_wait", "merf_server_cancel",
+        for name in ("merf_server_create", "merf_server_submit", "merf_server_wait", "merf_server_wait_timed",
+                     "merf_server_cancel",
                      "merf_server_get_stats"):
             getattr(L, name).restype = ct.c_int
         L.merf_last_error.restype = ct.c_char_p
@@ -306,6 +318,11 @@ def set_dense(scene: Scene, grid: torch.Tensor, planes: torch.Tensor, mlp: torch
                                       _dev_ptr(mlp, torch.float32, 883, "mlp"), _stream(stream)))
 
 
+def param_version(scene: Scene) -> int:
+    """How many times set_dense has replaced the scene's parameters (merf_scene_param_version)."""
+    return int(lib().merf_scene_param_version(scene.handle))
+
+
 def render_backward(scene: Scene, cams: np.ndarray, W: int, H: int, step: float, d_out: torch.Tensor,
                     g_grid: torch.Tensor, g_planes: torch.Tensor, g_mlp: torch.Tensor, t_term: float = 2e-4,
                     early_term: bool = True, stream=None, aux: Optional[torch.Tensor] = None):
@@ -326,24 +343,33 @@ def render_backward(scene: Scene, cams: np.ndarray, W: int, H: int, step: float,
 
 
 class _RenderFn(torch.autograd.Function):
+    """Forward: install the parameters in the scene and render.  Backward: the adjoint at the same
+    parameters.  The scene holds one set of parameters, so the forward records the scene's
+    parameter version and keeps its parameter tensors (autograd raises if they are modified in
+    place before the backward); if another forward installed other values in between, the
+    backward installs this forward's values again before running the adjoint."""
+
     @staticmethod
     def forward(ctx, grid, planes, mlp, scene, cams, W, H, step, t_term, early_term):
         set_dense(scene, grid.detach(), planes.detach(), mlp.detach())
+        ctx.version = param_version(scene)
+        ctx.save_for_backward(grid, planes, mlp)
         n = cams.shape[0]
         aux = torch.empty((n, H, W, AUX_SIZE), dtype=torch.float32, device="cuda")
         out = render(scene, cams, W, H, step, t_term=t_term, early_term=early_term, aux=aux)
         ctx.aux = aux        # C_d and F per pixel: the adjoint needs no second forward march
         ctx.scene, ctx.cams, ctx.args = scene, cams, (W, H, step, t_term, early_term)
-        ctx.shapes = (grid.shape, planes.shape, mlp.shape)
         return out
 
     @staticmethod
     def backward(ctx, g_out):
         W, H, step, t_term, early_term = ctx.args
-        gs, ps, ms = ctx.shapes
-        g_grid = torch.zeros(gs, dtype=torch.float32, device="cuda")
-        g_planes = torch.zeros(ps, dtype=torch.float32, device="cuda")
-        g_mlp = torch.zeros(ms, dtype=torch.float32, device="cuda")
+        grid, planes, mlp = ctx.saved_tensors
+        if param_version(ctx.scene) != ctx.version:
+            set_dense(ctx.scene, grid.detach(), planes.detach(), mlp.detach())
+        g_grid = torch.zeros(grid.shape, dtype=torch.float32, device="cuda")
+        g_planes = torch.zeros(planes.shape, dtype=torch.float32, device="cuda")
+        g_mlp = torch.zeros(mlp.shape, dtype=torch.float32, device="cuda")
         render_backward(ctx.scene, ctx.cams, W, H, step, g_out.contiguous(), g_grid, g_planes, g_mlp, t_term,
                         early_term, aux=ctx.aux)
         ctx.aux = None
@@ -355,7 +381,8 @@ def render_differentiable(scene: Scene, grid: torch.Tensor, planes: torch.Tensor
                           early_term: bool = True) -> torch.Tensor:
     """Render a dense float scene whose grid, planes and MLP weights are the given CUDA tensors;
     the result is differentiable with respect to them through the library's adjoint kernel.
-    The scene's device copy of the parameters is replaced by these values."""
+    The scene's device copy of the parameters is replaced by these values (and again by the
+    backward pass if another forward on the same scene replaced them in between)."""
     return _RenderFn.apply(grid, planes, mlp, scene, cameras(cams), W, H, step, t_term, early_term)
 
 
@@ -408,6 +435,17 @@ class Server:
         self._outs.pop(rid, None)
         _check(st)
         return lat.value
+
+    def wait_timed(self, rid: int, timeout: float = 60.0) -> dict:
+        """wait, returning where the latency went (merf_request_timing): total, admit, queue,
+        render and copy seconds."""
+        lat, t = ct.c_double(), RequestTiming()
+        st = lib().merf_server_wait_timed(self.handle, ct.c_uint64(rid), float(timeout), ct.byref(lat), ct.byref(t))
+        if st == ERR_TIMEOUT:
+            raise TimeoutError(lib().merf_last_error().decode())
+        self._outs.pop(rid, None)
+        _check(st)
+        return {k: getattr(t, k) for k, _ in RequestTiming._fields_}
 
     def cancel(self, rid: int) -> bool:
         """Withdraw a request (True) unless its image is already on its way out (False); either way

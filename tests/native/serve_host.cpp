@@ -163,6 +163,11 @@ int host_server_wait(void *p, uint64_t id, double timeout_s, double *latency_s)
     return static_cast<HostServer *>(p)->sched->wait(id, timeout_s, latency_s);
 }
 
+int host_server_wait_timed(void *p, uint64_t id, double timeout_s, double *latency_s, merf_request_timing *t)
+{
+    return static_cast<HostServer *>(p)->sched->wait_timed(id, timeout_s, latency_s, t);
+}
+
 int host_server_cancel(void *p, uint64_t id, int *cancelled)
 {
     return static_cast<HostServer *>(p)->sched->cancel(id, cancelled);

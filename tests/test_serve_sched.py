@@ -33,6 +33,8 @@ def hostlib(tmp_path_factory):
     L.host_server_create.restype = vp
     L.host_server_submit.argtypes = [vp, ct.c_int, vp, ct.c_int, ct.c_int, vp, ct.POINTER(ct.c_uint64)]
     L.host_server_wait.argtypes = [vp, ct.c_uint64, ct.c_double, ct.POINTER(ct.c_double)]
+    L.host_server_wait_timed.argtypes = [vp, ct.c_uint64, ct.c_double, ct.POINTER(ct.c_double),
+                                         ct.POINTER(merf.RequestTiming)]
     L.host_server_cancel.argtypes = [vp, ct.c_uint64, ct.POINTER(ct.c_int)]
     L.host_server_stats.argtypes = [vp, ct.POINTER(merf.ServerStats)]
     L.host_server_hold.argtypes = [vp, ct.c_int]
@@ -91,6 +93,11 @@ class Server:
     def wait(self, rid, timeout=60.0):
         lat = ct.c_double()
         return self.L.host_server_wait(self.h, rid, timeout, ct.byref(lat))
+
+    def wait_timed(self, rid, timeout=60.0):
+        lat, t = ct.c_double(), merf.RequestTiming()
+        st = self.L.host_server_wait_timed(self.h, rid, timeout, ct.byref(lat), ct.byref(t))
+        return st, lat.value, {k: getattr(t, k) for k, _ in merf.RequestTiming._fields_}
 
     def cancel(self, rid):
         c = ct.c_int(-1)
@@ -177,6 +184,33 @@ def test_admission_in_arrival_order(hostlib, scenes):
                 order.append(cy)
         assert order == sorted(order) == [15.5 + k for k in range(n)]
         assert srv.stats().peak_admitted == 1
+    finally:
+        srv.close()
+
+
+def test_latency_phases(hostlib, scenes):
+    """merf_request_timing: the phases are ordered and add up to the latency; with a one-image
+    pool the second request waits for admission while the first renders, and iterations held
+    for 0.2 s show up as render time."""
+    W, H = 24, 16
+    cams = _cams(2, seed=17)
+    srv = Server(hostlib, scenes, W * H * 3 * 4 + 255, max_tiles=64)
+    try:
+        srv.hold(True)
+        r0 = srv.submit(0, cams[0], W, H)[1]
+        r1 = srv.submit(1, cams[1], W, H)[1]
+        srv.until(lambda s: s.iterations >= 1)
+        time.sleep(0.2)
+        srv.hold(False)
+        res = [srv.wait_timed(r) for r in (r0, r1)]
+        for st, lat, t in res:
+            assert st == merf.MERF_OK
+            parts = [t["admit_s"], t["queue_s"], t["render_s"], t["copy_s"]]
+            assert min(parts) >= 0.0
+            assert abs(sum(parts) - t["total_s"]) < 1e-9 and abs(t["total_s"] - lat) < 1e-9
+        assert res[0][2]["render_s"] >= 0.19            # its iteration was held
+        assert res[1][2]["admit_s"] >= 0.19             # the pool held only the first image
+        assert res[0][2]["admit_s"] < 0.1
     finally:
         srv.close()
 
