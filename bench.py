@@ -112,10 +112,11 @@ class Clocks:
             return None
         sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
         mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        pw = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "power_w": statistics.median(pw) if pw else None}
 
 
 def _dist(backend: str = "nccl"):
@@ -219,7 +220,7 @@ def _precision_pixels():
     return cams, pix
 
 
-def _precision_form(gs, ref=None, steps=2):
+def _precision_form(gs, ref=None, steps=3):
     """Precision form: the same scene rendered from 64 ring cameras at 1920x1080 in FP32, FP16 and
     BF16 (uint8 features, appearance arithmetic and deferred MLP in 16 bits on tensor cores,
     density/transmittance/compositing in FP32).  Time per step and, on sampled pixels, the
@@ -235,6 +236,8 @@ def _precision_form(gs, ref=None, steps=2):
     for name, prec in (("fp32", merf.PREC_FP32), ("fp16", merf.PREC_FP16), ("bf16", merf.PREC_BF16)):
         merf.render(gs, cams, W_IMG, H_IMG, STEP, out=out, precision=prec)
         torch.cuda.synchronize()
+        ck = Clocks(torch.cuda.current_device())
+        ck.start()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         for _ in range(steps):
@@ -242,7 +245,8 @@ def _precision_form(gs, ref=None, steps=2):
         b.record()
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / steps
-        res[name] = {"ms_per_step": ms, "mrays_per_s": n_cams * W_IMG * H_IMG / (ms / 1e3) / 1e6}
+        res[name] = {"ms_per_step": ms, "mrays_per_s": n_cams * W_IMG * H_IMG / (ms / 1e3) / 1e6,
+                     "clocks": ck.stop()}
         if ref is not None:
             _, lo, hi = ref
             rgb = out.reshape(-1, 3)[lin].double().cpu().numpy()

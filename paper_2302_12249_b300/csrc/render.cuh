@@ -259,16 +259,22 @@ __device__ __forceinline__ void mlp_f32(const float *w, const float cd[3], const
 
 // ---------------------------------------------------------------------------------------------
 // The deferred MLP on the tensor cores (precision form): the CTA's 128 pixels are one M = 128
-// tile of tcgen05.mma (kind::f16: FP16 or BF16 operands from shared memory, FP32 accumulator in
-// tensor memory).  Layer 1 is [128 x 48] x [48 x 16] (34 inputs zero-padded to 48, three K = 16
-// steps), layer 2 [128 x 16] x [16 x 16], layer 3 [128 x 16] x [16 x 16] (3 outputs zero-padded to
-// 16).  One thread issues each layer's MMAs and commits them to an mbarrier; every thread then
-// reads its own pixel's row of the accumulator (TMEM lane = pixel), adds the bias, applies ReLU
-// and writes its row of the next layer's A operand.  BF16 keeps only 8 significant bits, so in
-// that mode every operand is carried as an unevaluated sum hi + lo of two bfloat16 values and
-// each product takes three passes (hi*hi + lo*hi + hi*lo, all accumulated in FP32); FP16 uses one.
+// tile of tcgen05.mma (kind::f16: FP16 or BF16 operands, FP32 accumulator in tensor memory).
+// Layer 1 is [128 x 48] x [48 x 16] (34 inputs zero-padded to 48, three K = 16 steps), layer 2
+// [128 x 16] x [16 x 16], layer 3 [128 x 16] x [16 x 16] (3 outputs zero-padded to 16).  The A
+// operand (the pixels' activations) is staged in tensor memory: every thread writes its own pixel's
+// row into its TMEM lane with tcgen05.st, so the operand takes no shared memory (which the gathers
+// use as L1 cache) and needs no layout beyond "row per lane".  The B operand (the weights) sits in
+// shared memory.  One thread issues each layer's MMAs and commits them to an mbarrier; every thread
+// then reads its own pixel's row of the accumulator (TMEM lane = pixel), adds the bias, applies
+// ReLU and writes its row of the next layer's A operand.  BF16 keeps only 8 significant bits, so in
+// that mode every operand is carried as an unevaluated sum hi + lo of two bfloat16 values and each
+// product takes three passes (hi*hi + lo*hi + hi*lo, all accumulated in FP32); FP16 uses one.
 
-constexpr int kTmemCols = 32;               // the smallest TMEM allocation; N = 16 uses 16
+// Tensor-memory columns of a CTA: the accumulator (16), layer 1's A operand (48 halves in 24
+// columns) and, for BF16, its low parts (24); layers 2 and 3 reuse the first 8 (+ 8) A columns.
+constexpr int kTmemCols = 64;
+constexpr int kColD = 0, kColA = 16, kColALo = 40;
 constexpr int kWaitPolls = 1 << 22;         // bounded wait for an MMA group (microseconds in practice)
 
 // The weights of one 16-bit form as the MMAs read them, built once per scene in device memory and
@@ -286,14 +292,10 @@ struct alignas(128) MlpWeights16 {
 template <int kPrec>
 struct MlpUmma {
     static constexpr int kParts = MlpWeights16<kPrec>::kParts;
-    // A operand.  Layer 1: the 128 x 48 rows (BF16: the high parts, then the low parts in a
-    // second round).  Layers 2 and 3: the 128 x 16 rows at 0, BF16 low parts at kLoOffset.
-    alignas(128) uint8_t x[128 * 48 * 2];
     MlpWeights16<kPrec> wt;
     alignas(8) uint64_t mbar;                              // MMA completion
-    uint32_t tmem;                                         // the CTA's accumulator columns
+    uint32_t tmem;                                         // the CTA's tensor-memory columns
 };
-constexpr int kLoOffset = 128 * 16 * 2;
 
 // A scene's MLP block in device memory: the 883 FP32 weights padded to 884 (16 bytes), then the
 // FP16 and the BF16 forms, each at a 128-byte boundary.  Each form is one bulk copy: 16-byte
@@ -396,33 +398,31 @@ __device__ __forceinline__ void mlp_pack16(MlpWeights16<kPrec> &o, const float *
     }
 }
 
-// This thread's row (pixel) of a K-column A tile at `dst` (BF16 low parts if kLow): 8 elements
-// per 16-byte store.
+// This thread's row (pixel) of a K-column A operand into its TMEM lane from column `col` (BF16
+// low parts if kLow): two 16-bit elements per column, 8 columns per store.
 template <int kPrec, int K, bool kLow>
-__device__ __forceinline__ void put_row(uint8_t *dst, const float *v)
+__device__ __forceinline__ void put_row(uint32_t tmem, int col, const float *v)
 {
-    const int t = threadIdx.x;
 #pragma unroll
-    for (int c = 0; c < K / 8; ++c) {
-        uint32_t u[4];
+    for (int c = 0; c < K / 16; ++c) {
+        uint32_t u[8];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            u[q] = kLow ? pack16_lo<kPrec>(v[8 * c + 2 * q], v[8 * c + 2 * q + 1])
-                        : pack16<kPrec>(v[8 * c + 2 * q], v[8 * c + 2 * q + 1]);
-        *reinterpret_cast<uint4 *>(dst + kmajor_offset(t, 8 * c, K)) = make_uint4(u[0], u[1], u[2], u[3]);
+        for (int q = 0; q < 8; ++q)
+            u[q] = kLow ? pack16_lo<kPrec>(v[16 * c + 2 * q], v[16 * c + 2 * q + 1])
+                        : pack16<kPrec>(v[16 * c + 2 * q], v[16 * c + 2 * q + 1]);
+        tmem_st8(tmem, col + 8 * c, u);
     }
 }
 
-// D (+)= A B over K (K / 16 MMAs of K = 16; two 128-byte core-matrix columns each), A and B
-// K-major tiles at shared addresses a and b.  Issuing thread only.
+// D (+)= A B over K (K / 16 MMAs of K = 16: 8 TMEM columns of A, two 128-byte core-matrix columns
+// of B each), A in TMEM from column a, B a K-major tile at shared address b.  Issuing thread only.
 template <int kPrec, int K>
 __device__ __forceinline__ void mma_k(uint32_t tmem, uint32_t a, uint32_t b, bool accumulate)
 {
     constexpr uint32_t kId = umma_idesc_f16(128, 16, kPrec == 2), kSbo = (K / 8) * 128;
 #pragma unroll
     for (int ks = 0; ks < K / 16; ++ks)
-        umma_f16(tmem, umma_smem_desc(a + 256u * ks, 128, kSbo), umma_smem_desc(b + 256u * ks, 128, kSbo), kId,
-                 accumulate || ks > 0);
+        umma_f16_ts(tmem + kColD, a + 8u * ks, umma_smem_desc(b + 256u * ks, 128, kSbo), kId, accumulate || ks > 0);
 }
 
 // One round on the tensor cores: every thread's operand rows are published, thread 0 issues the
@@ -431,7 +431,7 @@ __device__ __forceinline__ void mma_k(uint32_t tmem, uint32_t a, uint32_t b, boo
 template <int kPrec, typename Issue>
 __device__ __forceinline__ bool umma_round(MlpUmma<kPrec> &ms, uint32_t &phase, Issue issue)
 {
-    fence_async_smem();          // this thread's operand writes, to the tensor cores
+    tmem_st_wait();              // this thread's operand rows are in tensor memory
     tc_fence_before();
     __syncthreads();             // all rows written; every earlier accumulator read done
     tc_fence_after();
@@ -464,18 +464,18 @@ template <int kPrec, int nc>
 __device__ __forceinline__ void layer16(MlpUmma<kPrec> &ms, uint32_t &phase, uint8_t (&w)[MlpWeights16<kPrec>::kParts][512],
                                         const float h[16], float *acc)
 {
-    put_row<kPrec, 16, false>(ms.x, h);
-    if constexpr (kPrec == 2) put_row<kPrec, 16, true>(ms.x + kLoOffset, h);
-    const uint32_t x = smem_addr(ms.x), wh = smem_addr(w[0]), wl = smem_addr(w[MlpUmma<kPrec>::kParts - 1]);
     const uint32_t tm = ms.tmem;
+    put_row<kPrec, 16, false>(tm, kColA, h);
+    if constexpr (kPrec == 2) put_row<kPrec, 16, true>(tm, kColALo, h);
+    const uint32_t wh = smem_addr(w[0]), wl = smem_addr(w[MlpUmma<kPrec>::kParts - 1]);
     const bool ok = umma_round(ms, phase, [&] {
-        mma_k<kPrec, 16>(tm, x, wh, false);
+        mma_k<kPrec, 16>(tm, tm + kColA, wh, false);
         if constexpr (kPrec == 2) {
-            mma_k<kPrec, 16>(tm, x + kLoOffset, wh, true);
-            mma_k<kPrec, 16>(tm, x, wl, true);
+            mma_k<kPrec, 16>(tm, tm + kColALo, wh, true);
+            mma_k<kPrec, 16>(tm, tm + kColA, wl, true);
         }
     });
-    acc_row<nc>(tm, ok, acc);
+    acc_row<nc>(tm + kColD, ok, acc);
 }
 
 // h(C_d, F, d) of this thread's pixel; all 128 threads of the CTA call it together (threads
@@ -491,20 +491,19 @@ __device__ __forceinline__ void mlp_umma(MlpUmma<kPrec> &ms, uint32_t &phase, co
     posenc(d, x);
 #pragma unroll
     for (int k = 34; k < 48; ++k) x[k] = 0.0f;
-    // layer 1 (BF16: hi*hi + hi*lo, then the low parts replace the high ones for lo*hi)
-    const uint32_t xa = smem_addr(ms.x), wh = smem_addr(ms.wt.w0[0]), wl = smem_addr(ms.wt.w0[MlpUmma<kPrec>::kParts - 1]);
-    const uint32_t tm = ms.tmem;
-    put_row<kPrec, 48, false>(ms.x, x);
-    bool ok = umma_round(ms, phase, [&] {
-        mma_k<kPrec, 48>(tm, xa, wh, false);
-        if constexpr (kPrec == 2) mma_k<kPrec, 48>(tm, xa, wl, true);
+    // layer 1 (BF16: hi*hi + hi*lo + lo*hi, the low parts in their own columns)
+    const uint32_t tm = ms.tmem, wh = smem_addr(ms.wt.w0[0]), wl = smem_addr(ms.wt.w0[MlpUmma<kPrec>::kParts - 1]);
+    put_row<kPrec, 48, false>(tm, kColA, x);
+    if constexpr (kPrec == 2) put_row<kPrec, 48, true>(tm, kColALo, x);
+    const bool ok = umma_round(ms, phase, [&] {
+        mma_k<kPrec, 48>(tm, tm + kColA, wh, false);
+        if constexpr (kPrec == 2) {
+            mma_k<kPrec, 48>(tm, tm + kColA, wl, true);
+            mma_k<kPrec, 48>(tm, tm + kColALo, wh, true);
+        }
     });
-    if constexpr (kPrec == 2) {
-        put_row<kPrec, 48, true>(ms.x, x);
-        ok = umma_round(ms, phase, [&] { mma_k<kPrec, 48>(tm, xa, wh, true); }) && ok;
-    }
     float h[16];
-    acc_row<16>(tm, ok, h);
+    acc_row<16>(tm + kColD, ok, h);
 #pragma unroll
     for (int o = 0; o < 16; ++o) h[o] = fmaxf(h[o] + ms.wt.b0[o], 0.0f);
     float h2[16];

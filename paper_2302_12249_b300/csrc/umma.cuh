@@ -1,10 +1,11 @@
 // umma.cuh -- the sm_100-family primitives used by the deferred MLP: tcgen05.mma (one elected
-// thread issues a CTA-wide M = 128 MMA), its accumulator in tensor memory (TMEM), tcgen05.ld back
-// to registers, the mbarrier that tcgen05.commit signals when the MMAs are done, and the bulk
-// (TMA) copy that brings the weights into shared memory.
+// thread issues a CTA-wide M = 128 MMA), its A operand and accumulator in tensor memory (TMEM,
+// written by tcgen05.st and read back by tcgen05.ld), the mbarrier that tcgen05.commit signals
+// when the MMAs are done, and the bulk (TMA) copy that brings the weights into shared memory.
 //
-// Operands live in shared memory in the canonical K-major layout without swizzle: an R x K tile of
-// 16-bit elements is made of 8-row x 16-byte "core matrices"; element (r, k) sits at
+// The B operand (the weights) lives in shared memory in the canonical K-major layout without
+// swizzle: an R x K tile of 16-bit elements is made of 8-row x 16-byte "core matrices"; element
+// (r, k) sits at
 //     (r / 8) * SBO + (k / 8) * LBO + (r % 8) * 16 + (k % 8) * 2
 // with LBO = 128 (core matrices adjacent along K) and SBO = (K / 8) * 128 (the next 8 rows).
 // The accumulator of an M = 128 MMA (cta_group::1) holds row m in TMEM lane m and column n in
@@ -70,6 +71,17 @@ __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a_desc, uint6
                  : "memory");
 }
 
+// The same with A in tensor memory: row m of A in TMEM lane m, its 16-bit elements (k, k + 1) in
+// one 32-bit column, element k in the low half (a_tmem: the column of element 0).
+__device__ __forceinline__ void umma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                            uint32_t accumulate)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+                 "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+                 : "memory");
+}
+
 // The mbarrier gets one arrival when every MMA this thread issued before has completed.
 __device__ __forceinline__ void umma_commit(uint64_t *mbar)
 {
@@ -121,6 +133,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t tmem, int col, float v[16])
 #pragma unroll
     for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
 }
+
+// Columns col .. col + 7 of this thread's TMEM lane from registers; tmem_st_wait() makes the
+// thread's stores complete (before the barrier that precedes an MMA reading them).
+__device__ __forceinline__ void tmem_st8(uint32_t tmem, int col, const uint32_t r[8])
+{
+    const uint32_t addr = tmem + ((uint32_t)(32 * (threadIdx.x >> 5)) << 16) + (uint32_t)col;
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(addr), "r"(r[0]),
+                 "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void tmem_ld4(uint32_t tmem, int col, float v[4])
 {
