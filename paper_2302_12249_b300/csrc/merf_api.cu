@@ -243,14 +243,15 @@ merf::RenderParams make_params(const merf_scene *s, const merf_render_opts *o, i
 __global__ void status_self_test_kernel() { atomicOr(&merf::g_status, merf::kStatusSelfTest); }
 #endif
 
-// A bounded wait that runs out: an mbarrier that nothing arrives on, polled 1000 times with the
-// same wait the tensor-core MLP uses; giving up is recorded as the MLP's would be.
+// A bounded wait that runs out: an mbarrier that nothing arrives on, waited on for 100 us of the
+// global timer with the same wait the tensor-core MLP uses; giving up is recorded as the MLP's
+// would be.
 __global__ void wait_timeout_self_test_kernel()
 {
     __shared__ alignas(8) uint64_t mbar;
     merf::mbar_init(&mbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    if (!merf::mbar_wait(&mbar, 0, 1000)) merf::set_status(merf::kWaitTimeout);
+    if (!merf::mbar_wait(&mbar, 0, 100000)) merf::set_status(merf::kWaitTimeout);
 }
 
 template <int kPrec>

@@ -49,7 +49,8 @@ __global__ void __launch_bounds__(kThreads, (kMinBlocks<0, kPrec>)) serve_kernel
     ms.init();                          // the first barrier below publishes it
     const int n_tiles = P.work->n_tiles;
     int cur_scene = -1;
-    uint32_t phase = 0, wphase = 0;
+    UmmaState us;
+    uint32_t wphase = 0, lost = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(P.counter, 1);
@@ -76,8 +77,11 @@ __global__ void __launch_bounds__(kThreads, (kMinBlocks<0, kPrec>)) serve_kernel
         if (inside)
             march_ray<0, kPrec, kGeo>(P.scenes[sc].fv, P.scenes[sc].occ, R.cam, i, j, P.step, P.t_term, P.early_term, r);
         float h[3];
-        if (fetched) ms.wait(wphase);
-        deferred_mlp<kPrec>(ms, phase, r, inside, h);
+        // A copy or an MMA round that did not complete ends this CTA's work: no further copy or
+        // MMA is issued, the tile is left unwritten, and the status word reports it.
+        if (fetched && !__syncthreads_and(ms.wait(wphase, lost))) break;
+        deferred_mlp<kPrec>(ms, us, r, inside, h);
+        if (!__syncthreads_and(us.ok)) break;
         if (inside) {
             float *o = P.pool + R.out_off + ((size_t)j * R.W + i) * 3;
             o[0] = r.cd[0] + h[0];
@@ -86,7 +90,7 @@ __global__ void __launch_bounds__(kThreads, (kMinBlocks<0, kPrec>)) serve_kernel
         }
         __syncthreads();                // s_tile and the weights are reused next iteration
     }
-    ms.fini();
+    ms.fini(us, lost);
 }
 
 unsigned int take_server_status()

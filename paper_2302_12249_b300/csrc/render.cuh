@@ -275,7 +275,9 @@ __device__ __forceinline__ void mlp_f32(const float *w, const float cd[3], const
 // columns) and, for BF16, its low parts (24); layers 2 and 3 reuse the first 8 (+ 8) A columns.
 constexpr int kTmemCols = 64;
 constexpr int kColD = 0, kColA = 16, kColALo = 40;
-constexpr int kWaitPolls = 1 << 22;         // bounded wait for an MMA group (microseconds in practice)
+// Bounded waits (an MMA group or the weights' bulk copy completes in microseconds): 2 ms of the
+// global timer, after which the wait gives up and the status word records it.
+constexpr uint32_t kWaitNs = 2000000;
 
 // The weights of one 16-bit form as the MMAs read them, built once per scene in device memory and
 // brought to shared memory by one bulk copy: the B operands W0^T, W1^T, W2^T as K-major 16-bit
@@ -295,6 +297,14 @@ struct MlpUmma {
     MlpWeights16<kPrec> wt;
     alignas(8) uint64_t mbar;                              // MMA completion
     uint32_t tmem;                                         // the CTA's tensor-memory columns
+};
+
+// Per-thread state of the CTA's rounds: the completion barrier's next parity, and whether every
+// round so far completed (after a round that did not, no further MMA is issued, and the CTA waits
+// once more for that round before it frees its tensor memory).
+struct UmmaState {
+    uint32_t phase = 0, failed_parity = 0;
+    bool ok = true;
 };
 
 // A scene's MLP block in device memory: the 883 FP32 weights padded to 884 (16 bytes), then the
@@ -361,12 +371,14 @@ __device__ __forceinline__ void mlp_umma_init(MlpUmma<kPrec> &ms)
     }
 }
 
-// Every warp's accumulator reads are done; warp 0 frees the columns (all threads call it).
+// Every warp's accumulator reads are done; warp 0 frees the columns (all threads call it).  If a
+// round did not complete, its MMAs may still be running: wait for them once more (bounded) first.
 template <int kPrec>
-__device__ __forceinline__ void mlp_umma_fini(MlpUmma<kPrec> &ms)
+__device__ __forceinline__ void mlp_umma_fini(MlpUmma<kPrec> &ms, const UmmaState &us)
 {
     tc_fence_before();
-    __syncthreads();
+    const bool ok = __syncthreads_and(us.ok);
+    if (!ok) mbar_wait(&ms.mbar, us.failed_parity, kWaitNs);
     if (threadIdx.x < 32) {
         tc_fence_after();
         tmem_dealloc<kTmemCols>(ms.tmem);
@@ -426,24 +438,30 @@ __device__ __forceinline__ void mma_k(uint32_t tmem, uint32_t a, uint32_t b, boo
 }
 
 // One round on the tensor cores: every thread's operand rows are published, thread 0 issues the
-// MMAs (`issue`) and commits them to the barrier, and all threads wait for them.  False if the
-// wait gave up (recorded in the device status word); uniform within each warp.
+// MMAs (`issue`) and commits them to the barrier, and all threads wait for them.  False if this
+// round's wait gave up (recorded in the device status word; uniform within each warp) or an
+// earlier one did (uniform across the CTA: then nothing is issued).
 template <int kPrec, typename Issue>
-__device__ __forceinline__ bool umma_round(MlpUmma<kPrec> &ms, uint32_t &phase, Issue issue)
+__device__ __forceinline__ bool umma_round(MlpUmma<kPrec> &ms, UmmaState &us, Issue issue)
 {
     tmem_st_wait();              // this thread's operand rows are in tensor memory
     tc_fence_before();
-    __syncthreads();             // all rows written; every earlier accumulator read done
+    us.ok = __syncthreads_and(us.ok);   // all rows written; every earlier accumulator read done
     tc_fence_after();
+    if (!us.ok) return false;
     if (threadIdx.x == 0) {
         issue();
         umma_commit(&ms.mbar);
     }
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(&ms.mbar, phase, kWaitPolls));
-    phase ^= 1u;
+    const bool done = __all_sync(0xffffffffu, mbar_wait(&ms.mbar, us.phase, kWaitNs));
+    if (!done) {
+        us.ok = false;
+        us.failed_parity = us.phase;
+        if ((threadIdx.x & 31) == 0) set_status(kWaitTimeout);
+    }
+    us.phase ^= 1u;
     tc_fence_after();
-    if (!ok && (threadIdx.x & 31) == 0) set_status(kWaitTimeout);
-    return ok;
+    return done;
 }
 
 // This thread's accumulator row (nc = 16 or 4 columns), zeros if the MMAs did not complete.
@@ -461,14 +479,14 @@ __device__ __forceinline__ void acc_row(uint32_t tmem, bool ok, float *acc)
 
 // A 16-input layer (2 or 3): D = H W, BF16 as hi*hi + lo*hi + hi*lo in one round.
 template <int kPrec, int nc>
-__device__ __forceinline__ void layer16(MlpUmma<kPrec> &ms, uint32_t &phase, uint8_t (&w)[MlpWeights16<kPrec>::kParts][512],
+__device__ __forceinline__ void layer16(MlpUmma<kPrec> &ms, UmmaState &us, uint8_t (&w)[MlpWeights16<kPrec>::kParts][512],
                                         const float h[16], float *acc)
 {
     const uint32_t tm = ms.tmem;
     put_row<kPrec, 16, false>(tm, kColA, h);
     if constexpr (kPrec == 2) put_row<kPrec, 16, true>(tm, kColALo, h);
     const uint32_t wh = smem_addr(w[0]), wl = smem_addr(w[MlpUmma<kPrec>::kParts - 1]);
-    const bool ok = umma_round(ms, phase, [&] {
+    const bool ok = umma_round(ms, us, [&] {
         mma_k<kPrec, 16>(tm, tm + kColA, wh, false);
         if constexpr (kPrec == 2) {
             mma_k<kPrec, 16>(tm, tm + kColALo, wh, true);
@@ -481,7 +499,7 @@ __device__ __forceinline__ void layer16(MlpUmma<kPrec> &ms, uint32_t &phase, uin
 // h(C_d, F, d) of this thread's pixel; all 128 threads of the CTA call it together (threads
 // without a pixel pass zeros and ignore the result).
 template <int kPrec>
-__device__ __forceinline__ void mlp_umma(MlpUmma<kPrec> &ms, uint32_t &phase, const float cd[3], const float f[4],
+__device__ __forceinline__ void mlp_umma(MlpUmma<kPrec> &ms, UmmaState &us, const float cd[3], const float f[4],
                                          const float d[3], float out[3])
 {
     float x[48];
@@ -495,7 +513,7 @@ __device__ __forceinline__ void mlp_umma(MlpUmma<kPrec> &ms, uint32_t &phase, co
     const uint32_t tm = ms.tmem, wh = smem_addr(ms.wt.w0[0]), wl = smem_addr(ms.wt.w0[MlpUmma<kPrec>::kParts - 1]);
     put_row<kPrec, 48, false>(tm, kColA, x);
     if constexpr (kPrec == 2) put_row<kPrec, 48, true>(tm, kColALo, x);
-    const bool ok = umma_round(ms, phase, [&] {
+    const bool ok = umma_round(ms, us, [&] {
         mma_k<kPrec, 48>(tm, tm + kColA, wh, false);
         if constexpr (kPrec == 2) {
             mma_k<kPrec, 48>(tm, tm + kColA, wl, true);
@@ -507,11 +525,11 @@ __device__ __forceinline__ void mlp_umma(MlpUmma<kPrec> &ms, uint32_t &phase, co
 #pragma unroll
     for (int o = 0; o < 16; ++o) h[o] = fmaxf(h[o] + ms.wt.b0[o], 0.0f);
     float h2[16];
-    layer16<kPrec, 16>(ms, phase, ms.wt.w1, h, h2);
+    layer16<kPrec, 16>(ms, us, ms.wt.w1, h, h2);
 #pragma unroll
     for (int o = 0; o < 16; ++o) h2[o] = fmaxf(h2[o] + ms.wt.b1[o], 0.0f);
     float y[4];
-    layer16<kPrec, 4>(ms, phase, ms.wt.w2, h2, y);
+    layer16<kPrec, 4>(ms, us, ms.wt.w2, h2, y);
     out[0] = y[0] + ms.wt.b2[0];
     out[1] = y[1] + ms.wt.b2[1];
     out[2] = y[2] + ms.wt.b2[2];
@@ -668,11 +686,24 @@ struct MlpStage {
             bulk_g2s(dst, reinterpret_cast<const char *>(mlp) + mlp_form_offset<kPrec>(), bytes, &wbar);
         }
     }
-    // All threads; a wait that gives up is recorded in the device status word.
-    __device__ __forceinline__ void wait(uint32_t &wphase)
+    // All threads; true when the copy has landed (as this thread sees it).  A wait that gives up is
+    // recorded in the device status word, and its parity in this thread's `lost` bits.
+    __device__ __forceinline__ bool wait(uint32_t &wphase, uint32_t &lost)
     {
-        if (!mbar_wait(&wbar, wphase, kWaitPolls)) set_status(kWaitTimeout);
+        const bool landed = mbar_wait(&wbar, wphase, kWaitNs);
+        if (!landed) {
+            set_status(kWaitTimeout);
+            lost |= 1u << wphase;           // bit p: a copy completing parity p is outstanding
+        }
         wphase ^= 1u;
+        return landed;
+    }
+    // All threads, before the CTA exits: a copy whose wait gave up may still be in flight into this
+    // CTA's shared memory; wait for it once more (bounded).
+    __device__ __forceinline__ void drain(uint32_t lost)
+    {
+        if (lost & 1u) mbar_wait(&wbar, 0, kWaitNs);
+        if (lost & 2u) mbar_wait(&wbar, 1, kWaitNs);
     }
 };
 
@@ -683,7 +714,7 @@ struct MlpSmem<0> : MlpStage<0> {
     alignas(16) float w[kMlpF32Floats];
     __device__ __forceinline__ void init() { init_bar(); }                       // before a barrier
     __device__ __forceinline__ void fetch(const float *mlp) { copy(w, mlp, sizeof w); }
-    __device__ __forceinline__ void fini() {}
+    __device__ __forceinline__ void fini(const UmmaState &, uint32_t lost) { drain(lost); }
 };
 template <int kPrec>
 struct MlpSmem : MlpStage<kPrec> {
@@ -694,19 +725,23 @@ struct MlpSmem : MlpStage<kPrec> {
         mlp_umma_init<kPrec>(tc);
     }
     __device__ __forceinline__ void fetch(const float *mlp) { this->copy(&tc.wt, mlp, sizeof tc.wt); }
-    __device__ __forceinline__ void fini() { mlp_umma_fini<kPrec>(tc); }      // all threads, at the end
+    __device__ __forceinline__ void fini(const UmmaState &us, uint32_t lost)   // all threads, at the end
+    {
+        this->drain(lost);
+        mlp_umma_fini<kPrec>(tc, us);
+    }
 };
 
 // h(C_d, F, d) for this thread's pixel (every thread of the CTA calls; `live` ones own a pixel).
-// `phase`: parity of the tensor-core completion barrier, carried across calls.
+// `us`: the tensor-core rounds' state, carried across calls.
 template <int kPrec>
-__device__ __forceinline__ void deferred_mlp(MlpSmem<kPrec> &ms, uint32_t &phase, const RayState &r, bool live,
+__device__ __forceinline__ void deferred_mlp(MlpSmem<kPrec> &ms, UmmaState &us, const RayState &r, bool live,
                                              float h[3])
 {
     if constexpr (kPrec == 0) {
         if (live) mlp_f32(ms.w, r.cd, r.F, r.d, h);
     } else {
-        mlp_umma<kPrec>(ms.tc, phase, r.cd, r.F, r.d, h);     // whole CTA, tensor cores
+        mlp_umma<kPrec>(ms.tc, us, r.cd, r.F, r.d, h);        // whole CTA, tensor cores
     }
 }
 
@@ -739,9 +774,10 @@ __global__ void __launch_bounds__(kThreads, (kMinBlocks<kStorage, kPrec>)) rende
             march_ray_sph<kStorage, kGeo>(P.fv, P.occ, P.cams.m[cl], i, j, P.step, P.t_term, P.early_term, r);
     }
     float h[3];
-    uint32_t phase = 0, wphase = 0;
-    ms.wait(wphase);
-    deferred_mlp<kPrec>(ms, phase, r, inside, h);
+    UmmaState us;
+    uint32_t wphase = 0, lost = 0;
+    ms.wait(wphase, lost);             // a copy that did not land leaves garbage weights and the status bit
+    deferred_mlp<kPrec>(ms, us, r, inside, h);
     if (inside) {
         const size_t pix = ((size_t)(P.cam0 + cl) * P.H + j) * P.W + i;
         P.out[pix * 3 + 0] = r.cd[0] + h[0];
@@ -771,7 +807,7 @@ __global__ void __launch_bounds__(kThreads, (kMinBlocks<kStorage, kPrec>)) rende
             atomicAdd(P.counters + 3, a);
         }
     }
-    ms.fini();
+    ms.fini(us, lost);
 }
 
 // Traversal only (no gather, no termination): the set of evaluated lattice samples per ray.

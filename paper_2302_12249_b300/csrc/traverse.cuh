@@ -29,7 +29,9 @@
 
 namespace merf {
 
-constexpr int kMaxSegs = 16;
+// A ray has at most 12 region-boundary crossings (two faces of |x_a| = 1 per axis, two diagonal
+// planes per axis pair), hence at most 13 intervals and 13 merged segments.
+constexpr int kMaxSegs = 13;
 constexpr int kMaxLevels = 8;
 
 #define F_ADD __fadd_rn
@@ -136,71 +138,86 @@ struct Segs {
     int n;
 };
 
+__device__ __forceinline__ void sort2(float &a, float &b)
+{
+    const float lo = fminf(a, b), hi = fmaxf(a, b);
+    a = lo;
+    b = hi;
+}
+
+// The segment table of a ray, built without scratch arrays (every index below is a compile-time
+// constant except the table's own, so the candidates stay in registers): the 12 breakpoint
+// candidates, rejected ones as +inf, sorted by an odd-even transposition network; the intervals
+// between strictly increasing breakpoints classified by their midpoints and merged while the
+// region repeats, each merged segment's [t_a, t_b] and region recorded as it closes; then each
+// segment's contracted end points, direction, arc length and world-length constants.  The same
+// values, in the same order of operations, as sorting the candidates, dropping duplicates,
+// classifying every interval and then merging.
 __device__ __forceinline__ void build_segments(const float o[3], const float d[3], Segs &sg)
 {
     // region-boundary candidates: |x_a| = 1 and x_a = +-x_b
-    float cand[12];
-    int nc = 0;
+    float c[12];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        float t1 = F_DIV(F_SUB(1.0f, o[a]), d[a]);
-        float t2 = F_DIV(F_SUB(-1.0f, o[a]), d[a]);
-        if (t1 > 0.0f && t1 < CUDART_INF_F) cand[nc++] = t1;
-        if (t2 > 0.0f && t2 < CUDART_INF_F) cand[nc++] = t2;
+        const float t1 = F_DIV(F_SUB(1.0f, o[a]), d[a]);
+        const float t2 = F_DIV(F_SUB(-1.0f, o[a]), d[a]);
+        c[2 * a] = (t1 > 0.0f && t1 < CUDART_INF_F) ? t1 : CUDART_INF_F;
+        c[2 * a + 1] = (t2 > 0.0f && t2 < CUDART_INF_F) ? t2 : CUDART_INF_F;
     }
 #pragma unroll
     for (int pr = 0; pr < 3; ++pr) {
         const int a = pr == 2 ? 1 : 0, b = pr == 0 ? 1 : 2;
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-            float num = F_SUB(s == 0 ? o[b] : -o[b], o[a]);
-            float den = F_SUB(d[a], s == 0 ? d[b] : -d[b]);
-            float t = F_DIV(num, den);
-            if (t > 0.0f && t < CUDART_INF_F) cand[nc++] = t;
+            const float num = F_SUB(s == 0 ? o[b] : -o[b], o[a]);
+            const float den = F_SUB(d[a], s == 0 ? d[b] : -d[b]);
+            const float t = F_DIV(num, den);
+            c[6 + 2 * pr + s] = (t > 0.0f && t < CUDART_INF_F) ? t : CUDART_INF_F;
         }
     }
-    for (int i = 1; i < nc; ++i) {
-        float v = cand[i];
-        int k = i - 1;
-        while (k >= 0 && cand[k] > v) { cand[k + 1] = cand[k]; --k; }
-        cand[k + 1] = v;
-    }
-    float bounds[14];
-    int nb = 0;
-    bounds[nb++] = 0.0f;
-    for (int i = 0; i < nc; ++i)
-        if (cand[i] > bounds[nb - 1]) bounds[nb++] = cand[i];
-    bounds[nb++] = CUDART_INF_F;
+#pragma unroll
+    for (int round = 0; round < 12; ++round)
+#pragma unroll
+        for (int i = round & 1; i + 1 < 12; i += 2) sort2(c[i], c[i + 1]);
 
-    float ta[kMaxSegs], tb[kMaxSegs];
-    int reg[kMaxSegs];
-    int n = 0;
-    for (int m = 0; m + 1 < nb; ++m) {
-        float t0 = bounds[m], t1 = bounds[m + 1];
-        float tm = (t1 < CUDART_INF_F) ? F_MUL(F_ADD(t0, t1), 0.5f) : F_ADD(F_MUL(t0, 2.0f), 1.0f);
+    // merged segments: t_a in sg.c, t_b in sg.g (until the second pass), regions 3 bits each
+    unsigned long long regions = 0ull;
+    int n = 0, cur = -1;
+    float t0 = 0.0f;
+#pragma unroll
+    for (int m = 0; m <= 12; ++m) {
+        const float t1 = m < 12 ? c[m] : CUDART_INF_F;
+        if (m < 12 && !(t1 > t0 && t1 < CUDART_INF_F)) continue;    // duplicate or no crossing
+        const float tm = (t1 < CUDART_INF_F) ? F_MUL(F_ADD(t0, t1), 0.5f) : F_ADD(F_MUL(t0, 2.0f), 1.0f);
         float x[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) x[k] = F_ADD(o[k], F_MUL(tm, d[k]));
-        int r = region_f32(x);
-        if (n > 0 && reg[n - 1] == r) { tb[n - 1] = t1; continue; }
-        reg[n] = r;
-        ta[n] = t0;
-        tb[n] = t1;
-        ++n;
+        const int r = region_f32(x);
+        if (r != cur) {
+            if (cur >= 0) ++n;
+            sg.c[n] = t0;
+            regions |= (unsigned long long)r << (3 * n);
+            cur = r;
+        }
+        sg.g[n] = t1;
+        t0 = t1;
     }
+    ++n;
+
     sg.n = n;
     sg.S[0] = 0.0f;
     for (int i = 0; i < n; ++i) {
-        const int r = reg[i];
+        const int r = (int)((regions >> (3 * i)) & 7ull);
+        const float ta = sg.c[i], tb = sg.g[i];
         float xa[3], pa[3], pb[3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) xa[k] = F_ADD(o[k], F_MUL(ta[i], d[k]));
+        for (int k = 0; k < 3; ++k) xa[k] = F_ADD(o[k], F_MUL(ta, d[k]));
         contract_f32(r, xa, pa);
         const int j = (r - 1) >> 1;
-        if (tb[i] < CUDART_INF_F) {
+        if (tb < CUDART_INF_F) {
             float xb[3];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) xb[k] = F_ADD(o[k], F_MUL(tb[i], d[k]));
+            for (int k = 0; k < 3; ++k) xb[k] = F_ADD(o[k], F_MUL(tb, d[k]));
             contract_f32(r, xb, pb);
         } else if (r == 0) {
             // only reachable for a degenerate direction: an empty segment
@@ -231,7 +248,7 @@ __device__ __forceinline__ void build_segments(const float o[3], const float d[3
         } else {
             const float sgn = ((r - 1) & 1) ? -1.0f : 1.0f;
             const float dj = comp3(d, j);
-            const float xj = comp3(o, j) + ta[i] * dj;
+            const float xj = comp3(o, j) + ta * dj;
             const float w = 1.0f / fabsf(xj);           // 1 / |x_j| at the segment start
             float v2 = 0.0f;
 #pragma unroll

@@ -94,17 +94,31 @@ __device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count) : "memory");
 }
 
-// Wait for the phase with parity `parity` to complete, giving up after `limit` polls (false).
-__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, int limit)
+__device__ __forceinline__ uint64_t globaltimer_ns()
 {
-    uint32_t done = 0;
-    for (int it = 0; it < limit && !done; ++it)
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase with parity `parity` to complete; false once `limit_ns` nanoseconds of the
+// global timer have passed without it (each try_wait may suspend the thread for a while before it
+// reports, so the clock is read after every poll), or after `max_polls` polls should the timer
+// not advance.
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint32_t limit_ns, int max_polls = 1 << 26)
+{
+    const uint64_t t0 = globaltimer_ns();
+    for (int it = 0; it < max_polls; ++it) {
+        uint32_t done;
         asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
                      "selp.u32 %0, 1, 0, p;\n\t}"
                      : "=r"(done)
                      : "r"(smem_addr(mbar)), "r"(parity)
                      : "memory");
-    return done != 0;
+        if (done) return true;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
+    }
+    return false;
 }
 
 // One bulk (TMA, untiled) copy of `bytes` from global to shared memory, completing on `mbar`
