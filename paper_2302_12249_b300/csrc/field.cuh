@@ -217,16 +217,6 @@ grid_done:;
     }
 }
 
-// Density pre-activation from its weighted byte sum k: (28 / 255) k - 14 W, where W = W_V + 3
-// is the total interpolation weight of the sources (the planes' weights sum to one each; W = W_V
-// for a grid-only scene).  Every path that evaluates density calls this one expression, so their
-// opacities agree bit for bit.
-__device__ __forceinline__ float dequant_density(float k, float wsum)
-{
-    return k * (28.0f / 255.0f) - 14.0f * wsum;
-}
-
-
 // ---------------------------------------------------------------------------------------------
 // Weighted byte sums by integer dot products.  The interpolated value of channel c is
 // K_c = sum_i w_i b_ic over the taps i (8 grid corners, then 4 texels per plane), and bytes are
@@ -283,8 +273,40 @@ __device__ __forceinline__ uint32_t weight_word(float a, float b)
     return __float_as_uint(fmaf(a, b, kWMagic));
 }
 
-// Weight words of the first nt taps at scale S (grid corners: trilinear; plane q: bilinear in
-// its column axis (1, 0, 0)[q] and row axis (2, 2, 1)[q]).
+// The weights of tap pair p (taps 2p and 2p + 1, neighbours along x for the grid and along the
+// column axis for a plane): (g, f) times the pair's shared factor v, where g = 1 - f.  Grid pair p:
+// f = f_x, v = the y and z weights of rows (p & 1, p >> 1); plane pair p = 4 + 2q + r: plane q's
+// column fraction and the weight of its row r.  The same weights as grid_w (each rounding in the
+// same order up to the product's association).
+template <int p>
+__device__ __forceinline__ void pair_factors(const Taps &t, float &f, float &v)
+{
+    if constexpr (p < 4) {
+        f = t.fx;
+        v = ((p & 1) ? t.fy : 1.0f - t.fy) * ((p >> 1) ? t.fz : 1.0f - t.fz);
+    } else {
+        constexpr int q = (p - 4) >> 1, r = (p - 4) & 1;
+        constexpr int ca = q == 0 ? 1 : 0, ra = q == 2 ? 1 : 2;     // column axis (1, 0, 0)[q], row axis (2, 2, 1)[q]
+        f = t.fu[ca];
+        v = r ? t.fu[ra] : 1.0f - t.fu[ra];
+    }
+}
+
+// Weight words of tap pair p at scale S (2^23 + round(w S) each).
+template <int p>
+__device__ __forceinline__ void pair_weight_words(const Taps &t, float S, uint32_t &w0, uint32_t &w1)
+{
+    float f, v;
+    pair_factors<p>(t, f, v);
+    const float vs = v * S;
+    w0 = weight_word(1.0f - f, vs);
+    w1 = weight_word(f, vs);
+}
+
+// Weight words of the first nt taps at scale S, all at once (the FP32 form's arrangement, which
+// measured faster there than forming them pair by pair; the 16-bit forms, with a second set of
+// words, do better pair by pair): grid corners trilinear, plane q bilinear in its column axis
+// (1, 0, 0)[q] and row axis (2, 2, 1)[q].
 template <int nt>
 __device__ __forceinline__ void weight_words(const Taps &t, float S, uint32_t w[nt])
 {
@@ -327,42 +349,65 @@ struct DotSums {
     uint32_t lo[8], hi[kPrec == 0 ? 8 : 1];
 };
 
+// One tap pair's contribution.  FP32: the weight words w22 come in; 16-bit forms: the pair's words
+// (both scales) are formed here, just before use, so that only one pair's are live at a time.
+template <int kPrec, int p>
+__device__ __forceinline__ void dot_pair(const Taps &t, DotSums<kPrec> &s, const uint32_t *w22)
+{
+    uint32_t m0, m1;
+    if constexpr (kPrec == 0) {
+        m0 = w22[2 * p];
+        m1 = w22[2 * p + 1];
+    } else {
+        pair_weight_words<p>(t, kW22, m0, m1);
+    }
+    const uint32_t wl = prmt(m0, m1, 0x5410u);     // low 16 bits of both
+    const uint32_t wh = prmt(m0, m1, 0xE6A2u);     // bits 16..22, zero-extended
+    uint32_t B[4];
+    pair_bytes(t.v[2 * p], t.v[2 * p + 1], B);
+    if constexpr (kPrec == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            s.lo[2 * q] = dp2a_lo(wl, B[q], s.lo[2 * q]);
+            s.lo[2 * q + 1] = dp2a_hi(wl, B[q], s.lo[2 * q + 1]);
+            s.hi[2 * q] = dp2a_lo(wh, B[q], s.hi[2 * q]);
+            s.hi[2 * q + 1] = dp2a_hi(wh, B[q], s.hi[2 * q + 1]);
+        }
+    } else {
+        uint32_t n0, n1;
+        pair_weight_words<p>(t, kW16, n0, n1);
+        const uint32_t ws = prmt(n0, n1, 0x5410u);
+        s.lo[0] = dp2a_lo(wl, B[0], s.lo[0]);
+        s.hi[0] = dp2a_lo(wh, B[0], s.hi[0]);
+        s.lo[1] = dp2a_hi(ws, B[0], s.lo[1]);
+#pragma unroll
+        for (int q = 1; q < 4; ++q) {
+            s.lo[2 * q] = dp2a_lo(ws, B[q], s.lo[2 * q]);
+            s.lo[2 * q + 1] = dp2a_hi(ws, B[q], s.lo[2 * q + 1]);
+        }
+    }
+}
+
 template <int kPrec, int nt>
 __device__ __forceinline__ void dot_sums(const Taps &t, DotSums<kPrec> &s)
 {
-    uint32_t w[nt];
-    weight_words<nt>(t, kW22, w);
-    uint32_t w16[kPrec == 0 ? 1 : nt];
-    if constexpr (kPrec != 0) weight_words<nt>(t, kW16, w16);
 #pragma unroll
     for (int c = 0; c < 8; ++c) s.lo[c] = 0u;
 #pragma unroll
     for (int c = 0; c < (kPrec == 0 ? 8 : 1); ++c) s.hi[c] = 0u;
-#pragma unroll
-    for (int p = 0; p < nt / 2; ++p) {
-        const uint32_t wl = prmt(w[2 * p], w[2 * p + 1], 0x5410u);     // low 16 bits of both
-        const uint32_t wh = prmt(w[2 * p], w[2 * p + 1], 0xE6A2u);     // bits 16..22, zero-extended
-        uint32_t B[4];
-        pair_bytes(t.v[2 * p], t.v[2 * p + 1], B);
-        if constexpr (kPrec == 0) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                s.lo[2 * q] = dp2a_lo(wl, B[q], s.lo[2 * q]);
-                s.lo[2 * q + 1] = dp2a_hi(wl, B[q], s.lo[2 * q + 1]);
-                s.hi[2 * q] = dp2a_lo(wh, B[q], s.hi[2 * q]);
-                s.hi[2 * q + 1] = dp2a_hi(wh, B[q], s.hi[2 * q + 1]);
-            }
-        } else {
-            const uint32_t ws = prmt(w16[2 * p], w16[2 * p + 1], 0x5410u);
-            s.lo[0] = dp2a_lo(wl, B[0], s.lo[0]);
-            s.hi[0] = dp2a_lo(wh, B[0], s.hi[0]);
-            s.lo[1] = dp2a_hi(ws, B[0], s.lo[1]);
-#pragma unroll
-            for (int q = 1; q < 4; ++q) {
-                s.lo[2 * q] = dp2a_lo(ws, B[q], s.lo[2 * q]);
-                s.lo[2 * q + 1] = dp2a_hi(ws, B[q], s.lo[2 * q + 1]);
-            }
-        }
+    uint32_t w[kPrec == 0 ? nt : 1];
+    if constexpr (kPrec == 0) weight_words<nt>(t, kW22, w);
+    dot_pair<kPrec, 0>(t, s, w);
+    dot_pair<kPrec, 1>(t, s, w);
+    dot_pair<kPrec, 2>(t, s, w);
+    dot_pair<kPrec, 3>(t, s, w);
+    if constexpr (nt > 8) {
+        dot_pair<kPrec, 4>(t, s, w);
+        dot_pair<kPrec, 5>(t, s, w);
+        dot_pair<kPrec, 6>(t, s, w);
+        dot_pair<kPrec, 7>(t, s, w);
+        dot_pair<kPrec, 8>(t, s, w);
+        dot_pair<kPrec, 9>(t, s, w);
     }
 }
 
@@ -370,10 +415,12 @@ __device__ __forceinline__ void dot_sums(const Taps &t, DotSums<kPrec> &s)
 // the total interpolation weight of the sources (the planes' weights sum to one each; W = W_V for
 // a grid-only scene).  Every path that evaluates a uint8 scene's density calls this one
 // expression, so their opacities agree bit for bit.
-__device__ __forceinline__ float dequant_density(uint32_t lo, uint32_t hi, float wsum)
+template <int kPrec>
+__device__ __forceinline__ float dequant_density(const DotSums<kPrec> &k, float wsum)
 {
     constexpr float A = 28.0f / 255.0f;
-    return fmaf(__uint2float_rn(lo), A * (1.0f / kW22), fmaf(__uint2float_rn(hi), A * (65536.0f / kW22), -14.0f * wsum));
+    return fmaf(__uint2float_rn(k.lo[0]), A * (1.0f / kW22),
+                fmaf(__uint2float_rn(k.hi[0]), A * (65536.0f / kW22), -14.0f * wsum));
 }
 
 // Dense float storage: all eight channels of all 20 taps, summed.

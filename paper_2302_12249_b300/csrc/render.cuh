@@ -561,7 +561,7 @@ __device__ __forceinline__ void eval_field(const FieldView &fv, float p0, float 
         DotSums<kPrec> k;
         dot_sums<kPrec, kTaps<kGeo>>(tp, k);      // 16-bit forms: one-level appearance weights
         const float wsum = tp.wv + (float)kPlaneSources<kGeo>;
-        dens = dequant_density(k.lo[0], k.hi[0], wsum);
+        dens = dequant_density<kPrec>(k, wsum);
         if constexpr (kPrec == 0) ya = app_arg_u8(k, wsum);
         else ya = app_arg_u8_half<kPrec>(k, wsum);
     } else {
