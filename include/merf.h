@@ -130,6 +130,21 @@ merf_status merf_scene_upload(const merf_scene_desc *desc, const int32_t *index_
                               const uint8_t *const *occ_levels, const float *mlp_weights,
                               void *stream, merf_scene **out);
 
+/* merf_scene_upload with the scene's arrays in device memory (on the current device, the same
+ * layouts as merf_scene_upload: index_grid int32 [(L/B)^3], atlas uint8 [n_blocks][B][B][B][8],
+ * planes uint8 [3][R][R][8] or NULL when R = 0, occupancy levels uint8 [N][N][N] (an array of
+ * device pointers in host memory), mlp float32 [883]).  For scenes too large to stage in host
+ * memory, or already on the GPU (Sec. 4.3's baked arrays produced there): the index grid,
+ * occupancy levels and MLP weights (a few MB) are copied to the host and checked as
+ * merf_scene_upload checks them, and, in addition, every atlas slot must be named by exactly one
+ * index-grid entry; the padded atlas and bordered planes are built by kernels on `stream` from
+ * the caller's arrays, which the call only reads.  Synchronises `stream` before returning; the
+ * caller may free its arrays then.  Errors as merf_scene_upload. */
+merf_status merf_scene_upload_device(const merf_scene_desc *desc, const int32_t *d_index_grid,
+                                     const uint8_t *d_atlas, const uint8_t *d_planes,
+                                     const uint8_t *const *d_occ_levels, const float *d_mlp, void *stream,
+                                     merf_scene **out);
+
 /* Same for a dense float32 scene (storage MERF_STORAGE_F32_DENSE): grid float32
  * [L][L][L][8] and planes float32 [3][R][R][8] hold pre-activation values directly
  * (no dequantisation); block_size and n_blocks are ignored. */

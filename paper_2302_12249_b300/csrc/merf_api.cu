@@ -329,6 +329,64 @@ merf_status set_error(merf_status s, const char *fmt, ...)
 merf_status clear_error() { return ok(); }
 }  // namespace merf
 
+// The device index grid: a stored block's atlas slot in bits 0..23 and, in bits 24..30, a mask of
+// its +x/+y/+z neighbour blocks (dx + 2 dy + 4 dz in 1..7, bit 23 + that number) that are not
+// stored or lie past the grid edge; -1 for a block that is not stored.
+static std::vector<int32_t> index_with_neighbour_masks(const int32_t *index_grid, size_t nbi)
+{
+    std::vector<int32_t> ig(nbi * nbi * nbi);
+    auto id_at = [&](size_t bx, size_t by, size_t bz) -> int32_t {
+        if (bx >= nbi || by >= nbi || bz >= nbi) return -1;
+        return index_grid[(bz * nbi + by) * nbi + bx];
+    };
+    for (size_t bz = 0; bz < nbi; ++bz)
+        for (size_t by = 0; by < nbi; ++by)
+            for (size_t bx = 0; bx < nbi; ++bx) {
+                const int32_t id = id_at(bx, by, bz);
+                if (id < 0) { ig[(bz * nbi + by) * nbi + bx] = -1; continue; }
+                uint32_t miss = 0;
+                for (int n = 1; n < 8; ++n)
+                    if (id_at(bx + (n & 1), by + ((n >> 1) & 1), bz + (n >> 2)) < 0) miss |= 1u << (n - 1);
+                ig[(bz * nbi + by) * nbi + bx] = (int32_t)((uint32_t)id | (miss << 24));
+            }
+    return ig;
+}
+
+// The padded atlas from an unpadded one in device memory: CTA `slot` fills the (B+1)^3 voxels of
+// that atlas slot (the block at `coords[slot]` = bx | by << 10 | bz << 20, plus its +x/+y/+z apron
+// from the neighbouring blocks; zero where a neighbour is not stored or past the grid edge).
+// index_grid: the caller's grid (slot or -1), already validated.
+__global__ void pad_atlas_kernel(const uint2 *atlas, const int32_t *index_grid, const uint32_t *coords, int L, int B,
+                                 uint2 *padded)
+{
+    const int slot = blockIdx.x, B1 = B + 1, nb = L / B;
+    const uint32_t c = coords[slot];
+    const int bx = c & 1023, by = (c >> 10) & 1023, bz = c >> 20;
+    uint2 *dst = padded + (size_t)slot * B1 * B1 * B1;
+    for (int v = threadIdx.x; v < B1 * B1 * B1; v += blockDim.x) {
+        const int lx = v % B1, ly = (v / B1) % B1, lz = v / (B1 * B1);
+        const int gx = bx * B + lx, gy = by * B + ly, gz = bz * B + lz;
+        uint2 val = make_uint2(0u, 0u);
+        if (gx < L && gy < L && gz < L) {
+            const int src = index_grid[((size_t)(gz / B) * nb + gy / B) * nb + gx / B];
+            if (src >= 0) val = atlas[(((size_t)src * B + gz % B) * B + gy % B) * B + gx % B];
+        }
+        dst[v] = val;
+    }
+}
+
+// Planes with a one-texel border that repeats their edge texels: [3][R+2][R+2] from [3][R][R].
+__global__ void border_planes_kernel(const uint2 *planes, int R, uint2 *bordered)
+{
+    const int Rp = R + 2;
+    const size_t n = 3ull * Rp * Rp;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+        const int u = (int)(t % Rp), v = (int)((t / Rp) % Rp), q = (int)(t / ((size_t)Rp * Rp));
+        const int su = min(max(u - 1, 0), R - 1), sv = min(max(v - 1, 0), R - 1);
+        bordered[t] = planes[((size_t)q * R + sv) * R + su];
+    }
+}
+
 extern "C" {
 
 merf_status merf_scene_upload(const merf_scene_desc *desc, const int32_t *index_grid, const uint8_t *atlas,
@@ -358,9 +416,10 @@ merf_status merf_scene_upload(const merf_scene_desc *desc, const int32_t *index_
     const int B = desc->block_size, B1 = B + 1, L = desc->grid_res;
     const size_t R = desc->plane_res, nbi = nb;
     std::vector<uint8_t> apron;
-    std::vector<int32_t> ig(nb * nb * nb);
+    std::vector<int32_t> ig;
     try {
         apron.assign((size_t)desc->n_blocks * B1 * B1 * B1 * 8, 0);
+        ig = index_with_neighbour_masks(index_grid, nbi);
     } catch (...) {
         return fail(MERF_ERR_OOM, "host memory for the padded atlas");
     }
@@ -372,11 +431,7 @@ merf_status merf_scene_upload(const merf_scene_desc *desc, const int32_t *index_
         for (size_t by = 0; by < nbi; ++by)
             for (size_t bx = 0; bx < nbi; ++bx) {
                 const int32_t id = id_at(bx, by, bz);
-                if (id < 0) { ig[(bz * nbi + by) * nbi + bx] = -1; continue; }
-                uint32_t miss = 0;
-                for (int n = 1; n < 8; ++n)
-                    if (id_at(bx + (n & 1), by + ((n >> 1) & 1), bz + (n >> 2)) < 0) miss |= 1u << (n - 1);
-                ig[(bz * nbi + by) * nbi + bx] = (int32_t)((uint32_t)id | (miss << 24));
+                if (id < 0) continue;
                 uint8_t *dst = apron.data() + (size_t)id * B1 * B1 * B1 * 8;
                 for (int lz = 0; lz < B1; ++lz)
                     for (int ly = 0; ly < B1; ++ly)
@@ -407,6 +462,111 @@ merf_status merf_scene_upload(const merf_scene_desc *desc, const int32_t *index_
             }
     return upload_common(desc, apron.data(), apron.size(), padded.data(), padded.size(), ig.data(),
                          nb * nb * nb * sizeof(int32_t), occ_levels, mlp_weights, stream, out);
+}
+
+merf_status merf_scene_upload_device(const merf_scene_desc *desc, const int32_t *d_index_grid,
+                                     const uint8_t *d_atlas, const uint8_t *d_planes,
+                                     const uint8_t *const *d_occ_levels, const float *d_mlp, void *stream,
+                                     merf_scene **out)
+{
+    const merf::NvtxRange nvtx_range("merf_scene_upload_device");
+    merf_status st = check_desc(desc, MERF_STORAGE_U8_SPARSE);
+    if (st) return st;
+    if (!out) return fail(MERF_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!d_index_grid || (desc->plane_res > 0 && !d_planes) || !d_mlp || !d_occ_levels ||
+        (desc->n_blocks > 0 && !d_atlas))
+        return fail(MERF_ERR_INVALID_ARG, "a scene array is NULL");
+    for (int l = 0; l < desc->n_occ_levels; ++l)
+        if (!d_occ_levels[l]) return fail(MERF_ERR_INVALID_ARG, "occ_levels[%d] is NULL", l);
+    if (desc->n_blocks >= (1 << 24)) return fail(MERF_ERR_INVALID_ARG, "n_blocks %d >= 2^24", desc->n_blocks);
+    cudaStream_t cs = (cudaStream_t)stream;
+    // the small arrays come to the host for the checks merf_scene_upload makes
+    const size_t nb = (size_t)desc->grid_res / desc->block_size, n_index = nb * nb * nb;
+    std::vector<int32_t> index(n_index);
+    std::vector<std::vector<uint8_t>> occ(desc->n_occ_levels);
+    std::vector<float> mlp(MERF_MLP_PARAMS);
+    cudaError_t e = cudaMemcpyAsync(index.data(), d_index_grid, n_index * sizeof(int32_t), cudaMemcpyDeviceToHost, cs);
+    for (int l = 0; l < desc->n_occ_levels && e == cudaSuccess; ++l) {
+        occ[l].resize((size_t)desc->occ_res[l] * desc->occ_res[l] * desc->occ_res[l]);
+        e = cudaMemcpyAsync(occ[l].data(), d_occ_levels[l], occ[l].size(), cudaMemcpyDeviceToHost, cs);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mlp.data(), d_mlp, sizeof(float) * MERF_MLP_PARAMS, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) return fail(MERF_ERR_CUDA, "reading the scene's index, occupancy and MLP: %s", cudaGetErrorString(e));
+    std::vector<uint32_t> coords((size_t)std::max(desc->n_blocks, 1), 0xffffffffu);
+    for (size_t i = 0; i < n_index; ++i) {
+        if (index[i] < -1 || index[i] >= desc->n_blocks)
+            return fail(MERF_ERR_INVALID_ARG, "index_grid[%zu] = %d outside [-1, %d)", i, index[i], desc->n_blocks);
+        if (index[i] >= 0) {
+            if (coords[index[i]] != 0xffffffffu)
+                return fail(MERF_ERR_INVALID_ARG, "atlas slot %d is named by two index-grid entries", index[i]);
+            coords[index[i]] = (uint32_t)(i % nb) | ((uint32_t)((i / nb) % nb) << 10) | ((uint32_t)(i / (nb * nb)) << 20);
+        }
+    }
+    for (int b = 0; b < desc->n_blocks; ++b)
+        if (coords[b] == 0xffffffffu) return fail(MERF_ERR_INVALID_ARG, "atlas slot %d is named by no index-grid entry", b);
+    std::vector<const uint8_t *> occ_ptrs(desc->n_occ_levels);
+    for (int l = 0; l < desc->n_occ_levels; ++l) occ_ptrs[l] = occ[l].data();
+    if ((st = check_occupancy(desc, occ_ptrs.data()))) return st;
+    for (int i = 0; i < MERF_MLP_PARAMS; ++i)
+        if (!std::isfinite(mlp[i])) return fail(MERF_ERR_INVALID_ARG, "mlp_weights[%d] not finite", i);
+    std::vector<int32_t> ig;
+    try {
+        ig = index_with_neighbour_masks(index.data(), nb);
+    } catch (...) {
+        return fail(MERF_ERR_OOM, "host memory for the index grid");
+    }
+    // Device layout as merf_scene_upload builds it, made on the device: the padded atlas and the
+    // bordered planes by kernels from the caller's arrays; the rest copied.
+    const int B = desc->block_size, B1 = B + 1;
+    const size_t R = desc->plane_res, Rp = R + 2;
+    const size_t atlas_bytes = (size_t)desc->n_blocks * B1 * B1 * B1 * 8, plane_bytes = R > 0 ? 3 * Rp * Rp * 8 : 0;
+    size_t total = atlas_bytes + plane_bytes + n_index * sizeof(int32_t) + merf::kMlpBlockBytes;
+    for (int l = 0; l < desc->n_occ_levels; ++l) total += occ[l].size();
+    if (g_budget && total > g_budget)
+        return fail(MERF_ERR_OOM, "scene needs %zu device bytes, budget is %zu", total, g_budget);
+    merf_scene *sc = new merf_scene();
+    sc->desc = *desc;
+    cudaGetDevice(&sc->device);
+    uint32_t *d_coords = nullptr;
+    auto bail = [&](merf_status code, const char *what, cudaError_t err) {
+        cudaGetLastError();
+        cudaFree(d_coords);
+        free_scene_memory(sc);
+        delete sc;
+        return fail(code, "%s: %s", what, cudaGetErrorString(err));
+    };
+    struct Item { void **dst; size_t n; };
+    std::vector<Item> items = {{&sc->atlas, atlas_bytes}, {&sc->planes, plane_bytes},
+                               {&sc->index_grid, n_index * sizeof(int32_t)}, {&sc->mlp, merf::kMlpBlockBytes},
+                               {(void **)&d_coords, coords.size() * sizeof(uint32_t)}};
+    for (int l = 0; l < desc->n_occ_levels; ++l) items.push_back({&sc->occ[l], occ[l].size()});
+    for (auto &it : items) {
+        if (it.n == 0) continue;
+        if ((e = cudaMalloc(it.dst, it.n)) != cudaSuccess)
+            return bail(e == cudaErrorMemoryAllocation ? MERF_ERR_OOM : MERF_ERR_CUDA, "cudaMalloc", e);
+    }
+    e = cudaMemcpyAsync(sc->index_grid, ig.data(), n_index * sizeof(int32_t), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_coords, coords.data(), coords.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, cs);
+    for (int l = 0; l < desc->n_occ_levels && e == cudaSuccess; ++l)
+        e = cudaMemcpyAsync(sc->occ[l], d_occ_levels[l], occ[l].size(), cudaMemcpyDeviceToDevice, cs);
+    if (e == cudaSuccess) e = put_mlp_block(sc->mlp, d_mlp, cudaMemcpyDeviceToDevice, cs);
+    if (e == cudaSuccess && desc->n_blocks > 0) {
+        pad_atlas_kernel<<<desc->n_blocks, 256, 0, cs>>>((const uint2 *)d_atlas, d_index_grid, d_coords, desc->grid_res,
+                                                         B, (uint2 *)sc->atlas);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && R > 0) {
+        border_planes_kernel<<<4 * 148, 256, 0, cs>>>((const uint2 *)d_planes, (int)R, (uint2 *)sc->planes);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) return bail(MERF_ERR_CUDA, "building the scene on the device", e);
+    cudaFree(d_coords);
+    sc->bytes = total;
+    *out = sc;
+    return ok();
 }
 
 merf_status merf_scene_upload_dense(const merf_scene_desc *desc, const float *grid, const float *planes,

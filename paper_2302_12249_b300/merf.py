@@ -25,7 +25,8 @@ NOALLOC_STAGING_BYTES = 32 << 20
 AUX_CD, AUX_F, AUX_T, AUX_NLAT, AUX_NEVAL, AUX_NAPP, AUX_TERM = 0, 3, 7, 8, 9, 10, 11
 CNT_RAYS, CNT_LATTICE, CNT_EVAL, CNT_APPEAR = 0, 1, 2, 3
 
-EXPORTS = ("merf_scene_upload", "merf_scene_upload_dense", "merf_scene_load", "merf_scene_free",
+EXPORTS = ("merf_scene_upload", "merf_scene_upload_dense", "merf_scene_upload_device", "merf_scene_load",
+           "merf_scene_free",
            "merf_scene_device_bytes", "merf_render", "merf_render_aux", "merf_render_host", "merf_render_host_noalloc",
            "merf_trace", "merf_set_device_budget", "merf_scene_set_dense", "merf_scene_param_version",
            "merf_render_backward",
@@ -93,6 +94,7 @@ def lib():
         vp, i32 = ct.c_void_p, ct.c_int
         L.merf_scene_upload.argtypes = [ct.POINTER(Desc), vp, vp, vp, vp, vp, vp, ct.POINTER(vp)]
         L.merf_scene_upload_dense.argtypes = [ct.POINTER(Desc), vp, vp, vp, vp, vp, ct.POINTER(vp)]
+        L.merf_scene_upload_device.argtypes = [ct.POINTER(Desc), vp, vp, vp, vp, vp, vp, ct.POINTER(vp)]
         L.merf_scene_free.argtypes = [vp]
         L.merf_scene_free.restype = None
         L.merf_scene_device_bytes.argtypes = [vp]
@@ -131,7 +133,8 @@ def lib():
             getattr(L, name).restype = ct.c_int
         L.merf_last_error.restype = ct.c_char_p
         L.merf_version.restype = ct.c_char_p
-        for name in ("merf_scene_upload", "merf_scene_upload_dense", "merf_render", "merf_render_aux",
+        for name in ("merf_scene_upload", "merf_scene_upload_dense", "merf_scene_upload_device", "merf_render",
+                     "merf_render_aux",
                      "merf_render_host", "merf_render_host_noalloc", "merf_trace"):
             getattr(L, name).restype = ct.c_int
         _lib = L
@@ -191,7 +194,23 @@ class Scene:
         mlp = np.ascontiguousarray(scene.mlp, dtype=np.float32)
         handle = ct.c_void_p()
         s = _stream(stream)
-        if cfg.storage == "u8":
+        if cfg.storage == "u8" and torch.is_tensor(scene.atlas) and scene.atlas.is_cuda:
+            # arrays already on the device (merf_scene_upload_device): small ones follow them there
+            d.storage = STORAGE_U8_SPARSE
+            d.block_size, d.n_blocks = cfg.B, int(scene.atlas.shape[0])
+            dev = scene.atlas.device
+            occ_d = [torch.as_tensor(np.ascontiguousarray(o, dtype=np.uint8)).to(dev) for o in scene.occ]
+            ig = torch.as_tensor(scene.index_grid).to(device=dev, dtype=torch.int32).contiguous()
+            atlas = scene.atlas.contiguous()
+            planes = None if scene.planes is None else torch.as_tensor(scene.planes).to(dev).contiguous()
+            mlp_d = torch.as_tensor(mlp).to(dev)
+            dptrs = (ct.c_void_p * MAX_OCC_LEVELS)(*[o.data_ptr() for o in occ_d])
+            _check(lib().merf_scene_upload_device(ct.byref(d), ct.c_void_p(ig.data_ptr()),
+                                                  ct.c_void_p(atlas.data_ptr()),
+                                                  None if planes is None else ct.c_void_p(planes.data_ptr()),
+                                                  ct.cast(dptrs, ct.c_void_p), ct.c_void_p(mlp_d.data_ptr()), s,
+                                                  ct.byref(handle)))
+        elif cfg.storage == "u8":
             d.storage = STORAGE_U8_SPARSE
             d.block_size, d.n_blocks = cfg.B, scene.n_blocks
             ig = np.ascontiguousarray(scene.index_grid, dtype=np.int32)

@@ -125,7 +125,7 @@ class Scene:
         n = sum(int(o.nbytes) for o in self.occ) + int(self.mlp.nbytes)
         for a in (self.index_grid, self.atlas, self.planes, self.grid_f32, self.planes_f32):
             if a is not None:
-                n += int(a.nbytes)
+                n += int(a.nbytes) if isinstance(a, np.ndarray) else a.numel() * a.element_size()
         return n
 
 
@@ -191,8 +191,12 @@ def _mlp_weights(seed: int) -> np.ndarray:
     return flat
 
 
-def make_scene(name_or_cfg, seed: Optional[int] = None, mlp_seed: int = SEED_MLP) -> Scene:
-    """Build a seeded baked scene.  `name_or_cfg` is a key of CONFIGS or a SceneConfig."""
+def make_scene(name_or_cfg, seed: Optional[int] = None, mlp_seed: int = SEED_MLP, device: str = "cpu") -> Scene:
+    """Build a seeded baked scene.  `name_or_cfg` is a key of CONFIGS or a SceneConfig.  device
+    "cuda" (uint8 grid-only scenes): the stored blocks are evaluated on the GPU and the atlas is
+    returned as a CUDA tensor, for scenes whose atlas is too large to stage in host memory (the
+    same fields and quantisation; values may differ from the CPU build in the last bits of FP64
+    summation order, so a byte can differ where a value sits on a rounding boundary)."""
     cfg = CONFIGS[name_or_cfg] if isinstance(name_or_cfg, str) else name_or_cfg
     seed = SEED_SCENE if seed is None else seed
     rng = np.random.default_rng(seed)
@@ -266,23 +270,26 @@ def make_scene(name_or_cfg, seed: Optional[int] = None, mlp_seed: int = SEED_MLP
                 planes[pi, :, :, 1 + ch] = app[ch].clamp(-M_APPEAR, M_APPEAR).to(torch.float32)
 
     # ---- 3D grid values on a set of voxel boxes
+    if device != "cpu" and not (cfg.grid_only and cfg.storage == "u8"):
+        raise ValueError("device generation is for uint8 grid-only scenes")
     gax = _centres(L, -2.0, 2.0)
-    gx, gy, gz = gauss(gax, 0), gauss(gax, 1), gauss(gax, 2)
+    gx, gy, gz = (gauss(gax, d).to(device) for d in range(3))
     vol_facs = [_wave_factors(k, phi, a, [gax, gax, gax]) for (k, phi, a) in vol_waves]
+    vol_facs = [(coef.to(device), [f.to(device) for f in facs]) for coef, facs in vol_facs]
     # grid only: the plane fields evaluated at the grid's voxel centres, [3][C][L][L] (row, column)
     ptab = None
     if cfg.grid_only:
-        ptab = torch.empty((3, C, L, L), dtype=torch.float64)
+        ptab = torch.empty((3, C, L, L), dtype=torch.float64, device=device)
         for pi in range(3):
-            ptab[pi, 0] = plane_field([plane_dens[pi]], M_DENSITY, gax)[0]
+            ptab[pi, 0] = plane_field([plane_dens[pi]], M_DENSITY, gax)[0].to(device)
             for ch, v in enumerate(plane_field(plane_waves[pi], M_APPEAR, gax)):
-                ptab[pi, 1 + ch] = v
+                ptab[pi, 1 + ch] = v.to(device)
 
     def grid_values(z0: torch.Tensor, y0: torch.Tensor, x0: torch.Tensor, n: int) -> torch.Tensor:
         """Pre-quantisation values of boxes of n^3 voxels starting at (z0, y0, x0): [nb, n, n, n, C]."""
-        ar = torch.arange(n)
+        ar = torch.arange(n, device=z0.device)
         iz, iy, ix = z0[:, None] + ar, y0[:, None] + ar, x0[:, None] + ar       # [nb, n]
-        out = torch.empty((z0.shape[0], n, n, n, C), dtype=torch.float64)
+        out = torch.empty((z0.shape[0], n, n, n, C), dtype=torch.float64, device=z0.device)
         tau = amp * torch.einsum("bkz,bky,bkx->bzyx", gz[:, iz].permute(1, 0, 2),
                                  gy[:, iy].permute(1, 0, 2), gx[:, ix].permute(1, 0, 2))
         out[..., 0] = torch.log(torch.clamp(tau, min=1e-30)).clamp(LOG_TAU_MIN, M_DENSITY)
@@ -317,8 +324,9 @@ def make_scene(name_or_cfg, seed: Optional[int] = None, mlp_seed: int = SEED_MLP
         bz, by, bx = torch.nonzero(need, as_tuple=True)
         nblk = int(bz.numel())
         ids[bz, by, bx] = torch.arange(nblk, dtype=torch.int32)
-        atlas = torch.empty((nblk, B, B, B, C), dtype=torch.uint8)
-        chunk = max(1, (1 << 20) // (B ** 3))
+        atlas = torch.empty((nblk, B, B, B, C), dtype=torch.uint8, device=device)
+        chunk = max(1, ((1 << 20) if device == "cpu" else (1 << 23)) // (B ** 3))
+        bz, by, bx = bz.to(device), by.to(device), bx.to(device)
         for s in range(0, nblk, chunk):
             e = min(nblk, s + chunk)
             vals = grid_values(bz[s:e] * B, by[s:e] * B, bx[s:e] * B, B)
@@ -326,7 +334,7 @@ def make_scene(name_or_cfg, seed: Optional[int] = None, mlp_seed: int = SEED_MLP
             for ch in range(1, C):
                 atlas[s:e, ..., ch] = _quantise(vals[..., ch], M_APPEAR)
         scene.index_grid = ids.numpy()
-        scene.atlas = atlas.numpy()
+        scene.atlas = atlas.numpy() if device == "cpu" else atlas
         scene.stats["block_fraction"] = nblk / float(nbx ** 3)
     else:
         z0 = torch.arange(0, L, 16)

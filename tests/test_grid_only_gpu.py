@@ -1,5 +1,6 @@
 """GPU parity of grid-only scenes (plane_res 0, t~ = V): the SNeRG++-style baseline that the
 paper compares MERF with in Sec. 6, rendered by the same kernel with the plane taps compiled out."""
+import dataclasses
 import math
 
 import numpy as np
@@ -59,12 +60,11 @@ def test_grid_only_paper_scale_sampled_pixels():
     assert err.max() <= parity.RGB_TOL, (err.max(), np.argmax(err))
 
 
-# FP16 meets the precision form's 2e-3 per channel here.  BF16 does not on this scene (2.6e-3
-# measured): folding the planes' short wavelengths into a 64^3 grid leaves neighbouring voxels up
-# to ~100 byte steps apart, and a bfloat16 accumulator (8 significant bits) cannot carry
-# interpolation corrections of that size to 2e-3; on the MERF scenes BF16 stays at 6e-5.  Its
-# bar here is PSNR > 50 dB with at most 5e-3 per channel.
-@pytest.mark.parametrize("prec,tol", [(merf.PREC_FP16, 2e-3), (merf.PREC_BF16, 5e-3)])
+# Both 16-bit forms meet the precision form's 2e-3 per channel here, although folding the
+# planes' short wavelengths into a 64^3 grid leaves neighbouring voxels up to ~100 byte steps
+# apart: their appearance sums are exact integers with 16-bit weights (a bfloat16 accumulator,
+# used before, reached 2.6e-3 on this scene).
+@pytest.mark.parametrize("prec,tol", [(merf.PREC_FP16, 2e-3), (merf.PREC_BF16, 2e-3)])
 def test_grid_only_reduced_precision(tiny_grid, prec, tol):
     """FP16 / BF16 appearance arithmetic on a grid-only scene against the oracle, and the same
     evaluated samples and transmittance as the FP32 path."""
@@ -91,3 +91,77 @@ def test_server_refuses_grid_only_scenes(tiny_grid):
     with pytest.raises(merf.MerfError) as e:
         merf.Server([gs], pool_bytes=1 << 24, step=1 / 64)
     assert e.value.status == merf.ERR_UNSUPPORTED
+
+
+def _blocks_near_rays(cams, pix, step, L, B):
+    """Linear indices of every grid block that a trilinear corner of any lattice sample of the
+    listed rays can fall in: FP64 lattice positions along each ray's contracted segments, both
+    corners per axis, each widened by 0.01 voxel for FP32 position rounding."""
+    nb = L // B
+    found = []
+    for c, i, j in pix:
+        o, d = oracle.ray(cams[c], int(i), int(j))
+        sg = oracle.Segments(o, d)
+        segs = [sg[m] for m in range(len(sg))]
+        s0 = np.array([g["s0"] for g in segs])
+        n = int(math.floor(sg.total / step)) + 1
+        s = (np.arange(n) + 0.5) * step
+        s = s[(np.arange(n) + 1.0) * step < sg.total]
+        m = np.clip(np.searchsorted(s0, s, side="right") - 1, 0, len(segs) - 1)
+        a = np.array([g["a"] for g in segs])[m]
+        b = np.array([g["b"] for g in segs])[m]
+        ln = np.array([max(g["len"], 1e-300) for g in segs])[m]
+        p = a + ((s - s0[m]) / ln)[:, None] * (b - a)
+        u = (p + 2.0) / 4.0 * L - 0.5
+        lo = np.clip(np.floor(u - 0.01), 0, L - 1).astype(np.int64) // B
+        hi = np.clip(np.floor(u + 0.01) + 1, 0, L - 1).astype(np.int64) // B
+        for cz in (lo[:, 2], hi[:, 2]):
+            for cy in (lo[:, 1], hi[:, 1]):
+                for cx in (lo[:, 0], hi[:, 0]):
+                    found.append(np.unique((cz * nb + cy) * nb + cx))
+    return np.unique(np.concatenate(found))
+
+
+def test_grid_only_paper_default_2048():
+    """SNeRG++ at the paper's default grid (Sec. 6: L = 2048 in 16^3 blocks, about 24 GB of stored
+    blocks, 28 GB on the device with the aprons), generated on the GPU and uploaded from device
+    memory (merf_scene_upload_device); the benchmark's 8 cameras at 1920 x 1080.  The oracle gets
+    an atlas restricted to the blocks the sampled rays can reach (every other block marked not
+    stored): exact for those rays."""
+    sc = synth.make_scene("snerg2048", device="cuda")
+    assert torch.is_tensor(sc.atlas) and sc.atlas.shape[0] > 500_000
+    gs = merf.Scene(sc)
+    assert gs.device_bytes > 20e9
+    cams = synth.config_cameras("paper")
+    W, H, step, L, B = 1920, 1080, 1 / 256, 2048, 16
+    out = merf.render(gs, cams, W, H, step)
+    torch.cuda.synchronize()
+    pix, lin = parity.pick_pixels(cams.shape[0], W, H, 200, seed=8)
+    rgb = out.reshape(-1, 3)[torch.from_numpy(lin).cuda()].double().cpu().numpy()
+    del out
+    gs.close()
+    near = _blocks_near_rays(cams, pix, step, L, B)
+    ids = sc.index_grid.reshape(-1)
+    keep = near[ids[near] >= 0]
+    sub_ids = np.full(ids.shape, -1, np.int32)
+    sub_ids[keep] = np.arange(keep.size, dtype=np.int32)
+    slots = torch.from_numpy(ids[keep].astype(np.int64)).cuda()
+    sub = dataclasses.replace(sc, index_grid=sub_ids.reshape(sc.index_grid.shape),
+                              atlas=sc.atlas[slots].cpu().numpy())
+    del sc, slots
+    torch.cuda.empty_cache()
+    lo, hi = parity.oracle_rgb(oracle.OracleScene(sub), cams, W, H, step, pix=pix)
+    err = parity.max_err(rgb, lo, hi)
+    assert err.max() <= parity.RGB_TOL, (err.max(), np.argmax(err))
+
+
+def test_device_upload_equals_host_upload(tiny_scene):
+    """merf_scene_upload_device builds the same scene as merf_scene_upload: images identical bit
+    for bit (tiny scene with planes, and a grid-only one)."""
+    for sc in (tiny_scene, synth.make_scene("tiny_grid")):
+        cams = synth.sphere_cameras(2, 40, 32, radius=2.5, seed=31)
+        ref = merf.render(merf.Scene(sc), cams, 40, 32, sc.cfg.step)
+        dev = dataclasses.replace(sc, atlas=torch.from_numpy(sc.atlas).cuda(),
+                                  planes=None if sc.planes is None else torch.from_numpy(sc.planes).cuda())
+        got = merf.render(merf.Scene(dev), cams, 40, 32, sc.cfg.step)
+        assert torch.equal(ref, got)

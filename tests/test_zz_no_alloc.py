@@ -16,10 +16,12 @@ from tests import parity
 pytestmark = pytest.mark.gpu
 
 
-def _noalloc(gs, cams, W, H, step):
-    """Call the entry point through the C ABI; returns the host image as numpy."""
+def _noalloc(gs, cams, W, H, step, pinned=True):
+    """Call the entry point through the C ABI; returns the host image as numpy.  pinned False: the
+    output is ordinary pageable host memory, which the copy out of the staging area must also
+    serve."""
     cams = merf.cameras(cams)
-    host = torch.full((cams.shape[0], H, W, 3), float("nan"), dtype=torch.float32, pin_memory=True)
+    host = torch.full((cams.shape[0], H, W, 3), float("nan"), dtype=torch.float32, pin_memory=pinned)
     o = merf.opts(step)
     st = merf.lib().merf_render_host_noalloc(gs.handle, cams.ctypes.data_as(ct.c_void_p), cams.shape[0], W, H,
                                              ct.c_void_p(host.data_ptr()), ct.byref(o),
@@ -36,6 +38,19 @@ def test_noalloc_matches_render_on_consecutive_calls(tiny_scene):
         cams = synth.sphere_cameras(n, W, H, radius=3.0, seed=seed)
         ref = merf.render(gs, cams, W, H, step).cpu().numpy()
         got = _noalloc(gs, cams, W, H, step)
+        assert np.isfinite(got).all()
+        assert np.abs(got - ref).max() <= parity.RGB_TOL
+    gs.close()
+
+
+def test_noalloc_pageable_output_on_consecutive_calls(tiny_scene):
+    """The same with pageable host output (not page-locked)."""
+    gs = merf.Scene(tiny_scene)
+    step = tiny_scene.cfg.step
+    for n, W, H, seed in ((2, 56, 40, 23), (3, 32, 24, 24)):
+        cams = synth.sphere_cameras(n, W, H, radius=3.0, seed=seed)
+        ref = merf.render(gs, cams, W, H, step).cpu().numpy()
+        got = _noalloc(gs, cams, W, H, step, pinned=False)
         assert np.isfinite(got).all()
         assert np.abs(got - ref).max() <= parity.RGB_TOL
     gs.close()
