@@ -165,3 +165,36 @@ def test_device_upload_equals_host_upload(tiny_scene):
                                   planes=None if sc.planes is None else torch.from_numpy(sc.planes).cuda())
         got = merf.render(merf.Scene(dev), cams, 40, 32, sc.cfg.step)
         assert torch.equal(ref, got)
+
+
+def test_device_upload_validates_like_host_upload(tiny_scene):
+    """merf_scene_upload_device refuses what merf_scene_upload refuses (an index outside the
+    atlas, an occupancy pyramid that is not max-pooled) and also an atlas slot named twice or not
+    at all; nothing is left allocated."""
+    sc = tiny_scene
+    atlas = torch.from_numpy(sc.atlas).cuda()
+
+    def upload(**kw):
+        dev = dataclasses.replace(sc, atlas=atlas, planes=torch.from_numpy(sc.planes).cuda(), **kw)
+        with pytest.raises(merf.MerfError) as e:
+            merf.Scene(dev)
+        return e.value.status, merf.lib().merf_last_error().decode()
+
+    ids = sc.index_grid.copy()
+    ids.reshape(-1)[np.argmax(ids.reshape(-1) >= 0)] = sc.n_blocks          # outside the atlas
+    st, msg = upload(index_grid=ids)
+    assert st == merf.ERR_INVALID_ARG and "outside" in msg
+    ids = sc.index_grid.copy()
+    flat = ids.reshape(-1)
+    stored = np.nonzero(flat >= 0)[0]
+    flat[stored[1]] = flat[stored[0]]                                        # one slot named twice
+    st, msg = upload(index_grid=ids)
+    assert st == merf.ERR_INVALID_ARG and "named" in msg
+    occ = [o.copy() for o in sc.occ]
+    if len(occ) > 1:
+        occ[1][:] = 0
+        st, msg = upload(occ=occ)
+        assert st == merf.ERR_INVALID_ARG and "occupancy" in msg
+    free0 = torch.cuda.mem_get_info()[0]
+    torch.cuda.synchronize()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) < (64 << 20)
