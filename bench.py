@@ -461,7 +461,7 @@ def _serving_stream(srv, n_scenes: int, n_requests: int, rate, seed_arrivals: in
 
 
 def _serving(gs_first, n_requests: int, rate: float = 200.0, seed_arrivals: int = 4000, max_tiles: int = 16384,
-             sweep=((300.0, 4000), (400.0, 4000), (None, 2000))):
+             max_tiles_backlog: int = 65536, sweep=((300.0, 4000), (400.0, 4000), (None, 2000))):
     """Serving form: four resident paper-scale scenes, Poisson arrivals, random scene and orbit
     camera, resolution uniform over SERVE_RES, FP16 continuous batching.  Latency is measured by the
     library from submission to the image being in host memory.  The configured stream (200
@@ -472,7 +472,8 @@ def _serving(gs_first, n_requests: int, rate: float = 200.0, seed_arrivals: int 
     scenes = [gs_first] + [merf.Scene(synth.make_scene("paper", seed=synth.SEED_SCENE + k)) for k in (1, 2, 3)]
     free_b, total_b = torch.cuda.mem_get_info()
     pool = int(min(4 << 30, free_b // 4))
-    srv = merf.Server(scenes, pool_bytes=pool, step=STEP, max_tiles_per_iter=max_tiles, precision=merf.PREC_FP16)
+    srv = merf.Server(scenes, pool_bytes=pool, step=STEP, max_tiles_per_iter=max_tiles, precision=merf.PREC_FP16,
+                      max_tiles_backlog=max_tiles_backlog)
     bufs = {r: queue.Queue() for r in range(len(SERVE_RES))}
     for r, (W, H) in enumerate(SERVE_RES):
         for _ in range(48):
@@ -492,7 +493,8 @@ def _serving(gs_first, n_requests: int, rate: float = 200.0, seed_arrivals: int 
     srv.close()
     for sc in scenes[1:]:
         sc.close()
-    main.update({"precision": "fp16", "max_tiles_per_iter": max_tiles, "iterations": st["iterations"] - it0,
+    main.update({"precision": "fp16", "max_tiles_per_iter": max_tiles, "max_tiles_backlog": max_tiles_backlog,
+                 "iterations": st["iterations"] - it0,
                  "peak_admitted": st["peak_admitted"], "pool_mb": st["pool_bytes"] / 1e6,
                  "peak_pool_mb": st["peak_pool_bytes"] / 1e6,
                  "sweep": runs,

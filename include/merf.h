@@ -298,7 +298,10 @@ typedef struct merf_server_opts {
     float step;                   /* lattice step, as in merf_render_opts */
     float t_term;                 /* early-termination threshold */
     int32_t early_term;
-    int32_t reserved;             /* must be 0 */
+    int32_t max_tiles_backlog;    /* 0, or max_tiles_per_iter .. 65536: tiles an iteration may carry
+                                     while more than twice max_tiles_per_iter tiles of admitted and
+                                     queued requests wait to be scheduled (fewer, larger iterations
+                                     under load; 0 keeps every iteration at max_tiles_per_iter) */
 } merf_server_opts;
 
 typedef struct merf_server_stats {

@@ -248,10 +248,13 @@ merf_status merf_server_create(const merf_scene *const *scenes, int n_scenes, co
     if (!scenes || n_scenes < 1 || n_scenes > merf::kServeMaxScenes)
         return merf::set_error(MERF_ERR_INVALID_ARG, "n_scenes %d not in [1, %d]", n_scenes, merf::kServeMaxScenes);
     if (!opts) return merf::set_error(MERF_ERR_INVALID_ARG, "opts is NULL");
-    if (opts->reserved != 0) return merf::set_error(MERF_ERR_INVALID_ARG, "reserved must be 0");
     if (opts->max_tiles_per_iter < 1 || opts->max_tiles_per_iter > merf::kServeMaxTiles)
         return merf::set_error(MERF_ERR_INVALID_ARG, "max_tiles_per_iter %d not in [1, %d]", opts->max_tiles_per_iter,
                                merf::kServeMaxTiles);
+    if (opts->max_tiles_backlog != 0 &&
+        (opts->max_tiles_backlog < opts->max_tiles_per_iter || opts->max_tiles_backlog > merf::kServeMaxTiles))
+        return merf::set_error(MERF_ERR_INVALID_ARG, "max_tiles_backlog %d: 0 or in [max_tiles_per_iter, %d]",
+                               opts->max_tiles_backlog, merf::kServeMaxTiles);
     if (opts->precision != MERF_PREC_FP32 && opts->precision != MERF_PREC_FP16 && opts->precision != MERF_PREC_BF16)
         return merf::set_error(MERF_ERR_INVALID_ARG, "precision %d is not a MERF_PREC_* value", opts->precision);
     if (!(opts->step >= 1e-5f) || !(opts->step < 1e30f) || !(opts->t_term >= 0.0f) || !(opts->t_term < 1.0f) ||
@@ -321,7 +324,7 @@ merf_status merf_server_create(const merf_scene *const *scenes, int n_scenes, co
     merf_server *srv = new merf_server();
     srv->be = s;
     srv->sched = new merf::ServeScheduler(*s, n_scenes, opts->pool_bytes / sizeof(float), opts->max_tiles_per_iter,
-                                          serve_err);
+                                          serve_err, opts->max_tiles_backlog);
     srv->sched->start();
     *out = srv;
     return merf::clear_error();

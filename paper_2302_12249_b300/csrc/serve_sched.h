@@ -144,8 +144,11 @@ class ServeScheduler {
 public:
     using Clock = std::chrono::steady_clock;
 
-    ServeScheduler(ServeBackend &be, int n_scenes, size_t pool_floats, int max_tiles_per_iter, ServeErrFn err)
-        : be_(be), err_(err), n_scenes_(n_scenes), max_tiles_(max_tiles_per_iter), pool_(pool_floats & ~(size_t)63)
+    ServeScheduler(ServeBackend &be, int n_scenes, size_t pool_floats, int max_tiles_per_iter, ServeErrFn err,
+                   int max_tiles_backlog = 0)
+        : be_(be), err_(err), n_scenes_(n_scenes), max_tiles_(max_tiles_per_iter),
+          max_tiles_backlog_(max_tiles_backlog > max_tiles_per_iter ? max_tiles_backlog : max_tiles_per_iter),
+          pool_(pool_floats & ~(size_t)63)
     {
         st_.pool_bytes = pool_.capacity() * sizeof(float);
     }
@@ -343,12 +346,27 @@ private:
         cv_done_.notify_all();
     }
 
+    // (mutex held) tiles the next iteration may carry: max_tiles_, or, while the admitted and queued
+    // requests hold more than twice that many tiles not yet scheduled, up to max_tiles_backlog_
+    // (half the backlog at most): under load, fewer and larger iterations spend less on each
+    // iteration's launch and uneven finish, and latency is queueing then anyway
+    int iteration_cap() const
+    {
+        if (max_tiles_backlog_ <= max_tiles_) return max_tiles_;
+        long long backlog = 0;
+        for (const ServeRequest *r : active_) backlog += r->tiles_total - r->tiles_next;
+        for (const ServeRequest *r : pending_) backlog += r->tiles_total;
+        if (backlog <= 2LL * max_tiles_) return max_tiles_;
+        return (int)std::min<long long>(max_tiles_backlog_, std::max<long long>(max_tiles_, backlog / 2));
+    }
+
     // (mutex held) pack the oldest admitted requests' next tiles into slot b's work list
     void build(int b)
     {
         ServeWork &w = *be_.work(b);
         int nt = 0, nr = 0;
-        while (!active_.empty() && nt < max_tiles_ && nr < kServeMaxReq) {
+        const int cap = iteration_cap();
+        while (!active_.empty() && nt < cap && nr < kServeMaxReq) {
             ServeRequest *r = active_.front();
             ServeReq &q = w.req[nr];
             q.scene = r->scene;
@@ -357,7 +375,7 @@ private:
             q.tiles_x = r->tiles_x;
             q.out_off = r->pool_off;
             memcpy(q.cam, r->cam, sizeof q.cam);
-            const int take = std::min(max_tiles_ - nt, r->tiles_total - r->tiles_next);
+            const int take = std::min(cap - nt, r->tiles_total - r->tiles_next);
             if (r->tiles_next == 0) r->t_launch = now_s();          // its first tiles: this iteration
             for (int t = 0; t < take; ++t) w.tiles[nt + t] = ((uint32_t)nr << 20) | (uint32_t)(r->tiles_next + t);
             nt += take;
@@ -447,7 +465,7 @@ private:
 
     ServeBackend &be_;
     ServeErrFn err_;
-    const int n_scenes_, max_tiles_;
+    const int n_scenes_, max_tiles_, max_tiles_backlog_;
     ServePool pool_;
 
     std::mutex mu_;

@@ -56,7 +56,8 @@ class Opts(ct.Structure):
 
 class ServerOpts(ct.Structure):
     _fields_ = [("pool_bytes", ct.c_size_t), ("max_tiles_per_iter", ct.c_int32), ("precision", ct.c_int32),
-                ("step", ct.c_float), ("t_term", ct.c_float), ("early_term", ct.c_int32), ("reserved", ct.c_int32)]
+                ("step", ct.c_float), ("t_term", ct.c_float), ("early_term", ct.c_int32),
+                ("max_tiles_backlog", ct.c_int32)]
 
 
 class ServerStats(ct.Structure):
@@ -425,11 +426,13 @@ class Server:
     admission, batching and launches; this class only marshals arguments)."""
 
     def __init__(self, scenes: Sequence[Scene], pool_bytes: int, step: float, max_tiles_per_iter: int = 16384,
-                 precision: int = PREC_FP16, t_term: float = 2e-4, early_term: bool = True):
+                 precision: int = PREC_FP16, t_term: float = 2e-4, early_term: bool = True,
+                 max_tiles_backlog: int = 0):
         self.scenes = list(scenes)
         arr = (ct.c_void_p * len(self.scenes))(*[sc.handle.value for sc in self.scenes])
         o = ServerOpts(pool_bytes=int(pool_bytes), max_tiles_per_iter=int(max_tiles_per_iter), precision=precision,
-                       step=step, t_term=t_term, early_term=int(early_term), reserved=0)
+                       step=step, t_term=t_term, early_term=int(early_term),
+                       max_tiles_backlog=int(max_tiles_backlog))
         h = ct.c_void_p()
         _check(lib().merf_server_create(ct.cast(arr, ct.c_void_p), len(self.scenes), ct.byref(o), ct.byref(h)))
         self.handle = h

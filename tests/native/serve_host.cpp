@@ -144,11 +144,12 @@ struct HostServer {
 extern "C" {
 
 void *host_server_create(int n_scenes, size_t pool_bytes, int max_tiles_per_iter, int workers, host_tile_fn fn,
-                         void *user)
+                         void *user, int max_tiles_backlog)
 {
     HostServer *h = new HostServer();
     h->be = new HostBackend(pool_bytes / sizeof(float), workers, fn, user);
-    h->sched = new merf::ServeScheduler(*h->be, n_scenes, pool_bytes / sizeof(float), max_tiles_per_iter, host_err);
+    h->sched = new merf::ServeScheduler(*h->be, n_scenes, pool_bytes / sizeof(float), max_tiles_per_iter, host_err,
+                                        max_tiles_backlog);
     h->sched->start();
     return h;
 }

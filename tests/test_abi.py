@@ -173,14 +173,15 @@ def test_render_rejects_bad_opts(kw):
 def test_server_create_and_submit_reject_bad_arguments():
     L = merf.lib()
     o = merf.ServerOpts(pool_bytes=1 << 20, max_tiles_per_iter=128, precision=1, step=1 / 64, t_term=2e-4,
-                        early_term=1, reserved=0)
+                        early_term=1, max_tiles_backlog=0)
     h = ct.c_void_p()
     assert L.merf_server_create(None, 1, ct.byref(o), ct.byref(h)) == merf.ERR_INVALID_ARG
     fake = (ct.c_void_p * 1)(1)
     assert L.merf_server_create(ct.cast(fake, ct.c_void_p), 0, ct.byref(o), ct.byref(h)) == merf.ERR_INVALID_ARG
     assert L.merf_server_create(ct.cast(fake, ct.c_void_p), 9, ct.byref(o), ct.byref(h)) == merf.ERR_INVALID_ARG
     for field, value in (("max_tiles_per_iter", 0), ("max_tiles_per_iter", 1 << 17), ("precision", 7),
-                         ("reserved", 1), ("pool_bytes", 16), ("step", 0.0)):
+                         ("max_tiles_backlog", 64), ("max_tiles_backlog", 1 << 17), ("pool_bytes", 16),
+                         ("step", 0.0)):
         bad = merf.ServerOpts.from_buffer_copy(o)
         setattr(bad, field, value)
         assert L.merf_server_create(ct.cast(fake, ct.c_void_p), 1, ct.byref(bad), ct.byref(h)) == merf.ERR_INVALID_ARG

@@ -181,3 +181,24 @@ def test_four_paper_scenes_mixed_resolutions_against_oracle(paper_scene):
         err = np.abs(rgb - closer)
         assert err.max() <= 2e-3, (k, W, H, err.max())
         assert 10 * math.log10(1.0 / max(float(np.mean(err ** 2)), 1e-30)) > 50.0
+
+
+def test_latency_phases_through_the_cuda_backend(scenes):
+    """merf_server_wait_timed on the CUDA backend: every phase non-negative, the four adding up to
+    the latency merf_server_wait reports, render time present for every request, and a request
+    that waits behind a one-image pool shows admission time; the images stay correct."""
+    W, H = 48, 40
+    cams = synth.sphere_cameras(4, W, H, radius=2.6, seed=61)
+    srv = merf.Server(scenes, pool_bytes=W * H * 3 * 4 + 255, step=1 / 64, max_tiles_per_iter=8)
+    outs = [_host(W, H) for _ in range(4)]
+    ids = [srv.submit(k % 2, cams[k], W, H, outs[k]) for k in range(4)]
+    times = [srv.wait_timed(rid) for rid in ids]
+    srv.close()
+    for k, t in enumerate(times):
+        parts = [t["admit_s"], t["queue_s"], t["render_s"], t["copy_s"]]
+        assert min(parts) >= 0.0 and t["render_s"] > 0.0
+        assert abs(sum(parts) - t["total_s"]) < 1e-9
+        ref = _reference(scenes[k % 2], cams[k], W, H, merf.PREC_FP16)
+        assert (outs[k] - ref).abs().max().item() <= parity.RGB_TOL
+    # the pool holds one image, so the later requests waited for the earlier ones to leave it
+    assert times[3]["admit_s"] >= times[0]["render_s"]

@@ -29,7 +29,7 @@ def hostlib(tmp_path_factory):
                     "-I", os.path.join(ROOT, "paper_2302_12249_b300", "csrc"), SRC, "-o", out], check=True)
     L = ct.CDLL(out)
     vp = ct.c_void_p
-    L.host_server_create.argtypes = [ct.c_int, ct.c_size_t, ct.c_int, ct.c_int, TILE_FN, vp]
+    L.host_server_create.argtypes = [ct.c_int, ct.c_size_t, ct.c_int, ct.c_int, TILE_FN, vp, ct.c_int]
     L.host_server_create.restype = vp
     L.host_server_submit.argtypes = [vp, ct.c_int, vp, ct.c_int, ct.c_int, vp, ct.POINTER(ct.c_uint64)]
     L.host_server_wait.argtypes = [vp, ct.c_uint64, ct.c_double, ct.POINTER(ct.c_double)]
@@ -56,12 +56,12 @@ class Server:
     """The scheduler over the host device; tiles are rendered by the oracle (FP64, stored as
     float32 exactly as the oracle's full-image result would be)."""
 
-    def __init__(self, L, oscenes, pool_bytes, max_tiles, workers=3, fail_scene=None):
+    def __init__(self, L, oscenes, pool_bytes, max_tiles, workers=3, fail_scene=None, max_tiles_backlog=0):
         self.L, self.oscenes, self.fail_scene = L, oscenes, fail_scene
         self.calls = []                       # (scene, cam[15], x0, y0) per tile
         self.lock = threading.Lock()
         self.fn = TILE_FN(self._tile)         # kept alive for the server's lifetime
-        self.h = L.host_server_create(len(oscenes), pool_bytes, max_tiles, workers, self.fn, None)
+        self.h = L.host_server_create(len(oscenes), pool_bytes, max_tiles, workers, self.fn, None, max_tiles_backlog)
         self.bufs = {}
 
     def _tile(self, user, scene, W, H, cam, x0, y0, image):
@@ -213,6 +213,31 @@ def test_latency_phases(hostlib, scenes):
         assert res[0][2]["admit_s"] < 0.1
     finally:
         srv.close()
+
+
+def test_iterations_grow_under_a_backlog(hostlib, scenes):
+    """With max_tiles_backlog, iterations carry more tiles while more than twice max_tiles_per_iter
+    tiles wait (and never more than max_tiles_backlog); without it they stay at the cap.  Images
+    are the oracle's either way."""
+    W, H = 64, 32                                   # 16 tiles per request
+    cams = _cams(8, seed=19)
+    counts = {}
+    for backlog in (0, 48):
+        srv = Server(hostlib, scenes, 1 << 22, max_tiles=8, max_tiles_backlog=backlog)
+        try:
+            srv.hold(True)
+            rids = [srv.submit(k % 2, cams[k], W, H)[1] for k in range(8)]
+            srv.until(lambda s: s.iterations >= 1)
+            srv.hold(False)
+            for k, rid in enumerate(rids):
+                assert srv.wait(rid) == merf.MERF_OK
+                np.testing.assert_array_equal(srv.bufs[rid], _expected(scenes[k % 2], cams[k], W, H))
+            counts[backlog] = srv.stats().iterations
+        finally:
+            srv.close()
+    assert counts[0] >= 16                          # 128 tiles, 8 per iteration
+    assert counts[48] < counts[0]
+    assert counts[48] >= 128 // 48
 
 
 def test_requests_share_iterations(hostlib, scenes):
