@@ -61,18 +61,9 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 // writes before the tensor cores read them, earlier reads before a bulk copy overwrites them.
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// D (TMEM) = A B (+ D if accumulate); one thread issues it for the CTA.
-__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
-                                         uint32_t accumulate)
-{
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-                 "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-                 : "memory");
-}
-
-// The same with A in tensor memory: row m of A in TMEM lane m, its 16-bit elements (k, k + 1) in
-// one 32-bit column, element k in the low half (a_tmem: the column of element 0).
+// D (TMEM) = A B (+ D if accumulate), with A in tensor memory (row m of A in TMEM lane m, its
+// 16-bit elements (k, k + 1) in one 32-bit column, element k in the low half; a_tmem: the column
+// of element 0) and B in shared memory (descriptor b_desc); one thread issues it for the CTA.
 __device__ __forceinline__ void umma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
                                             uint32_t accumulate)
 {

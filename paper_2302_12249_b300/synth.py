@@ -98,10 +98,19 @@ CONFIGS: Dict[str, SceneConfig] = {
                              inner_blobs=128, step=1.0 / 256, peak_opacity=3.0, grid_only=True),
     "snerg2048": SceneConfig("snerg2048", L=2048, B=16, R=0, occ_res=(128, 64, 32, 16), n_blobs=256,
                              inner_blobs=128, step=1.0 / 256, peak_opacity=3.0, grid_only=True),
+    # The paper-scale configuration with smaller blobs (radii U(0.01, 0.08)): about 9 % of 16^3
+    # blocks stored and about 200 MB of arrays, the sparsity and size of the paper's scenes
+    # (Sec. 6: 198-233 MB each), beside its grid-only counterpart at SNeRG++'s default L = 2048.
+    "paper_sparse": SceneConfig("paper_sparse", L=512, B=16, R=2048, occ_res=(128, 64, 32, 16), n_blobs=256,
+                                inner_blobs=128, step=1.0 / 256, peak_opacity=3.0, radius_range=(0.01, 0.08)),
+    "snerg2048_sparse": SceneConfig("snerg2048_sparse", L=2048, B=16, R=0, occ_res=(128, 64, 32, 16), n_blobs=256,
+                                    inner_blobs=128, step=1.0 / 256, peak_opacity=3.0, radius_range=(0.01, 0.08),
+                                    grid_only=True),
 }
 
 # the MERF configuration whose seeded draws a grid-only configuration shares
-GRID_ONLY_BASE = {"tiny_grid": 256, "tiny_grid128": 256, "snerg512": 2048, "snerg1024": 2048, "snerg2048": 2048}
+GRID_ONLY_BASE = {"tiny_grid": 256, "tiny_grid128": 256, "snerg512": 2048, "snerg1024": 2048, "snerg2048": 2048,
+                  "snerg2048_sparse": 2048}
 
 
 @dataclasses.dataclass
@@ -404,6 +413,6 @@ def config_cameras(name: str, W: Optional[int] = None, H: Optional[int] = None, 
         return sphere_cameras(n or 1, W or 64, H or 64, radius=3.0)
     if name == "dense128":
         return sphere_cameras(n or 4, W or 512, H or 512, radius=3.0)
-    if name == "paper":
+    if name in ("paper", "paper_sparse"):
         return ring_cameras(n or 8, W or 1920, H or 1080, radius=1.5)
     raise KeyError(name)

@@ -313,3 +313,19 @@ def test_maximum_sizes(tiny, n, W, H):
     torch.cuda.empty_cache()
     lo, hi = parity.oracle_rgb(osc, cams, W, H, 1 / 64, pix=pix)
     assert parity.max_err(rgb, lo, hi).max() <= parity.RGB_TOL
+
+
+def test_paper_sparsity_scene_sampled_pixels():
+    """The paper-scale geometry at the paper's sparsity (blob radii U(0.01, 0.08): about 9 % of
+    blocks stored, ~200 MB): sampled pixels of the bench cameras against the oracle."""
+    sc = synth.make_scene("paper_sparse")
+    assert 0.05 < sc.stats["block_fraction"] < 0.12
+    gs, osc = merf.Scene(sc), oracle.OracleScene(sc)
+    cams = synth.config_cameras("paper_sparse")
+    W, H, step = 1920, 1080, 1 / 256
+    rgb, aux = parity.gpu_render(gs, cams, W, H, step)
+    pix, lin = parity.pick_pixels(cams.shape[0], W, H, 1500, seed=12)
+    lo, hi = parity.oracle_rgb(osc, cams, W, H, step, pix=pix)
+    err = parity.max_err(rgb[lin], lo, hi)
+    assert err.max() <= parity.RGB_TOL, (err.max(), np.argmax(err))
+    assert aux[lin, merf.AUX_NEVAL].mean() > 1.0          # the rays do meet the blobs
