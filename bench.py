@@ -44,15 +44,15 @@ B_DENSITY, B_INDEX, B_APPEAR, B_OUT = 20, 4, 140, 12
 # launch from an ncu capture of this workload; reported as roofline.traffic only while the
 # render kernel's sources (device code, launch and scene layout) hash to the value they were
 # measured with (otherwise null).
-TRAFFIC_BYTES_PER_LAUNCH = (380.00 + 256.48) * 1e6
+TRAFFIC_BYTES_PER_LAUNCH = (380.44 + 256.16) * 1e6
 TRAFFIC_SOURCES = ("debug.cuh", "field.cuh", "geometry.h", "merf_api.cu", "render.cuh", "scene.h", "traverse.cuh",
                    "umma.cuh")
 # Warp-level instructions (smsp__inst_executed.sum) of the same timed launch from an ncu capture
 # (1 pass, full size), for the issue-rate roofline: the kernel is bound by instruction issue, and
 # an SM's four schedulers issue at most one warp instruction per clock each.
-INST_PER_LAUNCH = 38.167982624e9
+INST_PER_LAUNCH = 38.167976089e9
 SMS, SCHEDULERS_PER_SM = 148, 4
-TRAFFIC_SOURCES_SHA256 = "f01134d7a2f09b4df10447682d47517221b259e73905e35a6ff8278d230313f4"
+TRAFFIC_SOURCES_SHA256 = "2ce078b7ac2429fefeaa322701966d55c69bd99be0edfbf30ba8eb7ca605a7fd"
 
 
 def _sources_sha256() -> str:

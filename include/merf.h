@@ -93,11 +93,13 @@ typedef struct merf_render_opts {
     float step;          /* lattice step delta_s in contracted arc length, > 0 */
     float t_term;        /* early-termination threshold on transmittance (Sec. 5: 2e-4) */
     int32_t precision;   /* MERF_PREC_FP32: every step in FP32.  MERF_PREC_FP16 / _BF16 (uint8
-                            storage only): appearance interpolation corrections in 16-bit pairs,
-                            appearance sigmoids through tanh.approx, and the deferred MLP on the
-                            tcgen05 tensor cores (16-bit operands, FP32 accumulation); density,
-                            opacity, transmittance, compositing and traversal stay FP32, so the
-                            evaluated samples are the FP32 form's */
+                            storage only): appearance interpolated with 15-bit fixed-point
+                            weights, appearance sigmoids through tanh.approx, and the deferred MLP
+                            on the tcgen05 tensor cores (16-bit operands, FP32 accumulation);
+                            density is the FP32 form's exact integer sum (converted to float in a
+                            different order: a few ulps), and opacity, transmittance, compositing
+                            and traversal stay FP32, so the evaluated samples are the FP32
+                            form's */
     int32_t early_term;  /* 1: stop a ray after the sample at which T < t_term */
     int32_t contraction; /* 0: contract_pi (Sec. 3.2) with its segment lattice and empty-space
                             skipping.  1: the ablation of Sec. 3.2 / Table 2 (c), mip-NeRF 360's

@@ -228,22 +228,29 @@ grid_done:;
 // a multiply-add per two bytes.
 //
 // Weights.  One fused multiply-add forms each weight's last product and rounds it to the integer
-// round(w S) in the low mantissa bits of 2^23 + w S (S <= 2^22, so the exponent stays that of
-// 2^23 and bit 23 stays zero).
-// * Two-level (the FP32 form, and density in every form): S = 2^22, the weight split into its low
-//   16 bits and its bits 16..22 (<= 64), two dot products per byte pair, and
-//   K_c = (H_c 2^16 + L_c) / 2^22.  The weight's rounding (2^-23) bounds the error of K_c by
-//   20 * 255 * 2^-23 < 6.1e-4 byte units, the same as float accumulation of the sum to 1020
-//   (half an ulp of 1020 per step); L_c < 20 * 65535 * 255 < 2^32 cannot overflow.
-// * One-level (appearance channels 1..7 of the 16-bit forms): S = 65535, one dot product,
-//   K_c = L_c / 65535, error at most 20 * 255 / 131070 < 0.039 byte units (typically 1e-3),
-//   within the 16-bit forms' tolerance and more accurate than half-precision weights (2^-11).
+// W = round(w S), S = 256 * 32767 = 2^23 - 256, in the low mantissa bits of M + w S (M = 2^23, or
+// 2^23 + 128 below; the sum stays below 2^24, so the exponent byte is that of 2^23 and bit 23 is
+// zero).  Byte permutes then cut the word at byte boundaries, two taps at a time: bits 8..22 form
+// the high level (at most 32767) and bits 0..7 the low level, zero-extended.
+// * FP32 form, every channel: M = 2^23, so the levels are H = floor(W / 256) and L = W mod 256,
+//   and K_c = (256 H_c + L_c) / S exactly, with H_c, L_c the two levels' dot products.  The
+//   weight's rounding (2^-24 relative to a unit weight) bounds the error of K_c by
+//   20 * 255 / (2 S) < 3.1e-4 byte units, below float accumulation of the sum (half an ulp of
+//   1020 per step); H_c < 20 * 32767 * 255 < 2^28.
+// * 16-bit forms: M = 2^23 + 128, so the high level is H' = floor((W + 128) / 256), W / 256
+//   rounded, and the low level L' = (W + 128) mod 256.  Appearance channels take the high level
+//   alone, K_c = H'_c / 32767, error at most 20 * 255 * 0.502 / 32767 < 0.079 byte units
+//   (typically 3e-3), within the 16-bit forms' tolerance.  Density takes both levels and the
+//   tap pair's plain byte sum N_0 (one more dot product, with unit weights):
+//   W + 128 = 256 H' + L', so sum_i W_i b_i0 = 256 H'_0 + L'_0 - 128 N_0, the FP32 form's integer.
+// Either way density rests on the same exact integer X = sum_i W_i b_i0; the forms differ only in
+// how its two parts are converted and combined in float (a few ulps of the pre-activation).
 // A grid corner that is not stored holds zero bytes, so it adds nothing whatever its weight.
 
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel)
 {
     // PTX prmt, default mode: a selector nibble with its high bit set replicates the selected
-    // byte's sign bit (here always zero) over the output byte
+    // byte's sign bit over the output byte (used here on bytes whose top bit is zero, for zeros)
     uint32_t d;
     asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
     return d;
@@ -263,53 +270,55 @@ __device__ __forceinline__ uint32_t dp2a_hi(uint32_t a, uint32_t b, uint32_t c)
     return d;
 }
 
-constexpr float kW22 = 4194304.0f;            // two-level weight scale 2^22
-constexpr float kW16 = 65535.0f;              // one-level weight scale
-constexpr float kWMagic = 8388608.0f;         // 2^23
+constexpr float kWScale = 8388352.0f;         // S = 256 * 32767
+constexpr float kWMagic = 8388608.0f;         // 2^23: H = floor(W / 256), L = W mod 256
+constexpr float kWMagicRound = 8388736.0f;    // 2^23 + 128: H' = W / 256 rounded
+constexpr uint32_t kSelHigh = 0x6521u;        // bytes 1, 2 of both words: bits 8..23
+constexpr uint32_t kSelLow = 0xF4B0u;         // byte 0 of both words, zero-extended by the sign of byte 3
 
-// 2^23 + round(a b): a weight's last product, rounded to an integer in the low mantissa bits.
-__device__ __forceinline__ uint32_t weight_word(float a, float b)
+// M + round(a b): a weight's last product, rounded to an integer in the low mantissa bits.
+__device__ __forceinline__ uint32_t weight_word(float a, float b, float M = kWMagic)
 {
-    return __float_as_uint(fmaf(a, b, kWMagic));
+    return __float_as_uint(fmaf(a, b, M));
 }
 
 // The weights of tap pair p (taps 2p and 2p + 1, neighbours along x for the grid and along the
-// column axis for a plane): (g, f) times the pair's shared factor v, where g = 1 - f.  Grid pair p:
-// f = f_x, v = the y and z weights of rows (p & 1, p >> 1); plane pair p = 4 + 2q + r: plane q's
-// column fraction and the weight of its row r.  The same weights as grid_w (each rounding in the
-// same order up to the product's association).
+// column axis for a plane), scaled by S: (g, f) times the pair's shared factor v S, where
+// g = 1 - f.  Grid pair p: f = f_x, v = the y and z weights of rows (p & 1, p >> 1), formed as
+// w_y (w_z S) so that the two z factors serve all four pairs; plane pair p = 4 + 2q + r: plane
+// q's column fraction and the weight of its row r.  The same weights as grid_w up to the
+// products' association.
 template <int p>
-__device__ __forceinline__ void pair_factors(const Taps &t, float &f, float &v)
+__device__ __forceinline__ void pair_factors(const Taps &t, float &f, float &vs)
 {
     if constexpr (p < 4) {
         f = t.fx;
-        v = ((p & 1) ? t.fy : 1.0f - t.fy) * ((p >> 1) ? t.fz : 1.0f - t.fz);
+        vs = ((p & 1) ? t.fy : 1.0f - t.fy) * ((p >> 1) ? t.fz * kWScale : (1.0f - t.fz) * kWScale);
     } else {
         constexpr int q = (p - 4) >> 1, r = (p - 4) & 1;
         constexpr int ca = q == 0 ? 1 : 0, ra = q == 2 ? 1 : 2;     // column axis (1, 0, 0)[q], row axis (2, 2, 1)[q]
         f = t.fu[ca];
-        v = r ? t.fu[ra] : 1.0f - t.fu[ra];
+        vs = (r ? t.fu[ra] : 1.0f - t.fu[ra]) * kWScale;
     }
 }
 
-// Weight words of tap pair p at scale S (2^23 + round(w S) each).
+// Weight words of tap pair p (M + round(w S) each).
 template <int p>
-__device__ __forceinline__ void pair_weight_words(const Taps &t, float S, uint32_t &w0, uint32_t &w1)
+__device__ __forceinline__ void pair_weight_words(const Taps &t, float M, uint32_t &w0, uint32_t &w1)
 {
-    float f, v;
-    pair_factors<p>(t, f, v);
-    const float vs = v * S;
-    w0 = weight_word(1.0f - f, vs);
-    w1 = weight_word(f, vs);
+    float f, vs;
+    pair_factors<p>(t, f, vs);
+    w0 = weight_word(1.0f - f, vs, M);
+    w1 = weight_word(f, vs, M);
 }
 
-// Weight words of the first nt taps at scale S, all at once (the FP32 form's arrangement, which
-// measured faster there than forming them pair by pair; the 16-bit forms, with a second set of
-// words, do better pair by pair): grid corners trilinear, plane q bilinear in its column axis
-// (1, 0, 0)[q] and row axis (2, 2, 1)[q].
+// Weight words (2^23 + round(w S)) of the first nt taps, all at once (the FP32 form's
+// arrangement, which measured faster there than forming them pair by pair): grid corners
+// trilinear, plane q bilinear in its column axis (1, 0, 0)[q] and row axis (2, 2, 1)[q].
 template <int nt>
-__device__ __forceinline__ void weight_words(const Taps &t, float S, uint32_t w[nt])
+__device__ __forceinline__ void weight_words(const Taps &t, uint32_t w[nt])
 {
+    constexpr float S = kWScale;
     const float gx = 1.0f - t.fx, gy = 1.0f - t.fy;
     const float xy[4] = {gx * gy, t.fx * gy, gx * t.fy, t.fx * t.fy};
     const float z1 = t.fz * S, z0 = (1.0f - t.fz) * S;
@@ -341,50 +350,43 @@ __device__ __forceinline__ void pair_bytes(uint2 a, uint2 b, uint32_t B[4])
 }
 
 // Integer weighted byte sums of one sample over the first nt taps.  kPrec 0 (FP32): every
-// channel two-level, K_c = (hi[c] 2^16 + lo[c]) / 2^22.  kPrec 1, 2 (the 16-bit forms): density
-// two-level as in FP32 (so density, opacity and transmittance equal the FP32 form's bit for bit),
-// channels 1..7 one-level, K_c = lo[c] / 65535 (hi[1..7] unused).
+// channel at two levels, K_c = (256 hi[c] + lo[c]) / S.  kPrec 1, 2 (the 16-bit forms): the
+// rounded high level of every channel, hi[c] (K_c = hi[c] / 32767 for appearance), and for
+// density also its low level lo[0] and byte sum n0.
 template <int kPrec>
 struct DotSums {
-    uint32_t lo[8], hi[kPrec == 0 ? 8 : 1];
+    uint32_t hi[8], lo[kPrec == 0 ? 8 : 1];
+    uint32_t n0;                                 // 16-bit forms only
 };
 
-// One tap pair's contribution.  FP32: the weight words w22 come in; 16-bit forms: the pair's words
-// (both scales) are formed here, just before use, so that only one pair's are live at a time.
+// One tap pair's contribution.  FP32: the weight words come in; 16-bit forms: the pair's words
+// are formed here, just before use, so that only one pair's are live at a time.
 template <int kPrec, int p>
-__device__ __forceinline__ void dot_pair(const Taps &t, DotSums<kPrec> &s, const uint32_t *w22)
+__device__ __forceinline__ void dot_pair(const Taps &t, DotSums<kPrec> &s, const uint32_t *w)
 {
     uint32_t m0, m1;
     if constexpr (kPrec == 0) {
-        m0 = w22[2 * p];
-        m1 = w22[2 * p + 1];
+        m0 = w[2 * p];
+        m1 = w[2 * p + 1];
     } else {
-        pair_weight_words<p>(t, kW22, m0, m1);
+        pair_weight_words<p>(t, kWMagicRound, m0, m1);
     }
-    const uint32_t wl = prmt(m0, m1, 0x5410u);     // low 16 bits of both
-    const uint32_t wh = prmt(m0, m1, 0xE6A2u);     // bits 16..22, zero-extended
+    const uint32_t wh = prmt(m0, m1, kSelHigh);
+    const uint32_t wl = prmt(m0, m1, kSelLow);
     uint32_t B[4];
     pair_bytes(t.v[2 * p], t.v[2 * p + 1], B);
-    if constexpr (kPrec == 0) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 4; ++q) {
+        s.hi[2 * q] = dp2a_lo(wh, B[q], s.hi[2 * q]);
+        s.hi[2 * q + 1] = dp2a_hi(wh, B[q], s.hi[2 * q + 1]);
+        if constexpr (kPrec == 0) {
             s.lo[2 * q] = dp2a_lo(wl, B[q], s.lo[2 * q]);
             s.lo[2 * q + 1] = dp2a_hi(wl, B[q], s.lo[2 * q + 1]);
-            s.hi[2 * q] = dp2a_lo(wh, B[q], s.hi[2 * q]);
-            s.hi[2 * q + 1] = dp2a_hi(wh, B[q], s.hi[2 * q + 1]);
         }
-    } else {
-        uint32_t n0, n1;
-        pair_weight_words<p>(t, kW16, n0, n1);
-        const uint32_t ws = prmt(n0, n1, 0x5410u);
+    }
+    if constexpr (kPrec != 0) {
         s.lo[0] = dp2a_lo(wl, B[0], s.lo[0]);
-        s.hi[0] = dp2a_lo(wh, B[0], s.hi[0]);
-        s.lo[1] = dp2a_hi(ws, B[0], s.lo[1]);
-#pragma unroll
-        for (int q = 1; q < 4; ++q) {
-            s.lo[2 * q] = dp2a_lo(ws, B[q], s.lo[2 * q]);
-            s.lo[2 * q + 1] = dp2a_hi(ws, B[q], s.lo[2 * q + 1]);
-        }
+        s.n0 = dp2a_lo(0x00010001u, B[0], s.n0);
     }
 }
 
@@ -392,11 +394,12 @@ template <int kPrec, int nt>
 __device__ __forceinline__ void dot_sums(const Taps &t, DotSums<kPrec> &s)
 {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) s.lo[c] = 0u;
+    for (int c = 0; c < 8; ++c) s.hi[c] = 0u;
 #pragma unroll
-    for (int c = 0; c < (kPrec == 0 ? 8 : 1); ++c) s.hi[c] = 0u;
+    for (int c = 0; c < (kPrec == 0 ? 8 : 1); ++c) s.lo[c] = 0u;
+    s.n0 = 0u;
     uint32_t w[kPrec == 0 ? nt : 1];
-    if constexpr (kPrec == 0) weight_words<nt>(t, kW22, w);
+    if constexpr (kPrec == 0) weight_words<nt>(t, w);
     dot_pair<kPrec, 0>(t, s, w);
     dot_pair<kPrec, 1>(t, s, w);
     dot_pair<kPrec, 2>(t, s, w);
@@ -411,16 +414,22 @@ __device__ __forceinline__ void dot_sums(const Taps &t, DotSums<kPrec> &s)
     }
 }
 
-// Density pre-activation from its two-level sums: (28 / 255) K_0 - 14 W, where W = W_V + 3 is
-// the total interpolation weight of the sources (the planes' weights sum to one each; W = W_V for
-// a grid-only scene).  Every path that evaluates a uint8 scene's density calls this one
-// expression, so their opacities agree bit for bit.
+// Density pre-activation: (28 / 255) K_0 - 14 W, where W = W_V + 3 is the total interpolation
+// weight of the sources (the planes' weights sum to one each; W = W_V for a grid-only scene), and
+// K_0 = X / S with X = sum_i W_i b_i0 = 256 H_0 + L_0 (FP32) = 128 (2 H'_0 - N_0) + L'_0 (16-bit
+// forms).  The low parts convert exactly (< 2^21); the high parts round only above 2^24.  Every
+// path of one form that evaluates a uint8 scene's density calls this one expression, so their
+// opacities agree bit for bit.
 template <int kPrec>
 __device__ __forceinline__ float dequant_density(const DotSums<kPrec> &k, float wsum)
 {
     constexpr float A = 28.0f / 255.0f;
-    return fmaf(__uint2float_rn(k.lo[0]), A * (1.0f / kW22),
-                fmaf(__uint2float_rn(k.hi[0]), A * (65536.0f / kW22), -14.0f * wsum));
+    if constexpr (kPrec == 0)
+        return fmaf(__uint2float_rn(k.lo[0]), A * (1.0f / kWScale),
+                    fmaf(__uint2float_rn(k.hi[0]), A * (256.0f / kWScale), -14.0f * wsum));
+    else
+        return fmaf(__uint2float_rn(k.lo[0]), A * (1.0f / kWScale),
+                    fmaf(__int2float_rn((int)(2u * k.hi[0]) - (int)k.n0), A * (128.0f / kWScale), -14.0f * wsum));
 }
 
 // Dense float storage: all eight channels of all 20 taps, summed.

@@ -84,8 +84,8 @@ __device__ __forceinline__ AppArg app_arg(const float app[7])
 }
 
 // From the two-level integer sums of the FP32 uint8 path: x = (14 / 255) K - 7 W (W the sources'
-// total weight, as in dequant_density) with K = (H 2^16 + L) / 2^22, so
-// y = -x log2(e) = L A / 2^22 + (H A / 2^6 + 7 log2(e) W), A = -14 log2(e) / 255: two fused
+// total weight, as in dequant_density) with K = (256 H + L) / S, so
+// y = -x log2(e) = L A / S + (H 256 A / S + 7 log2(e) W), A = -14 log2(e) / 255: two fused
 // multiply-adds per channel, in pairs.
 __device__ __forceinline__ float2 u2f2(uint32_t a, uint32_t b)
 {
@@ -95,7 +95,7 @@ __device__ __forceinline__ float2 u2f2(uint32_t a, uint32_t b)
 __device__ __forceinline__ AppArg app_arg_u8(const DotSums<0> &k, float wsum)
 {
     const float A = -kLog2e * 14.0f / 255.0f, b = (7.0f * kLog2e) * wsum;
-    const float Al = A * (1.0f / kW22), Ah = A * (65536.0f / kW22);
+    const float Al = A * (1.0f / kWScale), Ah = A * (256.0f / kWScale);
     const float2 Al2 = make_float2(Al, Al), Ah2 = make_float2(Ah, Ah), b2 = make_float2(b, b);
     AppArg a;
     a.y1 = fmaf(__uint2float_rn(k.lo[1]), Al, fmaf(__uint2float_rn(k.hi[1]), Ah, b));
@@ -135,19 +135,19 @@ __device__ __forceinline__ float tanh_approx(float x)
 }
 
 // 16-bit forms: sigmoid(x) = (1 + tanh(x / 2)) / 2, so AppArg holds t = x / 2 =
-// (7 / 255) K - 3.5 W with the one-level sums K = L / 65535, and compositing accumulates only
-// (w / 2) tanh(t); the constant halves sum to (1 - T) / 2 per ray (the weights alpha_i T_i sum
-// to 1 - T), added once at the end.
+// (7 / 255) K - 3.5 W with the rounded high-level sums K = H' / 32767, and compositing
+// accumulates only (w / 2) tanh(t); the constant halves sum to (1 - T) / 2 per ray (the weights
+// alpha_i T_i sum to 1 - T), added once at the end.
 template <int kPrec>
 __device__ __forceinline__ AppArg app_arg_u8_half(const DotSums<kPrec> &k, float wsum)
 {
-    const float A = 7.0f / 255.0f / kW16, b = -3.5f * wsum;
+    const float A = 7.0f / 255.0f * (256.0f / kWScale), b = -3.5f * wsum;
     const float2 A2 = make_float2(A, A), b2 = make_float2(b, b);
     AppArg a;
-    a.y1 = fmaf(__uint2float_rn(k.lo[1]), A, b);
-    a.y23 = __ffma2_rn(u2f2(k.lo[2], k.lo[3]), A2, b2);
-    a.y45 = __ffma2_rn(u2f2(k.lo[4], k.lo[5]), A2, b2);
-    a.y67 = __ffma2_rn(u2f2(k.lo[6], k.lo[7]), A2, b2);
+    a.y1 = fmaf(__uint2float_rn(k.hi[1]), A, b);
+    a.y23 = __ffma2_rn(u2f2(k.hi[2], k.hi[3]), A2, b2);
+    a.y45 = __ffma2_rn(u2f2(k.hi[4], k.hi[5]), A2, b2);
+    a.y67 = __ffma2_rn(u2f2(k.hi[6], k.hi[7]), A2, b2);
     return a;
 }
 
@@ -559,7 +559,7 @@ __device__ __forceinline__ void eval_field(const FieldView &fv, float p0, float 
         Taps tp;
         gather_u8<kGeo>(fv, p0, p1, p2, tp);
         DotSums<kPrec> k;
-        dot_sums<kPrec, kTaps<kGeo>>(tp, k);      // 16-bit forms: one-level appearance weights
+        dot_sums<kPrec, kTaps<kGeo>>(tp, k);      // 16-bit forms: appearance at one level
         const float wsum = tp.wv + (float)kPlaneSources<kGeo>;
         dens = dequant_density<kPrec>(k, wsum);
         if constexpr (kPrec == 0) ya = app_arg_u8(k, wsum);

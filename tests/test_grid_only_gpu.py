@@ -62,7 +62,7 @@ def test_grid_only_paper_scale_sampled_pixels():
 
 # Both 16-bit forms meet the precision form's 2e-3 per channel here, although folding the
 # planes' short wavelengths into a 64^3 grid leaves neighbouring voxels up to ~100 byte steps
-# apart: their appearance sums are exact integers with 16-bit weights (a bfloat16 accumulator,
+# apart: their appearance sums are exact integers with 15-bit weights (a bfloat16 accumulator,
 # used before, reached 2.6e-3 on this scene).
 @pytest.mark.parametrize("prec,tol", [(merf.PREC_FP16, 2e-3), (merf.PREC_BF16, 2e-3)])
 def test_grid_only_reduced_precision(tiny_grid, prec, tol):
@@ -83,7 +83,9 @@ def test_grid_only_reduced_precision(tiny_grid, prec, tol):
     assert 10 * math.log10(1.0 / max(float(np.mean((rgb - closest) ** 2)), 1e-30)) > 50.0
     a32, alp = a32.reshape(-1, merf.AUX_SIZE).cpu().numpy(), alp.reshape(-1, merf.AUX_SIZE).cpu().numpy()
     np.testing.assert_array_equal(alp[:, merf.AUX_NEVAL], a32[:, merf.AUX_NEVAL])
-    np.testing.assert_allclose(alp[:, merf.AUX_T], a32[:, merf.AUX_T], rtol=0, atol=1e-6)
+    # density: the same exact integer sum in both forms, converted in a different order (the
+    # bound of test_precision_gpu.test_density_and_traversal_unchanged)
+    np.testing.assert_allclose(alp[:, merf.AUX_T], a32[:, merf.AUX_T], rtol=1.5e-4, atol=1e-6)
 
 
 def test_server_refuses_grid_only_scenes(tiny_grid):

@@ -98,14 +98,20 @@ def test_64_camera_launch_sampled(paper, prec):
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_density_and_traversal_unchanged(tiny, prec):
-    """Only appearance and the MLP change precision: evaluated samples, opacity and hence
-    transmittance are those of the FP32 path."""
+    """Only appearance and the MLP change precision: the evaluated samples are those of the FP32
+    path, and opacity and hence transmittance agree with it to float rounding.  Density comes from
+    the same exact integer sum, converted to float in a different order: a few ulps of a
+    pre-activation |x| <= 56 (ulp <= 2^-18), so sigma = exp(x) differs by at most ~1.5e-5
+    relative, and ln T = -sum sigma_i delta_i by that fraction of -ln T (<= 8.6 above the 2e-4
+    threshold): |dT| <= 1.5e-4 T, measured 1.9e-6 T at most.  Past the threshold (the final T of
+    a terminated ray, down to 1e-8) the last factor 1 - alpha loses relative accuracy but little
+    in absolute terms: 1e-6 covers it."""
     gs, _ = tiny
     cams = synth.config_cameras("tiny", W=48, H=40)
     _, a32 = _render(gs, cams, 48, 40, 1 / 64, merf.PREC_FP32)
     _, alp = _render(gs, cams, 48, 40, 1 / 64, prec)
     np.testing.assert_array_equal(alp[:, merf.AUX_NEVAL], a32[:, merf.AUX_NEVAL])
-    np.testing.assert_allclose(alp[:, merf.AUX_T], a32[:, merf.AUX_T], rtol=0, atol=1e-6)
+    np.testing.assert_allclose(alp[:, merf.AUX_T], a32[:, merf.AUX_T], rtol=1.5e-4, atol=1e-6)
 
 
 @pytest.mark.parametrize("prec,tol", [pytest.param(merf.PREC_FP16, 1e-3, id="fp16"),
