@@ -44,15 +44,15 @@ B_DENSITY, B_INDEX, B_APPEAR, B_OUT = 20, 4, 140, 12
 # launch from an ncu capture of this workload; reported as roofline.traffic only while the
 # render kernel's sources (device code, launch and scene layout) hash to the value they were
 # measured with (otherwise null).
-TRAFFIC_BYTES_PER_LAUNCH = (380.44 + 256.16) * 1e6
+TRAFFIC_BYTES_PER_LAUNCH = (727.44 + 295.96) * 1e6
 TRAFFIC_SOURCES = ("debug.cuh", "field.cuh", "geometry.h", "merf_api.cu", "render.cuh", "scene.h", "traverse.cuh",
                    "umma.cuh")
 # Warp-level instructions (smsp__inst_executed.sum) of the same timed launch from an ncu capture
 # (1 pass, full size), for the issue-rate roofline: the kernel is bound by instruction issue, and
 # an SM's four schedulers issue at most one warp instruction per clock each.
-INST_PER_LAUNCH = 38.167976089e9
+INST_PER_LAUNCH = 34.947777282e9
 SMS, SCHEDULERS_PER_SM = 148, 4
-TRAFFIC_SOURCES_SHA256 = "2ce078b7ac2429fefeaa322701966d55c69bd99be0edfbf30ba8eb7ca605a7fd"
+TRAFFIC_SOURCES_SHA256 = "4cfdaa75152e2a6bddb8d0fdfd9e4c01d67ea0ddfa3b87d318ae6c2ab5ea66bb"
 
 
 def _sources_sha256() -> str:
@@ -296,9 +296,10 @@ def _differentiation(steps: int = 5):
 def _grid_only_variant(merf_ref, names=("snerg512", "snerg1024", "snerg2048"), steps=5, warmup=3):
     """The SNeRG++-style baseline the paper compares MERF with (Sec. 6): the same contents baked
     as a grid-only scene (no planes) at L = 512, 1024 and 2048 (the paper's SNeRG++ default),
-    rendered by the same kernel from the same 8 cameras at 1920x1080 in FP32.  L = 2048 holds
-    about 33 GB of stored blocks: they are generated on the GPU and uploaded from device memory
-    (merf_scene_upload_device).  Per configuration: device memory, time, Mrays/s and the
+    rendered by the same kernel from the same 8 cameras at 1920x1080 in FP32.  L = 2048 bakes
+    about 28 GB of stored blocks: they are generated on the GPU and uploaded from device memory
+    (merf_scene_upload_device).  Per configuration: device memory (the library's layout: texel
+    pairs, about twice the baked arrays) and the baked arrays' size, time, Mrays/s and the
     algorithmic gather bytes (per evaluated sample 8 density bytes + the 4-byte index entry, per
     sample with non-zero opacity 56 appearance bytes, per ray 12 output bytes)."""
     import torch
@@ -309,6 +310,7 @@ def _grid_only_variant(merf_ref, names=("snerg512", "snerg1024", "snerg2048"), s
     for name in names:
         t_build = time.perf_counter()
         sc = synth.make_scene(name, device="cuda" if synth.CONFIGS[name].L >= 2048 else "cpu")
+        baked = sc.baked_bytes()
         gs = merf.Scene(sc)
         if torch.is_tensor(sc.atlas):
             sc.atlas = None                  # the library holds its own padded copy
@@ -332,8 +334,8 @@ def _grid_only_variant(merf_ref, names=("snerg512", "snerg1024", "snerg2048"), s
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / steps
         alg = c[merf.CNT_EVAL] * (8 + B_INDEX) + c[merf.CNT_APPEAR] * 56 + c[merf.CNT_RAYS] * B_OUT
-        res[name] = {"L": sc.cfg.L, "device_mb": round(gs.device_bytes / 1e6, 1), "ms_per_step": ms,
-                     "build_s": round(t_build, 1),
+        res[name] = {"L": sc.cfg.L, "device_mb": round(gs.device_bytes / 1e6, 1), "baked_mb": round(baked / 1e6, 1),
+                     "ms_per_step": ms, "build_s": round(t_build, 1),
                      "mrays_per_s": n * W_IMG * H_IMG / (ms / 1e3) / 1e6,
                      "evaluated_per_ray": c[merf.CNT_EVAL] / c[merf.CNT_RAYS],
                      "gather_bytes_per_sample": 8 + B_INDEX + 56,
@@ -349,7 +351,7 @@ def _sparse_scene(steps=5, warmup=3):
     """The paper-scale configuration at the sparsity and size of the paper's scenes: the same 256
     blobs with radii U(0.01, 0.08), about 9 % of 16^3 blocks stored (the configured scene stores
     48 %), and its grid-only (SNeRG++-style) counterpart at L = 2048, the same 8 cameras at
-    1920x1080 in FP32: device memory, time, Mrays/s and evaluated samples per ray."""
+    1920x1080 in FP32: device memory and baked size, time, Mrays/s and evaluated samples per ray."""
     import torch
     from paper_2302_12249_b300 import merf, synth
     cams = synth.config_cameras("paper")
@@ -358,6 +360,7 @@ def _sparse_scene(steps=5, warmup=3):
     for name in ("paper_sparse", "snerg2048_sparse"):
         cfg = synth.CONFIGS[name]
         sc = synth.make_scene(name, device="cuda" if cfg.grid_only else "cpu")
+        baked = sc.baked_bytes()
         gs = merf.Scene(sc)
         if torch.is_tensor(sc.atlas):
             sc.atlas = None
@@ -377,12 +380,13 @@ def _sparse_scene(steps=5, warmup=3):
         ms = a.elapsed_time(b) / steps
         c = [int(v) for v in cnt.cpu().tolist()]
         res[name] = {"L": cfg.L, "R": cfg.R, "block_fraction": round(sc.stats["block_fraction"], 4),
-                     "device_mb": round(gs.device_bytes / 1e6, 1), "ms_per_step": ms,
-                     "mrays_per_s": n * W_IMG * H_IMG / (ms / 1e3) / 1e6,
+                     "device_mb": round(gs.device_bytes / 1e6, 1), "baked_mb": round(baked / 1e6, 1),
+                     "ms_per_step": ms, "mrays_per_s": n * W_IMG * H_IMG / (ms / 1e3) / 1e6,
                      "evaluated_per_ray": c[merf.CNT_EVAL] / c[merf.CNT_RAYS]}
         gs.close()
         del sc, out
     res["memory_ratio_grid_only_to_merf"] = res["snerg2048_sparse"]["device_mb"] / res["paper_sparse"]["device_mb"]
+    res["baked_ratio_grid_only_to_merf"] = res["snerg2048_sparse"]["baked_mb"] / res["paper_sparse"]["baked_mb"]
     res["workload"] = ("paper-scale scene with blob radii U(0.01, 0.08) (256 blobs, half in the unit cube), MERF "
                        "L=512 + three 2048^2 planes and grid-only L=2048, the 8 ring cameras at 1920x1080, FP32")
     return res
@@ -674,7 +678,8 @@ def run_ours(args):
         serving = _serving(gs, args.serve_requests)
     variants = ablation = sparse = None
     if rank == 0 and world == 1 and not args.no_variants:
-        merf_ref = {"L": 512, "R": 2048, "device_mb": round(gs.device_bytes / 1e6, 1), "ms_per_step": ms_per_step,
+        merf_ref = {"L": 512, "R": 2048, "device_mb": round(gs.device_bytes / 1e6, 1),
+                    "baked_mb": round(scene.baked_bytes() / 1e6, 1), "ms_per_step": ms_per_step,
                     "mrays_per_s": value, "evaluated_per_ray": c[merf.CNT_EVAL] / c[merf.CNT_RAYS],
                     "gather_bytes_per_sample": B_DENSITY + B_INDEX + B_APPEAR,
                     "algorithmic_gb_per_s": achieved}
@@ -690,6 +695,7 @@ def run_ours(args):
                 "config": {"workload": WORKLOAD.replace("FP32 path", f"{args.precision.upper()} path"),
                            "rays_per_step_per_gpu": rays_per_step,
                            "scene_device_mb": round(gs.device_bytes / 1e6, 1),
+                           "scene_baked_mb": round(scene.baked_bytes() / 1e6, 1),
                            "block_fraction": round(scene.stats["block_fraction"], 4),
                            "l2": "inputs larger than L2 (scene and per-step output each exceed 126 MB); no flush",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -709,7 +715,7 @@ def run_ours(args):
                              "kernel_ms": mean_kern_ms,
                              "peak_source": peak_src,
                              "note": "algorithmic gather bytes (no reuse) over the measured HBM copy peak, as "
-                                     "the metric defines its roofline; L1/L2 serve all but 0.2 % of the "
+                                     "the metric defines its roofline; L1/L2 serve all but 0.3 % of the "
                                      "gather, and the binding limit is instruction issue (roofline_issue)"},
                 "gpu_launches": args.steps,
                 "e2e": e2e, "clocks": ck}

@@ -121,7 +121,10 @@ typedef struct merf_scene merf_scene;  /* opaque; owns device memory */
  *   occ_levels  n_occ_levels pointers to uint8 [N][N][N], non-zero = occupied
  *   mlp_weights float32 [883]: W0[34][16], b0[16], W1[16][16], b1[16], W2[16][3], b2[3]
  * On the device the weights become one 11,776-byte block: the FP32 weights, then the FP16 and
- * BF16 forms packed as the tensor cores read them (built by a kernel on `stream`).
+ * BF16 forms packed as the tensor cores read them (built by a kernel on `stream`).  The atlas
+ * (with a one-voxel apron per block) and the planes (with a one-texel border) are stored as
+ * 16-byte texel pairs along x (along u for a plane), the two texels' bytes interleaved: about
+ * twice the texel bytes of the baked arrays, so that the renderer needs no byte permutes.
  * The layout is validated (ids in range, every coarse occupancy cell that is empty has
  * only empty children) before anything is allocated.  Returns MERF_ERR_OOM without
  * touching the device if the scene exceeds the budget set by merf_set_device_budget.
@@ -157,7 +160,8 @@ merf_status merf_scene_upload_dense(const merf_scene_desc *desc, const float *gr
 /* Release a scene (NULL is ignored).  Synchronises the device first. */
 void merf_scene_free(merf_scene *scene);
 
-/* Device bytes held by a scene (its arrays plus the 11,776-byte MLP block). */
+/* Device bytes held by a scene (its arrays in the device layout plus the 11,776-byte MLP
+ * block). */
 size_t merf_scene_device_bytes(const merf_scene *scene);
 
 /* Scene files: one baked scene as a raw binary file -- the arrays merf_scene_upload(_dense) takes,

@@ -10,18 +10,22 @@
 // stored contributes nothing).  A grid-only scene (no planes, R = 0: the SNeRG++-style baseline
 // of Sec. 6) has t~ = V and the offset m_c W_V.
 //
-// Layout in HBM.  Every texel is 8 bytes (one uint2: channels 0..3 in .x, 4..7 in .y), so a
-// single 64-bit load fetches density and appearance of a corner.  The 3D grid is
-// block-sparse: an int32 index grid over (L/B)^3 blocks holds, for a stored block, its atlas
-// slot in bits 0..23 and in bits 24..30 a mask of which of its +x/+y/+z neighbour blocks are
-// not stored (neighbour dx + 2 dy + 4 dz in 1..7 at bit 23 + that number); -1 marks a block
-// that is not stored.  Each atlas slot holds (B+1)^3 voxels [z][y][x]: the block plus a
-// one-voxel apron copied from its +x/+y/+z neighbours, so the eight corners of any sample
-// whose lowest corner lies in the block are one base address plus constant offsets.
+// Layout in HBM.  A texel is 8 bytes (channels 0..7), and every texel is stored together with
+// its +x neighbour (the +u neighbour in a plane) as one 16-byte texel pair, the two texels' bytes
+// interleaved (a0, b0, a1, b1, ..., a7, b7): one 128-bit load fetches density and appearance of
+// two corners in the byte order the interpolation's dot products take, so no byte permute is
+// left per sample (the pair of a row's last texel has a zero upper texel).  This doubles the
+// texel storage against 8 bytes per texel, for 10 loads and 40 permutes fewer per sample.  The
+// 3D grid is block-sparse: an int32 index grid over (L/B)^3 blocks holds, for a stored block,
+// its atlas slot in bits 0..23 and in bits 24..30 a mask of which of its +x/+y/+z neighbour
+// blocks are not stored (neighbour dx + 2 dy + 4 dz in 1..7 at bit 23 + that number); -1 marks
+// a block that is not stored.  Each atlas slot holds (B+1)^3 voxel pairs [z][y][x]: the block
+// plus a one-voxel apron copied from its +x/+y/+z neighbours, so the four corner pairs of any
+// sample whose lowest corner lies in the block are one base address plus constant offsets.
 // For the 3D grid, clamp-to-edge is folded into the integer coordinate and weight (lowest corner
-// kept in [0, N-2]), so no lookup leaves the array.  The planes are stored [3][R+2][R+2] with a
-// one-texel border that repeats their edge texels, so their taps need no clamp.  The occupancy
-// grids are not read here (the traversal tests them before a sample is evaluated).
+// kept in [0, N-2]), so no lookup leaves the array.  The planes are stored [3][R+2][R+2] (texel
+// pairs) with a one-texel border that repeats their edge texels, so their taps need no clamp.
+// The occupancy grids are not read here (the traversal tests them before a sample is evaluated).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -36,8 +40,8 @@ namespace merf {
 
 struct FieldView {
     const int32_t *index_grid;   // [(L/B)^3] slot | missing-neighbour mask << 24, or -1
-    const uint2 *atlas;          // [n_blocks][B+1][B+1][B+1]
-    const uint2 *planes;         // [3][R+2][R+2]: one-texel clamp-to-edge border
+    const uint4 *atlas;          // [n_blocks][B+1][B+1][B+1] texel pairs (x, x + 1)
+    const uint4 *planes;         // [3][R+2][R+2] texel pairs (u, u + 1): one-texel clamp-to-edge border
     const float4 *grid_f32;      // dense storage: [L][L][L][2]
     const float4 *planes_f32;    // dense storage: [3][R][R][2]
     int L, B, log2B, nb, R;
@@ -74,13 +78,37 @@ __device__ __forceinline__ void plane_coord(float p, float scale, int half, int 
     f = __fadd_rn(__fsub_rn(a, n), 0.5f);
 }
 
-// The 20 texels of one sample (8 grid corners, 4 texels in each plane) and their weights.
+// The 20 texels of one sample (8 grid corners, 4 texels in each plane) as 10 texel pairs, each
+// pair's bytes interleaved (pair_bytes), and their weights.
 struct Taps {
-    uint2 v[20];
+    uint4 q[10];
     float fx, fy, fz;       // grid fractions
     float fu[3];            // plane fractions along x, y, z
     float wv;               // weight of the stored grid corners
 };
+
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel)
+{
+    // PTX prmt, default mode: a selector nibble with its high bit set replicates the selected
+    // byte's sign bit over the output byte (used here on bytes whose top bit is zero, for zeros)
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+// The byte pairs of texels a and b: channels (0, 1), (2, 3), (4, 5), (6, 7), each as
+// (a.c, b.c, a.c', b.c'): the two texels' bytes interleaved, as the scene stores its texel pairs.
+__device__ __forceinline__ uint4 pair_bytes(uint2 a, uint2 b)
+{
+    return make_uint4(prmt(a.x, b.x, 0x5140u), prmt(a.x, b.x, 0x7362u), prmt(a.y, b.y, 0x5140u),
+                      prmt(a.y, b.y, 0x7362u));
+}
+
+// The lower texel of an interleaved pair (its even bytes).
+__device__ __forceinline__ uint2 pair_lower(uint4 q)
+{
+    return make_uint2(prmt(q.x, q.y, 0x6420u), prmt(q.z, q.w, 0x6420u));
+}
 
 // Trilinear weight of grid corner c.  A corner that is not stored holds zero bytes (the apron
 // of a missing neighbour is zero-filled and the slow path loads zeros), so it contributes
@@ -99,11 +127,13 @@ __device__ __forceinline__ float stored_weight(const Taps &t, uint32_t mask)
     return wv;
 }
 
-// Lowest corner in a block that is not stored: every corner is looked up on its own.
+// Lowest corner in a block that is not stored: every corner is looked up on its own (as the
+// lower texel of its stored pair) and the pairs are interleaved here.
 __device__ __forceinline__ void gather_grid_slow(const FieldView &fv, int x0, int y0, int z0, Taps &t)
 {
     const int sh = fv.log2B, msk = fv.B - 1, nb = fv.nb, B1 = fv.B + 1;
     uint32_t gmask = 0u;
+    uint2 v[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         const int x = x0 + (c & 1), y = y0 + ((c >> 1) & 1), z = z0 + (c >> 2);
@@ -112,12 +142,14 @@ __device__ __forceinline__ void gather_grid_slow(const FieldView &fv, int x0, in
         const size_t slot = (size_t)(ent & 0xffffff);
         const size_t ai = ((slot * B1 + (z & msk)) * B1 + (y & msk)) * B1 + (x & msk);
         if (ent >= 0 && MERF_IN_RANGE(ai, (long long)fv.n_blocks * B1 * B1 * B1, kBadAtlas)) {
-            t.v[c] = __ldg(fv.atlas + ai);
+            v[c] = pair_lower(__ldg(fv.atlas + ai));
             gmask |= 1u << c;
         } else {
-            t.v[c] = make_uint2(0u, 0u);
+            v[c] = make_uint2(0u, 0u);
         }
     }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) t.q[p] = pair_bytes(v[2 * p], v[2 * p + 1]);
     t.wv = stored_weight(t, gmask);
 }
 
@@ -162,20 +194,16 @@ __device__ __forceinline__ void gather_u8(const FieldView &fv, float p0, float p
         // bounds-checked build: the farthest corner is ai + B1^2 + B1 + 1
         if (!MERF_IN_RANGE(ai + B1 * B1 + B1 + 1, (long long)fv.n_blocks * B1 * B1 * B1, kBadAtlas)) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) t.v[c] = make_uint2(0u, 0u);
+            for (int c = 0; c < 4; ++c) t.q[c] = make_uint4(0u, 0u, 0u, 0u);
             t.wv = 0.0f;
             goto grid_done;
         }
-        const uint2 *base = fv.atlas + ai;
+        const uint4 *base = fv.atlas + ai;
         const int sy = B1, sz = B1 * B1;
-        t.v[0] = __ldg(base);
-        t.v[1] = __ldg(base + 1);
-        t.v[2] = __ldg(base + sy);
-        t.v[3] = __ldg(base + sy + 1);
-        t.v[4] = __ldg(base + sz);
-        t.v[5] = __ldg(base + sz + 1);
-        t.v[6] = __ldg(base + sz + sy);
-        t.v[7] = __ldg(base + sz + sy + 1);
+        t.q[0] = __ldg(base);
+        t.q[1] = __ldg(base + sy);
+        t.q[2] = __ldg(base + sz);
+        t.q[3] = __ldg(base + sz + sy);
         t.wv = 1.0f;
         const uint32_t miss = ((uint32_t)ent >> 24) << 1;     // bit n: neighbour n not stored
         if (miss) {
@@ -206,14 +234,12 @@ grid_done:;
         const int ca = q == 0 ? 1 : 0, ra = q == 2 ? 1 : 2;
         const Idx pi = ((Idx)q * Rp + u0[ra]) * Rp + u0[ca];
         if (!MERF_IN_RANGE(pi + Rp + 1, 3LL * Rp * Rp, kBadPlane)) {
-            t.v[8 + 4 * q + 0] = t.v[8 + 4 * q + 1] = t.v[8 + 4 * q + 2] = t.v[8 + 4 * q + 3] = make_uint2(0u, 0u);
+            t.q[4 + 2 * q] = t.q[4 + 2 * q + 1] = make_uint4(0u, 0u, 0u, 0u);
             continue;
         }
-        const uint2 *base = fv.planes + pi;
-        t.v[8 + 4 * q + 0] = __ldg(base);
-        t.v[8 + 4 * q + 1] = __ldg(base + 1);
-        t.v[8 + 4 * q + 2] = __ldg(base + Rp);
-        t.v[8 + 4 * q + 3] = __ldg(base + Rp + 1);
+        const uint4 *base = fv.planes + pi;
+        t.q[4 + 2 * q] = __ldg(base);
+        t.q[4 + 2 * q + 1] = __ldg(base + Rp);
     }
 }
 
@@ -221,11 +247,11 @@ grid_done:;
 // Weighted byte sums by integer dot products.  The interpolated value of channel c is
 // K_c = sum_i w_i b_ic over the taps i (8 grid corners, then 4 texels per plane), and bytes are
 // exact integers, so the sum is formed in integer arithmetic from fixed-point weights: the taps
-// are taken in pairs (i, j); one byte permute interleaves two channels of the pair's texels as
-// (b_ic, b_jc, b_ic', b_jc'), and dp2a multiplies a byte pair by a pair of 16-bit weights
-// (w_i, w_j) and adds to a 32-bit accumulator, exactly.  A pair of taps and two channels cost one
-// permute and two dot products, where float arithmetic needs a permute per byte, a subtraction and
-// a multiply-add per two bytes.
+// are taken in pairs (i, j), whose texel pair holds two channels as (b_ic, b_jc, b_ic', b_jc') in
+// each 32-bit word, and dp2a multiplies a byte pair by a pair of 16-bit weights (w_i, w_j) and
+// adds to a 32-bit accumulator, exactly.  A pair of taps and two channels cost two dot products,
+// where float arithmetic needs a permute per byte, a subtraction and a multiply-add per two
+// bytes.
 //
 // Weights.  One fused multiply-add forms each weight's last product and rounds it to the integer
 // W = round(w S), S = 256 * 32767 = 2^23 - 256, in the low mantissa bits of M + w S (M = 2^23, or
@@ -246,15 +272,6 @@ grid_done:;
 // Either way density rests on the same exact integer X = sum_i W_i b_i0; the forms differ only in
 // how its two parts are converted and combined in float (a few ulps of the pre-activation).
 // A grid corner that is not stored holds zero bytes, so it adds nothing whatever its weight.
-
-__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel)
-{
-    // PTX prmt, default mode: a selector nibble with its high bit set replicates the selected
-    // byte's sign bit over the output byte (used here on bytes whose top bit is zero, for zeros)
-    uint32_t d;
-    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
-    return d;
-}
 
 // c + a.h0 * b.b0 + a.h1 * b.b1 (lo) or c + a.h0 * b.b2 + a.h1 * b.b3 (hi), unsigned
 __device__ __forceinline__ uint32_t dp2a_lo(uint32_t a, uint32_t b, uint32_t c)
@@ -339,16 +356,6 @@ __device__ __forceinline__ void weight_words(const Taps &t, uint32_t w[nt])
     }
 }
 
-// The byte pairs of taps a and b: channels (0, 1), (2, 3), (4, 5), (6, 7), each as
-// (a.c, b.c, a.c', b.c').
-__device__ __forceinline__ void pair_bytes(uint2 a, uint2 b, uint32_t B[4])
-{
-    B[0] = prmt(a.x, b.x, 0x5140u);
-    B[1] = prmt(a.x, b.x, 0x7362u);
-    B[2] = prmt(a.y, b.y, 0x5140u);
-    B[3] = prmt(a.y, b.y, 0x7362u);
-}
-
 // Integer weighted byte sums of one sample over the first nt taps.  kPrec 0 (FP32): every
 // channel at two levels, K_c = (256 hi[c] + lo[c]) / S.  kPrec 1, 2 (the 16-bit forms): the
 // rounded high level of every channel, hi[c] (K_c = hi[c] / 32767 for appearance), and for
@@ -359,7 +366,8 @@ struct DotSums {
     uint32_t n0;                                 // 16-bit forms only
 };
 
-// One tap pair's contribution.  FP32: the weight words come in; 16-bit forms: the pair's words
+// One tap pair's contribution: its texel pair's four words are the byte pairs of channels
+// (0, 1), (2, 3), (4, 5), (6, 7).  FP32: the weight words come in; 16-bit forms: the pair's words
 // are formed here, just before use, so that only one pair's are live at a time.
 template <int kPrec, int p>
 __device__ __forceinline__ void dot_pair(const Taps &t, DotSums<kPrec> &s, const uint32_t *w)
@@ -373,8 +381,7 @@ __device__ __forceinline__ void dot_pair(const Taps &t, DotSums<kPrec> &s, const
     }
     const uint32_t wh = prmt(m0, m1, kSelHigh);
     const uint32_t wl = prmt(m0, m1, kSelLow);
-    uint32_t B[4];
-    pair_bytes(t.v[2 * p], t.v[2 * p + 1], B);
+    const uint32_t B[4] = {t.q[p].x, t.q[p].y, t.q[p].z, t.q[p].w};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         s.hi[2 * q] = dp2a_lo(wh, B[q], s.hi[2 * q]);

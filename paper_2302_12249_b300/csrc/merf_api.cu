@@ -354,36 +354,52 @@ static std::vector<int32_t> index_with_neighbour_masks(const int32_t *index_grid
 
 // The padded atlas from an unpadded one in device memory: CTA `slot` fills the (B+1)^3 voxels of
 // that atlas slot (the block at `coords[slot]` = bx | by << 10 | bz << 20, plus its +x/+y/+z apron
-// from the neighbouring blocks; zero where a neighbour is not stored or past the grid edge).
-// index_grid: the caller's grid (slot or -1), already validated.
+// from the neighbouring blocks; zero where a neighbour is not stored or past the grid edge), each
+// stored as the texel pair (x, x + 1) with the two texels' bytes interleaved (pair_bytes); the
+// pair of the last column has a zero upper texel.  index_grid: the caller's grid (slot or -1),
+// already validated.
 __global__ void pad_atlas_kernel(const uint2 *atlas, const int32_t *index_grid, const uint32_t *coords, int L, int B,
-                                 uint2 *padded)
+                                 uint4 *padded)
 {
     const int slot = blockIdx.x, B1 = B + 1, nb = L / B;
     const uint32_t c = coords[slot];
     const int bx = c & 1023, by = (c >> 10) & 1023, bz = c >> 20;
-    uint2 *dst = padded + (size_t)slot * B1 * B1 * B1;
+    uint4 *dst = padded + (size_t)slot * B1 * B1 * B1;
+    auto voxel = [&](int gx, int gy, int gz) {
+        if (gx >= L || gy >= L || gz >= L) return make_uint2(0u, 0u);
+        const int src = index_grid[((size_t)(gz / B) * nb + gy / B) * nb + gx / B];
+        return src >= 0 ? atlas[(((size_t)src * B + gz % B) * B + gy % B) * B + gx % B] : make_uint2(0u, 0u);
+    };
     for (int v = threadIdx.x; v < B1 * B1 * B1; v += blockDim.x) {
         const int lx = v % B1, ly = (v / B1) % B1, lz = v / (B1 * B1);
         const int gx = bx * B + lx, gy = by * B + ly, gz = bz * B + lz;
-        uint2 val = make_uint2(0u, 0u);
-        if (gx < L && gy < L && gz < L) {
-            const int src = index_grid[((size_t)(gz / B) * nb + gy / B) * nb + gx / B];
-            if (src >= 0) val = atlas[(((size_t)src * B + gz % B) * B + gy % B) * B + gx % B];
-        }
-        dst[v] = val;
+        dst[v] = merf::pair_bytes(voxel(gx, gy, gz), lx < B ? voxel(gx + 1, gy, gz) : make_uint2(0u, 0u));
     }
 }
 
-// Planes with a one-texel border that repeats their edge texels: [3][R+2][R+2] from [3][R][R].
-__global__ void border_planes_kernel(const uint2 *planes, int R, uint2 *bordered)
+// Planes with a one-texel border that repeats their edge texels, [3][R+2][R+2] from [3][R][R],
+// each stored as the texel pair (u, u + 1), bytes interleaved; the last column's upper texel is zero.
+__global__ void border_planes_kernel(const uint2 *planes, int R, uint4 *bordered)
 {
     const int Rp = R + 2;
     const size_t n = 3ull * Rp * Rp;
+    auto texel = [&](int q, int u, int v) {
+        const int su = min(max(u - 1, 0), R - 1), sv = min(max(v - 1, 0), R - 1);
+        return planes[((size_t)q * R + sv) * R + su];
+    };
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
         const int u = (int)(t % Rp), v = (int)((t / Rp) % Rp), q = (int)(t / ((size_t)Rp * Rp));
-        const int su = min(max(u - 1, 0), R - 1), sv = min(max(v - 1, 0), R - 1);
-        bordered[t] = planes[((size_t)q * R + sv) * R + su];
+        bordered[t] = merf::pair_bytes(texel(q, u, v), u + 1 < Rp ? texel(q, u + 1, v) : make_uint2(0u, 0u));
+    }
+}
+
+// Host side of the same layout: the 8 bytes of texel `src` as the lower texel of pair `lower`
+// (even bytes) and, when given, the upper texel of pair `upper` (odd bytes).
+static void put_in_pairs(const uint8_t *src, uint8_t *lower, uint8_t *upper)
+{
+    for (int k = 0; k < 8; ++k) {
+        lower[2 * k] = src[k];
+        if (upper) upper[2 * k + 1] = src[k];
     }
 }
 
@@ -418,7 +434,7 @@ merf_status merf_scene_upload(const merf_scene_desc *desc, const int32_t *index_
     std::vector<uint8_t> apron;
     std::vector<int32_t> ig;
     try {
-        apron.assign((size_t)desc->n_blocks * B1 * B1 * B1 * 8, 0);
+        apron.assign((size_t)desc->n_blocks * B1 * B1 * B1 * 16, 0);
         ig = index_with_neighbour_masks(index_grid, nbi);
     } catch (...) {
         return fail(MERF_ERR_OOM, "host memory for the padded atlas");
@@ -432,7 +448,7 @@ merf_status merf_scene_upload(const merf_scene_desc *desc, const int32_t *index_
             for (size_t bx = 0; bx < nbi; ++bx) {
                 const int32_t id = id_at(bx, by, bz);
                 if (id < 0) continue;
-                uint8_t *dst = apron.data() + (size_t)id * B1 * B1 * B1 * 8;
+                uint8_t *dst = apron.data() + (size_t)id * B1 * B1 * B1 * 16;
                 for (int lz = 0; lz < B1; ++lz)
                     for (int ly = 0; ly < B1; ++ly)
                         for (int lx = 0; lx < B1; ++lx) {
@@ -441,16 +457,19 @@ merf_status merf_scene_upload(const merf_scene_desc *desc, const int32_t *index_
                             const int32_t src = id_at(gx / B, gy / B, gz / B);
                             if (src < 0) continue;
                             const uint8_t *sv = atlas + ((((size_t)src * B + gz % B) * B + gy % B) * B + gx % B) * 8;
-                            memcpy(dst + (((size_t)lz * B1 + ly) * B1 + lx) * 8, sv, 8);
+                            uint8_t *pair = dst + (((size_t)lz * B1 + ly) * B1 + lx) * 16;
+                            put_in_pairs(sv, pair, lx > 0 ? pair - 16 : nullptr);
                         }
             }
     // Each plane gets a one-texel border that repeats its edge texels, so that bilinear taps of
     // clamp-to-edge interpolation never need their coordinates clamped: [3][R+2][R+2].
     // (a grid-only scene, R = 0, has no planes at all)
+    // Atlas voxels and plane texels are stored as pairs along x (the column axis), bytes
+    // interleaved: the byte order the interpolation's dot products take.
     const size_t Rp = R + 2;
     std::vector<uint8_t> padded;
     try {
-        padded.resize(R > 0 ? 3 * Rp * Rp * 8 : 0);
+        padded.assign(R > 0 ? 3 * Rp * Rp * 16 : 0, 0);
     } catch (...) {
         return fail(MERF_ERR_OOM, "host memory for the bordered planes");
     }
@@ -458,7 +477,8 @@ merf_status merf_scene_upload(const merf_scene_desc *desc, const int32_t *index_
         for (size_t v = 0; v < Rp; ++v)
             for (size_t u = 0; u < Rp; ++u) {
                 const size_t sv = v == 0 ? 0 : v > R ? R - 1 : v - 1, su = u == 0 ? 0 : u > R ? R - 1 : u - 1;
-                memcpy(padded.data() + ((q * Rp + v) * Rp + u) * 8, planes + ((q * R + sv) * R + su) * 8, 8);
+                uint8_t *pair = padded.data() + ((q * Rp + v) * Rp + u) * 16;
+                put_in_pairs(planes + ((q * R + sv) * R + su) * 8, pair, u > 0 ? pair - 16 : nullptr);
             }
     return upload_common(desc, apron.data(), apron.size(), padded.data(), padded.size(), ig.data(),
                          nb * nb * nb * sizeof(int32_t), occ_levels, mlp_weights, stream, out);
@@ -521,7 +541,7 @@ merf_status merf_scene_upload_device(const merf_scene_desc *desc, const int32_t 
     // bordered planes by kernels from the caller's arrays; the rest copied.
     const int B = desc->block_size, B1 = B + 1;
     const size_t R = desc->plane_res, Rp = R + 2;
-    const size_t atlas_bytes = (size_t)desc->n_blocks * B1 * B1 * B1 * 8, plane_bytes = R > 0 ? 3 * Rp * Rp * 8 : 0;
+    const size_t atlas_bytes = (size_t)desc->n_blocks * B1 * B1 * B1 * 16, plane_bytes = R > 0 ? 3 * Rp * Rp * 16 : 0;
     size_t total = atlas_bytes + plane_bytes + n_index * sizeof(int32_t) + merf::kMlpBlockBytes;
     for (int l = 0; l < desc->n_occ_levels; ++l) total += occ[l].size();
     if (g_budget && total > g_budget)
@@ -554,11 +574,11 @@ merf_status merf_scene_upload_device(const merf_scene_desc *desc, const int32_t 
     if (e == cudaSuccess) e = put_mlp_block(sc->mlp, d_mlp, cudaMemcpyDeviceToDevice, cs);
     if (e == cudaSuccess && desc->n_blocks > 0) {
         pad_atlas_kernel<<<desc->n_blocks, 256, 0, cs>>>((const uint2 *)d_atlas, d_index_grid, d_coords, desc->grid_res,
-                                                         B, (uint2 *)sc->atlas);
+                                                         B, (uint4 *)sc->atlas);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && R > 0) {
-        border_planes_kernel<<<4 * 148, 256, 0, cs>>>((const uint2 *)d_planes, (int)R, (uint2 *)sc->planes);
+        border_planes_kernel<<<4 * 148, 256, 0, cs>>>((const uint2 *)d_planes, (int)R, (uint4 *)sc->planes);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(cs);

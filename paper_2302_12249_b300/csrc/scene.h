@@ -39,8 +39,8 @@ inline void scene_views(const merf_scene *s, FieldView &fv, OccView &occ)
         fv.nb = d.grid_res / d.block_size;
         fv.n_blocks = d.n_blocks;
         fv.index_grid = (const int32_t *)s->index_grid;
-        fv.atlas = (const uint2 *)s->atlas;
-        fv.planes = (const uint2 *)s->planes;
+        fv.atlas = (const uint4 *)s->atlas;
+        fv.planes = (const uint4 *)s->planes;
     } else {
         fv.grid_f32 = (const float4 *)s->atlas;
         fv.planes_f32 = (const float4 *)s->planes;

@@ -130,7 +130,10 @@ class Scene:
     def n_blocks(self) -> int:
         return 0 if self.atlas is None else int(self.atlas.shape[0])
 
-    def device_bytes(self) -> int:
+    def baked_bytes(self) -> int:
+        """Bytes of the baked arrays (8 bytes per texel, no apron or border): the representation's
+        size, as a scene file stores it.  The library's device layout is larger
+        (merf.Scene.device_bytes)."""
         n = sum(int(o.nbytes) for o in self.occ) + int(self.mlp.nbytes)
         for a in (self.index_grid, self.atlas, self.planes, self.grid_f32, self.planes_f32):
             if a is not None:
@@ -355,7 +358,7 @@ def make_scene(name_or_cfg, seed: Optional[int] = None, mlp_seed: int = SEED_MLP
         scene.grid_f32 = grid.to(torch.float32).numpy()
         scene.planes_f32 = planes.numpy()
     scene.stats["occ_fraction"] = float(finest.float().mean())
-    scene.stats["device_mb"] = scene.device_bytes() / 1e6
+    scene.stats["baked_mb"] = scene.baked_bytes() / 1e6
     return scene
 
 
