@@ -227,10 +227,9 @@ merf_status merf_render_host(const merf_scene *scene, const merf_camera *cams, i
  * `h_out` (host float32 [n_cams][H][W][3]; page-locked for the copy to be asynchronous).
  * Requests whose image exceeds the staging area return MERF_ERR_INVALID_ARG.  The first call
  * on a device looks up the staging area's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  All calls share the one
- * staging area: the kernel writes every pixel of it that the call returns, so nothing needs
- * clearing, but calls that overlap on the GPU (from several host threads or streams at once)
- * race on it.  Returns after the copy has completed. */
+ * device current.  All calls share the one staging area: the kernel writes every pixel of it
+ * that the call returns, so nothing needs clearing, but calls that overlap on the GPU (from
+ * several host threads or streams at once) race on it.  Returns after the copy has completed. */
 enum { MERF_NOALLOC_STAGING_BYTES = 32 << 20 };
 merf_status merf_render_host_noalloc(const merf_scene *scene, const merf_camera *cams, int n_cams,
                                      int W, int H, float *h_out, const merf_render_opts *opts,
