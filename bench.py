@@ -5,7 +5,7 @@ feature-gather bandwidth roofline).
 One step renders 8 cameras at 1920 x 1080 (16.6 M pixel rays) of the paper-scale synthetic
 scene: 512^3 grid in 16^3 blocks, three 2048^2 planes, occupancy 128^3..16^3, step 1/256,
 cameras on a ring of radius 1.5.  Inputs are resident in HBM before timing; the scene
-(722 MB on the device) and each step's output (199 MB) exceed the 126 MB L2, so no flush is
+(1442 MB on the device) and each step's output (199 MB) exceed the 126 MB L2, so no flush is
 needed.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
