@@ -329,3 +329,15 @@ def test_paper_sparsity_scene_sampled_pixels():
     err = parity.max_err(rgb[lin], lo, hi)
     assert err.max() <= parity.RGB_TOL, (err.max(), np.argmax(err))
     assert aux[lin, merf.AUX_NEVAL].mean() > 1.0          # the rays do meet the blobs
+
+
+def test_device_layout_is_texel_pairs(tiny_scene):
+    """The device layout the upload builds: every atlas voxel and plane texel stored as a 16-byte
+    texel pair (with its +x / +u neighbour), atlas slots of (B+1)^3 pairs, planes bordered to
+    (R+2)^2 pairs, plus the index grid, the occupancy levels and the 11,776-byte MLP block."""
+    sc = tiny_scene
+    gs = merf.Scene(sc)
+    B, R = sc.cfg.B, sc.cfg.R
+    want = (sc.n_blocks * (B + 1) ** 3 * 16 + 3 * (R + 2) ** 2 * 16 + sc.index_grid.nbytes
+            + sum(o.nbytes for o in sc.occ) + 11776)
+    assert gs.device_bytes == want
