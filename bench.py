@@ -44,7 +44,7 @@ B_DENSITY, B_INDEX, B_APPEAR, B_OUT = 20, 4, 140, 12
 # launch from an ncu capture of this workload; reported as roofline.traffic only while the
 # render kernel's sources (device code, launch and scene layout) hash to the value they were
 # measured with (otherwise null).
-TRAFFIC_BYTES_PER_LAUNCH = (727.44 + 295.96) * 1e6
+TRAFFIC_BYTES_PER_LAUNCH = (722.20 + 279.55) * 1e6
 TRAFFIC_SOURCES = ("debug.cuh", "field.cuh", "geometry.h", "merf_api.cu", "render.cuh", "scene.h", "traverse.cuh",
                    "umma.cuh")
 # Warp-level instructions (smsp__inst_executed.sum) of the same timed launch from an ncu capture
@@ -52,7 +52,7 @@ TRAFFIC_SOURCES = ("debug.cuh", "field.cuh", "geometry.h", "merf_api.cu", "rende
 # an SM's four schedulers issue at most one warp instruction per clock each.
 INST_PER_LAUNCH = 34.947777282e9
 SMS, SCHEDULERS_PER_SM = 148, 4
-TRAFFIC_SOURCES_SHA256 = "4cfdaa75152e2a6bddb8d0fdfd9e4c01d67ea0ddfa3b87d318ae6c2ab5ea66bb"
+TRAFFIC_SOURCES_SHA256 = "3e42bb6721a6af1b377891f6cf88acea25c9ee99b346a86a9eef0d0fb95795eb"
 
 
 def _sources_sha256() -> str:

@@ -780,9 +780,11 @@ __global__ void __launch_bounds__(kThreads, (kMinBlocks<kStorage, kPrec>)) rende
     deferred_mlp<kPrec>(ms, us, r, inside, h);
     if (inside) {
         const size_t pix = ((size_t)(P.cam0 + cl) * P.H + j) * P.W + i;
-        P.out[pix * 3 + 0] = r.cd[0] + h[0];
-        P.out[pix * 3 + 1] = r.cd[1] + h[1];
-        P.out[pix * 3 + 2] = r.cd[2] + h[2];
+        // streaming stores: the image is not read again by this launch, so it should not
+        // displace the scene's texels or the rays' stacks in L2
+        __stcs(P.out + pix * 3 + 0, r.cd[0] + h[0]);
+        __stcs(P.out + pix * 3 + 1, r.cd[1] + h[1]);
+        __stcs(P.out + pix * 3 + 2, r.cd[2] + h[2]);
         if (P.aux) {
             float *a = P.aux + pix * kAuxSize;
             a[0] = r.cd[0]; a[1] = r.cd[1]; a[2] = r.cd[2];
