@@ -52,7 +52,7 @@ TRAFFIC_SOURCES = ("debug.cuh", "field.cuh", "geometry.h", "merf_api.cu", "rende
 # an SM's four schedulers issue at most one warp instruction per clock each.
 INST_PER_LAUNCH = 34.947777282e9
 SMS, SCHEDULERS_PER_SM = 148, 4
-TRAFFIC_SOURCES_SHA256 = "3e42bb6721a6af1b377891f6cf88acea25c9ee99b346a86a9eef0d0fb95795eb"
+TRAFFIC_SOURCES_SHA256 = "3da0b7c1f60f5874bf95166a725e5e2043c3ac435f004b9c31a91cadb398c28d"
 
 
 def _sources_sha256() -> str:

@@ -249,9 +249,9 @@ grid_done:;
 // exact integers, so the sum is formed in integer arithmetic from fixed-point weights: the taps
 // are taken in pairs (i, j), whose texel pair holds two channels as (b_ic, b_jc, b_ic', b_jc') in
 // each 32-bit word, and dp2a multiplies a byte pair by a pair of 16-bit weights (w_i, w_j) and
-// adds to a 32-bit accumulator, exactly.  A pair of taps and two channels cost two dot products,
-// where float arithmetic needs a permute per byte, a subtraction and a multiply-add per two
-// bytes.
+// adds to a 32-bit accumulator, exactly.  A pair of taps and two channels cost two dot products
+// per weight level, where float arithmetic needs a permute per byte, a subtraction and a
+// multiply-add per two bytes.
 //
 // Weights.  One fused multiply-add forms each weight's last product and rounds it to the integer
 // W = round(w S), S = 256 * 32767 = 2^23 - 256, in the low mantissa bits of M + w S (M = 2^23, or
